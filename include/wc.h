@@ -1,0 +1,186 @@
+/*
+ * wc.h -- C ABI of the GB300 Wilson-Clover library (libwc.so).
+ *
+ * The library applies the Wilson-Clover quark matrix
+ *     M = (1 + T) - kappa H
+ * to colour-spinor fields on a 4-D lattice and solves M x = b with BiCGStab,
+ * plain in FP64 or as an FP64 flexible (defect-correction) outer loop around
+ * an FP32/FP16-storage overlapped Restricted Additive Schwarz (RAS)
+ * preconditioner whose blocks are solved inside CTAs.  This is the solver
+ * stack of the paper's CCS-QCD benchmark (Sec. 2: double-precision flexible
+ * BiCGStab, single-precision preconditioner, overlapped RAS, SU(3)
+ * reconstruction; Sec. 3: the hopping multiplication "MULT").
+ *
+ * Conventions (the paper names the operator but prints no formula; these
+ * are this library's reading, identical to the test oracle's):
+ *   - site index  s = x + Lx*(y + Ly*(z + Lz*t)), directions mu = x,y,z,t
+ *   - chiral Dirac basis: gamma_k = [[0, i s_k], [-i s_k, 0]],
+ *     gamma_t = [[0, 1], [1, 0]], gamma_5 = diag(-1, -1, 1, 1)
+ *   - (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                        + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu);
+ *     hops across the time boundary are multiplied by t_bc (+1 or -1)
+ *   - T(x) = i csw kappa sum_{mu<nu} sigma_munu (x) Fhat_munu(x) with
+ *     sigma_munu = (i/2)[gamma_mu, gamma_nu] and Fhat the traceless
+ *     anti-Hermitian part of the four-leaf clover sum divided by 8
+ *
+ * Canonical (caller-side) layouts, all complex128 = interleaved (re, im)
+ * doubles in C order:
+ *   gauge   U[Lt][Lz][Ly][Lx][mu][3][3]   (row, column)
+ *   spinor  psi[Lt][Lz][Ly][Lx][spin 4][colour 3]
+ *   force   F[Lt][Lz][Ly][Lx][mu][3][3]
+ * Any pointer argument named "data" below may be a device pointer or a host
+ * pointer (pageable or pinned); the library detects which.  The library
+ * copies what it needs into memory it owns and never keeps a caller pointer
+ * after a call returns.
+ *
+ * Errors: every call returns a wc_status; no C++ exception crosses the ABI.
+ * A human-readable message for the last failure on a lattice is returned by
+ * wc_last_error(lat) (wc_last_error(NULL) for failures without a lattice).
+ * Argument errors are reported before any kernel is launched.
+ *
+ * Streams: each lattice runs its kernels on one CUDA stream, given at
+ * creation (NULL = the legacy default stream).  Applies, imports/exports of
+ * device data, casts and RAS applications are asynchronous with respect to
+ * the host; reductions, solves and the force call block until their result
+ * is on the host.
+ */
+#ifndef WC_H
+#define WC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wc_lattice_s *wc_lattice;
+typedef struct wc_field_s *wc_field;
+
+typedef enum {
+    WC_OK = 0,
+    WC_ERR_ARG = 1,           /* invalid argument; nothing was launched */
+    WC_ERR_CUDA = 2,          /* a CUDA call failed; see wc_last_error */
+    WC_ERR_STATE = 3,         /* gauge field / clover term not loaded yet */
+    WC_ERR_NOT_CONVERGED = 4, /* solver hit max_iter before tol */
+    WC_ERR_BREAKDOWN = 5,     /* BiCGStab breakdown: <rhat,r>, <rhat,v> or <t,t> = 0 */
+    WC_ERR_NAN = 6,           /* a non-finite norm was met inside a reduction */
+    WC_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up */
+} wc_status;
+
+typedef enum { WC_F64 = 0, WC_F32 = 1, WC_F16 = 2 } wc_prec;
+
+typedef enum { WC_PRECOND_NONE = 0, WC_PRECOND_RAS = 1 } wc_precond;
+
+/* Overlapped RAS (paper Sec. 2, "overlapped Restricted Additive Schwarz"):
+ * the lattice is tiled from the origin by blocks of block[mu] sites; each
+ * block is extended by `overlap` sites on every face (periodically), M is
+ * restricted to the extended block with hops that leave it dropped, and
+ * mr_iters minimal-residual steps from zero solve it; only the block's core
+ * is written back.  Requires L[mu] % block[mu] == 0 and
+ * L[mu] > block[mu] + 2*overlap. */
+typedef struct {
+    int block[4];
+    int overlap;
+    int mr_iters;
+} wc_ras_params;
+
+typedef struct {
+    double tol;            /* stop when |b - M x| / |b| <= tol (true residual) */
+    int max_iter;          /* total outer iterations over all restarts */
+    int max_restarts;      /* restarts after a failed true-residual check */
+    wc_precond precond;    /* NONE: plain FP64 BiCGStab; RAS: mixed precision */
+    wc_prec inner_prec;    /* storage of the RAS preconditioner: WC_F32 or WC_F16 */
+    wc_ras_params ras;
+} wc_solve_params;
+
+typedef struct {
+    int iters;             /* BiCGStab iterations performed */
+    int restarts;
+    double true_rel_resid; /* |b - M x| / |b| recomputed in FP64 at the end */
+    double seconds;        /* wall time of the solve on the host clock */
+    wc_status status;
+} wc_solve_info;
+
+/* ---- lattices ------------------------------------------------------ */
+
+/* Create a lattice of extent dims = {Lx, Ly, Lz, Lt} (each >= 2) with time
+ * boundary factor t_bc (+1 periodic, -1 antiperiodic) whose kernels run on
+ * cuda_stream (a cudaStream_t, or NULL).  Allocates the device workspace. */
+wc_status wc_create_lattice(const int dims[4], int t_bc, void *cuda_stream, wc_lattice *out);
+wc_status wc_destroy_lattice(wc_lattice lat);
+/* Switch the stream later kernels of this lattice are queued on. */
+wc_status wc_set_stream(wc_lattice lat, void *cuda_stream);
+
+/* Load the gauge field U (canonical layout, data = device or host pointer).
+ * Links are stored as their first two rows (12 reals; paper Sec. 2,
+ * "SU(3)-reconstruction") in FP64, FP32 and FP16; the third row is rebuilt
+ * as the complex conjugate of the cross product of the first two, so U must
+ * be special unitary to working precision.  Invalidates the clover term. */
+wc_status wc_load_gauge(wc_lattice lat, const double *data);
+
+/* Build A = 1 + T from the loaded gauge field on the GPU (FP64 arithmetic)
+ * and store it as two Hermitian 6x6 blocks per site (the chiral basis makes
+ * T block diagonal in spin pairs {0,1} and {2,3}): 6 real diagonal + 15
+ * complex lower entries each, 72 reals per site, in FP64, FP32 and FP16.
+ * kappa is also the hopping parameter used by every later apply. */
+wc_status wc_load_clover(wc_lattice lat, double csw, double kappa);
+
+/* ---- fields --------------------------------------------------------- */
+
+/* A colour-spinor field owned by the library, stored in prec:
+ * FP64 / FP32 values, or FP16 values with one FP32 scale per site. */
+wc_status wc_field_create(wc_lattice lat, wc_prec prec, wc_field *out);
+wc_status wc_field_destroy(wc_field f);
+/* canonical complex128 (device or host) -> field (rounded to nearest) */
+wc_status wc_field_import(wc_field f, const double *data);
+/* field -> canonical complex128 (device or host) */
+wc_status wc_field_export(wc_field f, double *data);
+/* dst = src converted to dst's precision, times scale (any precisions). */
+wc_status wc_field_copy(wc_field dst, wc_field src, double scale);
+
+/* ---- operator --------------------------------------------------------- */
+
+/* out = M in (paper Sec. 2-3: the Wilson-Clover matrix multiplication).
+ * out and in: distinct fields of the same lattice and precision; the
+ * arithmetic is FP64 for FP64 fields and FP32 otherwise.  Asynchronous. */
+wc_status wc_apply_M(wc_lattice lat, wc_field out, wc_field in);
+/* out = M^+ in = gamma5 M gamma5 in.  Same rules as wc_apply_M. */
+wc_status wc_apply_Mdag(wc_lattice lat, wc_field out, wc_field in);
+/* out = H in (hopping term only, no clover, no kappa).  Same rules. */
+wc_status wc_apply_hop(wc_lattice lat, wc_field out, wc_field in);
+
+/* ---- fused BLAS-1 (FP64 accumulation; blocking) ---------------------- */
+
+/* re_im[0] + i re_im[1] = <a, b> = sum conj(a) b over all sites */
+wc_status wc_dot(wc_lattice lat, wc_field a, wc_field b, double *re_im);
+wc_status wc_norm2(wc_lattice lat, wc_field a, double *out);
+/* y += (a[0] + i a[1]) x, then *norm2_y = |y|^2 (norm2_y may be NULL). */
+wc_status wc_axpy_norm(wc_lattice lat, const double *a, wc_field x, wc_field y,
+                       double *norm2_y);
+
+/* ---- preconditioner and solvers --------------------------------------- */
+
+/* out = RAS(in) (see wc_ras_params).  FP32 arithmetic on FP32 or FP16
+ * fields of the same precision.  Asynchronous. */
+wc_status wc_ras_precond(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params *p);
+
+/* Solve M x = b.  x (FP64) holds the initial guess on entry and the
+ * solution on return; b is FP64.  Blocking; fills *info. */
+wc_status wc_solve_bicgstab(wc_lattice lat, wc_field x, wc_field b, const wc_solve_params *p,
+                            wc_solve_info *info);
+
+/* Solve M_i x_i = b_i for n right-hand sides on possibly different
+ * lattices in one batched solve.  Blocking; fills infos[0..n-1]. */
+wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs, wc_field *bs,
+                         const wc_solve_params *p, wc_solve_info *infos);
+
+/* S = phi^+ (M^+ M)^-1 phi and its force F = dS/dU per link as traceless
+ * anti-Hermitian 3x3 matrices (canonical force layout, data = device or
+ * host), from two FP64 solves M^+ Y = phi, M X = Y.  Blocking. */
+wc_status wc_action_force(wc_lattice lat, wc_field phi, double *S_out, double *force,
+                          const wc_solve_params *p);
+
+const char *wc_last_error(wc_lattice lat);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,275 @@
+"""GB300 Wilson-Clover operator and RAS-BiCGStab solvers (Python binding).
+
+A thin ctypes layer over ``libwc.so`` (C ABI declared in ``include/wc.h``):
+it only marshals arguments.  Every step of the operator, the reductions, the
+preconditioner and the solvers runs in the library's CUDA kernels; PyTorch
+(when used) only supplies device memory and the CUDA stream.  There is no
+CPU fallback: importing this package fails if the library is not built
+(``python -m paper_1612_06556_gb300.build`` or ``__graft_entry__.build()``).
+
+Arrays crossing the boundary use the canonical complex128 layouts of
+``include/wc.h``: gauge U[V,4,3,3], spinor psi[V,4,3], force F[V,4,3,3],
+site = x + Lx*(y + Ly*(z + Lz*t)).  They may be CUDA torch tensors, CPU
+torch tensors or numpy arrays (C-contiguous complex128).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -m paper_1612_06556_gb300.build); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+F64, F32, F16 = 0, 1, 2
+PRECOND_NONE, PRECOND_RAS = 0, 1
+STATUS = {0: "WC_OK", 1: "WC_ERR_ARG", 2: "WC_ERR_CUDA", 3: "WC_ERR_STATE", 4: "WC_ERR_NOT_CONVERGED",
+          5: "WC_ERR_BREAKDOWN", 6: "WC_ERR_NAN", 7: "WC_ERR_TIMEOUT"}
+
+EXPORTED = [
+    "wc_create_lattice", "wc_destroy_lattice", "wc_set_stream", "wc_load_gauge", "wc_load_clover",
+    "wc_field_create", "wc_field_destroy", "wc_field_import", "wc_field_export", "wc_field_copy",
+    "wc_apply_M", "wc_apply_Mdag", "wc_apply_hop", "wc_dot", "wc_norm2", "wc_axpy_norm",
+    "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
+]
+
+
+class RasParams(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int * 4), ("overlap", ctypes.c_int), ("mr_iters", ctypes.c_int)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("precond", ctypes.c_int), ("inner_prec", ctypes.c_int), ("ras", RasParams)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def __repr__(self):
+        return (f"SolveInfo(iters={self.iters}, restarts={self.restarts}, "
+                f"true_rel_resid={self.true_rel_resid:.3e}, seconds={self.seconds:.4f}, "
+                f"status={STATUS.get(self.status, self.status)})")
+
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_L = _lib
+_L.wc_create_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+_L.wc_destroy_lattice.argtypes = [_vp]
+_L.wc_set_stream.argtypes = [_vp, _vp]
+_L.wc_load_gauge.argtypes = [_vp, _vp]
+_L.wc_load_clover.argtypes = [_vp, ctypes.c_double, ctypes.c_double]
+_L.wc_field_create.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(_vp)]
+_L.wc_field_destroy.argtypes = [_vp]
+_L.wc_field_import.argtypes = [_vp, _vp]
+_L.wc_field_export.argtypes = [_vp, _vp]
+_L.wc_field_copy.argtypes = [_vp, _vp, ctypes.c_double]
+for _n in ("wc_apply_M", "wc_apply_Mdag", "wc_apply_hop"):
+    getattr(_L, _n).argtypes = [_vp, _vp, _vp]
+_L.wc_dot.argtypes = [_vp, _vp, _vp, _dp]
+_L.wc_norm2.argtypes = [_vp, _vp, _dp]
+_L.wc_axpy_norm.argtypes = [_vp, _dp, _vp, _vp, _dp]
+_L.wc_ras_precond.argtypes = [_vp, _vp, _vp, ctypes.POINTER(RasParams)]
+_L.wc_solve_bicgstab.argtypes = [_vp, _vp, _vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]
+_L.wc_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                              ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]
+_L.wc_action_force.argtypes = [_vp, _vp, _dp, _vp, ctypes.POINTER(SolveParams)]
+_L.wc_last_error.argtypes = [_vp]
+_L.wc_last_error.restype = ctypes.c_char_p
+for _n in EXPORTED:
+    if _n != "wc_last_error":
+        getattr(_L, _n).restype = ctypes.c_int
+
+
+class WCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = _L.wc_last_error(handle)
+        raise WCError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Data pointer of a C-contiguous complex128 torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.complex128 or not a.is_contiguous():
+            raise ValueError("expected a contiguous complex128 tensor")
+        return a.data_ptr()
+    import numpy as np
+    if a.dtype != np.complex128 or not a.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous complex128 array")
+    return a.ctypes.data
+
+
+def _nbytes(a):
+    return a.numel() * 16 if hasattr(a, "numel") else a.size * 16
+
+
+def ras_params(block=(4, 4, 4, 4), overlap=1, mr_iters=4) -> RasParams:
+    return RasParams((ctypes.c_int * 4)(*block), int(overlap), int(mr_iters))
+
+
+def solve_params(tol=1e-10, max_iter=10000, max_restarts=5, precond=PRECOND_NONE, inner_prec=F32,
+                 block=(4, 4, 4, 4), overlap=1, mr_iters=4) -> SolveParams:
+    return SolveParams(float(tol), int(max_iter), int(max_restarts), int(precond), int(inner_prec),
+                       ras_params(block, overlap, mr_iters))
+
+
+class Field:
+    """A colour-spinor field owned by the library (FP64, FP32 or FP16+scale)."""
+
+    def __init__(self, lattice: "Lattice", prec: int = F64):
+        self.lattice = lattice
+        self.prec = prec
+        h = _vp()
+        _check(_L.wc_field_create(lattice.handle, int(prec), ctypes.byref(h)), lattice.handle)
+        self.handle = h
+
+    def _size_ok(self, a):
+        if _nbytes(a) != self.lattice.volume * 12 * 16:
+            raise ValueError(f"spinor buffer must hold {self.lattice.volume}*12 complex128")
+
+    def load(self, psi):
+        """Import canonical complex128 psi[V,4,3] (device or host)."""
+        self._size_ok(psi)
+        _check(_L.wc_field_import(self.handle, _vp(_ptr(psi))), self.lattice.handle)
+        return self
+
+    def store(self, out):
+        """Export into canonical complex128 out[V,4,3] (device or host)."""
+        self._size_ok(out)
+        _check(_L.wc_field_export(self.handle, _vp(_ptr(out))), self.lattice.handle)
+        return out
+
+    def copy_from(self, src: "Field", scale: float = 1.0):
+        _check(_L.wc_field_copy(self.handle, src.handle, float(scale)), self.lattice.handle)
+        return self
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _L.wc_field_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Lattice:
+    """A 4-D lattice with its gauge field and clover term on the GPU."""
+
+    def __init__(self, dims, t_bc: int = -1, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.volume = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
+        s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        h = _vp()
+        _check(_L.wc_create_lattice((ctypes.c_int * 4)(*self.dims), int(t_bc), _vp(s), ctypes.byref(h)))
+        self.handle = h
+        self.t_bc = t_bc
+
+    def set_stream(self, stream):
+        s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        _check(_L.wc_set_stream(self.handle, _vp(s)), self.handle)
+
+    def load_gauge(self, U):
+        if _nbytes(U) != self.volume * 36 * 16:
+            raise ValueError("gauge buffer must hold V*4*3*3 complex128")
+        _check(_L.wc_load_gauge(self.handle, _vp(_ptr(U))), self.handle)
+        return self
+
+    def load_clover(self, csw: float, kappa: float):
+        _check(_L.wc_load_clover(self.handle, float(csw), float(kappa)), self.handle)
+        self.csw, self.kappa = float(csw), float(kappa)
+        return self
+
+    def field(self, prec: int = F64) -> Field:
+        return Field(self, prec)
+
+    def apply_M(self, out: Field, inp: Field):
+        _check(_L.wc_apply_M(self.handle, out.handle, inp.handle), self.handle)
+
+    def apply_Mdag(self, out: Field, inp: Field):
+        _check(_L.wc_apply_Mdag(self.handle, out.handle, inp.handle), self.handle)
+
+    def apply_hop(self, out: Field, inp: Field):
+        _check(_L.wc_apply_hop(self.handle, out.handle, inp.handle), self.handle)
+
+    def dot(self, a: Field, b: Field) -> complex:
+        r = (ctypes.c_double * 2)()
+        _check(_L.wc_dot(self.handle, a.handle, b.handle, r), self.handle)
+        return complex(r[0], r[1])
+
+    def norm2(self, a: Field) -> float:
+        r = ctypes.c_double()
+        _check(_L.wc_norm2(self.handle, a.handle, ctypes.byref(r)), self.handle)
+        return r.value
+
+    def axpy_norm(self, a: complex, x: Field, y: Field) -> float:
+        c = (ctypes.c_double * 2)(a.real, a.imag)
+        r = ctypes.c_double()
+        _check(_L.wc_axpy_norm(self.handle, c, x.handle, y.handle, ctypes.byref(r)), self.handle)
+        return r.value
+
+    def ras(self, out: Field, inp: Field, block=(4, 4, 4, 4), overlap=1, mr_iters=4):
+        p = ras_params(block, overlap, mr_iters)
+        _check(_L.wc_ras_precond(self.handle, out.handle, inp.handle, ctypes.byref(p)), self.handle)
+
+    def solve(self, x: Field, b: Field, params: SolveParams | None = None, check=True, **kw) -> SolveInfo:
+        p = params if params is not None else solve_params(**kw)
+        info = SolveInfo()
+        st = _L.wc_solve_bicgstab(self.handle, x.handle, b.handle, ctypes.byref(p), ctypes.byref(info))
+        if check:
+            _check(st, self.handle)
+        return info
+
+    def action_force(self, phi: Field, force_out, params: SolveParams | None = None, **kw) -> float:
+        p = params if params is not None else solve_params(**kw)
+        if _nbytes(force_out) != self.volume * 36 * 16:
+            raise ValueError("force buffer must hold V*4*3*3 complex128")
+        S = ctypes.c_double()
+        _check(_L.wc_action_force(self.handle, phi.handle, ctypes.byref(S), _vp(_ptr(force_out)),
+                                  ctypes.byref(p)), self.handle)
+        return S.value
+
+    def last_error(self) -> str:
+        return _L.wc_last_error(self.handle).decode()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _L.wc_destroy_lattice(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(lattices, xs, bs, params: SolveParams | None = None, **kw):
+    """Solve M_i x_i = b_i for all i in one batched call; returns SolveInfos."""
+    n = len(xs)
+    p = params if params is not None else solve_params(**kw)
+    L = (_vp * n)(*[lat.handle for lat in lattices])
+    X = (_vp * n)(*[x.handle for x in xs])
+    B = (_vp * n)(*[b.handle for b in bs])
+    infos = (SolveInfo * n)()
+    st = _L.wc_solve_batch(n, L, X, B, ctypes.byref(p), infos)
+    if st != 0:
+        _check(st, None)
+    return list(infos)

@@ -1,0 +1,438 @@
+// Fused BLAS-1 with FP64 accumulation: inner products, norms, axpy, and the
+// per-iteration vector updates of BiCGStab, each one pass over its fields.
+//
+// Reductions are deterministic: every block reduces its grid-stride share
+// (warp shuffles, then one warp over the block's warps), writes one partial,
+// and the last block to finish (completion ticket) adds the partials in
+// block order and runs the scalar update of the solver in one thread.  The
+// ticket resets itself, so no memset is needed between launches.
+#include <math.h>
+
+#include "wc_internal.cuh"
+#include "wc_solver_kernels.cuh"
+
+namespace wc {
+
+namespace {
+
+constexpr int kRedBlock = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace
+
+// Reduce v[0..N) over the grid.  Returns true in thread 0 of the last block,
+// after out[0..N) holds the grid totals (summed in a fixed order).
+template <int N>
+__device__ __forceinline__ bool grid_reduce(double (&v)[N], const ReduceScratch &rs, double *out)
+{
+    __shared__ double sm[32][N];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = warp_sum(v[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) sm[wid][i] = v[i];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = lane < nw ? sm[lane][i] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) rs.partials[(size_t)blockIdx.x * 8 + i] = s;
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(rs.ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = 0.0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(rs.partials + (size_t)b * 8 + i);
+            s = warp_sum(s);
+            if (lane == 0) out[i] = s;
+        }
+        if (lane == 0) *rs.ticket = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
+int reduce_grid(const ReduceScratch &rs, long long n)
+{
+    long long b = (n + kRedBlock - 1) / kRedBlock;
+    if (b > rs.max_blocks) b = rs.max_blocks;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+namespace {
+
+// ------------------------------------------------------------------------
+// generic (any precision, per site) dot / norm / axpy for the C ABI
+// ------------------------------------------------------------------------
+
+template <class PA, class PB>
+__global__ void __launch_bounds__(kRedBlock) k_dot(int V, const void *a, const float *an, const void *b,
+                                                   const float *bn, ReduceScratch rs)
+{
+    double v[2] = {0.0, 0.0};
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        cx<typename PA::real> sa[12];
+        cx<typename PB::real> sb[12];
+        PA::load_spinor(a, an, V, x, sa);
+        PB::load_spinor(b, bn, V, x, sb);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double ar = sa[k].re, ai = sa[k].im, br = sb[k].re, bi = sb[k].im;
+            v[0] += ar * br + ai * bi;
+            v[1] += ar * bi - ai * br;
+        }
+    }
+    grid_reduce<2>(v, rs, rs.result);
+}
+
+template <class P>
+__global__ void __launch_bounds__(kRedBlock) k_axpy_norm(int V, double ar, double ai, const void *x_,
+                                                         const float *xn, void *y_, float *yn, ReduceScratch rs)
+{
+    double v[1] = {0.0};
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        using R = typename P::real;
+        cx<R> sx[12], sy[12];
+        P::load_spinor(x_, xn, V, x, sx);
+        P::load_spinor(y_, yn, V, x, sy);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double re = (double)sy[k].re + ar * sx[k].re - ai * sx[k].im;
+            const double im = (double)sy[k].im + ar * sx[k].im + ai * sx[k].re;
+            sy[k] = mkc((R)re, (R)im);
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[0] += (double)sy[k].re * sy[k].re + (double)sy[k].im * sy[k].im;
+        P::store_spinor(y_, yn, V, x, sy);
+    }
+    grid_reduce<1>(v, rs, rs.result);
+}
+
+template <class PA>
+cudaError_t launch_dot_a(wc_lattice lat, wc_field a, wc_field b)
+{
+    const int V = lat->g.V;
+    const int grid = reduce_grid(lat->red, V);
+    switch (b->prec) {
+    case WC_F64:
+        k_dot<PA, P64><<<grid, kRedBlock, 0, lat->stream>>>(V, a->data, a->nrm, b->data, b->nrm, lat->red);
+        break;
+    case WC_F32:
+        k_dot<PA, P32><<<grid, kRedBlock, 0, lat->stream>>>(V, a->data, a->nrm, b->data, b->nrm, lat->red);
+        break;
+    default:
+        k_dot<PA, P16><<<grid, kRedBlock, 0, lat->stream>>>(V, a->data, a->nrm, b->data, b->nrm, lat->red);
+    }
+    return cudaGetLastError();
+}
+
+wc_status fetch_result(wc_lattice lat, int n, double *out)
+{
+    wc_status st = check_cuda(lat,
+                              cudaMemcpyAsync(lat->red.host_result, lat->red.result, sizeof(double) * n,
+                                              cudaMemcpyDeviceToHost, lat->stream),
+                              "cudaMemcpyAsync(reduce)");
+    if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync(reduce)");
+    if (st == WC_OK)
+        for (int i = 0; i < n; ++i) out[i] = lat->red.host_result[i];
+    return st;
+}
+
+}  // namespace
+
+wc_status reduce_dot(wc_lattice lat, wc_field a, wc_field b, double out[2])
+{
+    cudaError_t e;
+    switch (a->prec) {
+    case WC_F64: e = launch_dot_a<P64>(lat, a, b); break;
+    case WC_F32: e = launch_dot_a<P32>(lat, a, b); break;
+    default: e = launch_dot_a<P16>(lat, a, b);
+    }
+    wc_status st = check_cuda(lat, e, "dot");
+    if (st != WC_OK) return st;
+    return fetch_result(lat, 2, out);
+}
+
+wc_status reduce_norm2(wc_lattice lat, wc_field a, double *out)
+{
+    double d[2];
+    wc_status st = reduce_dot(lat, a, a, d);
+    if (st == WC_OK) *out = d[0];
+    return st;
+}
+
+wc_status axpy_norm(wc_lattice lat, const double a[2], wc_field x, wc_field y, double *norm2)
+{
+    const int V = lat->g.V;
+    const int grid = reduce_grid(lat->red, V);
+    switch (y->prec) {
+    case WC_F64:
+        k_axpy_norm<P64><<<grid, kRedBlock, 0, lat->stream>>>(V, a[0], a[1], x->data, x->nrm, y->data, y->nrm,
+                                                              lat->red);
+        break;
+    case WC_F32:
+        k_axpy_norm<P32><<<grid, kRedBlock, 0, lat->stream>>>(V, a[0], a[1], x->data, x->nrm, y->data, y->nrm,
+                                                              lat->red);
+        break;
+    default:
+        k_axpy_norm<P16><<<grid, kRedBlock, 0, lat->stream>>>(V, a[0], a[1], x->data, x->nrm, y->data, y->nrm,
+                                                              lat->red);
+    }
+    wc_status st = check_launch(lat, "axpy_norm");
+    if (st != WC_OK) return st;
+    double n2 = 0.0;
+    st = fetch_result(lat, 1, &n2);
+    if (st == WC_OK && norm2) *norm2 = n2;
+    return st;
+}
+
+// ------------------------------------------------------------------------
+// BiCGStab vector updates on FP64 fields (flat arrays of n = 12 V complex)
+// ------------------------------------------------------------------------
+
+namespace {
+
+__device__ __forceinline__ cx<double> ld(const double2 *p, long long i)
+{
+    const double2 v = p[i];
+    return {v.x, v.y};
+}
+__device__ __forceinline__ void st(double2 *p, long long i, cx<double> a) { p[i] = make_double2(a.re, a.im); }
+__device__ __forceinline__ cx<double> c_of(double2 a) { return {a.x, a.y}; }
+__device__ __forceinline__ double2 d2_of(cx<double> a) { return make_double2(a.re, a.im); }
+__device__ __forceinline__ cx<double> cdiv(cx<double> a, cx<double> b)
+{
+    const double d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+__device__ __forceinline__ bool finite2(cx<double> a) { return isfinite(a.re) && isfinite(a.im); }
+
+// r = b - r (r holds M x on entry), rhat = r, p = v = 0;  rr = |r|^2
+__global__ void __launch_bounds__(kRedBlock) k_bicg_init(long long n, const double2 *b, double2 *r, double2 *rhat,
+                                                         double2 *p, double2 *v, ReduceScratch rs,
+                                                         SolverScalars *sc)
+{
+    double acc[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cx<double> ri = ld(b, i) - ld(r, i);
+        st(r, i, ri);
+        st(rhat, i, ri);
+        p[i] = make_double2(0.0, 0.0);
+        v[i] = make_double2(0.0, 0.0);
+        acc[0] += ri.re * ri.re + ri.im * ri.im;
+    }
+    if (grid_reduce<1>(acc, rs, rs.result)) {
+        const double rr = rs.result[0];
+        sc->rr = rr;
+        sc->rho = make_double2(rr, 0.0);   // <rhat, r> with rhat = r
+        sc->rho0 = make_double2(1.0, 0.0);
+        sc->alpha = make_double2(1.0, 0.0);
+        sc->omega = make_double2(1.0, 0.0);
+        sc->beta = make_double2(rr, 0.0);  // (rho/rho0)(alpha/omega)
+        sc->flags = isfinite(rr) ? 0 : FLAG_NAN;
+        if (rr == 0.0) sc->flags |= FLAG_BREAKDOWN;
+    }
+}
+
+// p = r + beta (p - omega v);  pp = |p|^2
+__global__ void __launch_bounds__(kRedBlock) k_bicg_p(long long n, const double2 *r, const double2 *v, double2 *p,
+                                                      ReduceScratch rs, SolverScalars *sc)
+{
+    const cx<double> beta = c_of(sc->beta), omega = c_of(sc->omega);
+    double acc[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cx<double> pi = ld(r, i) + beta * (ld(p, i) - omega * ld(v, i));
+        st(p, i, pi);
+        acc[0] += pi.re * pi.re + pi.im * pi.im;
+    }
+    if (grid_reduce<1>(acc, rs, rs.result)) {
+        sc->pp = rs.result[0];
+        if (!isfinite(sc->pp)) sc->flags |= FLAG_NAN;
+    }
+}
+
+// alpha = rho / <rhat, v>
+__global__ void __launch_bounds__(kRedBlock) k_bicg_alpha(long long n, const double2 *rhat, const double2 *v,
+                                                          ReduceScratch rs, SolverScalars *sc)
+{
+    double acc[2] = {0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cx<double> a = ld(rhat, i), b = ld(v, i);
+        acc[0] += a.re * b.re + a.im * b.im;
+        acc[1] += a.re * b.im - a.im * b.re;
+    }
+    if (grid_reduce<2>(acc, rs, rs.result)) {
+        const cx<double> rv = mkc(rs.result[0], rs.result[1]);
+        if (!finite2(rv)) sc->flags |= FLAG_NAN;
+        if (rv.re == 0.0 && rv.im == 0.0) {
+            sc->flags |= FLAG_BREAKDOWN;
+            sc->alpha = make_double2(0.0, 0.0);
+        } else {
+            sc->alpha = d2_of(cdiv(c_of(sc->rho), rv));
+        }
+    }
+}
+
+// s = r - alpha v;  ss = |s|^2
+__global__ void __launch_bounds__(kRedBlock) k_bicg_s(long long n, const double2 *r, const double2 *v, double2 *s,
+                                                      ReduceScratch rs, SolverScalars *sc)
+{
+    const cx<double> alpha = c_of(sc->alpha);
+    double acc[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cx<double> si = ld(r, i) - alpha * ld(v, i);
+        st(s, i, si);
+        acc[0] += si.re * si.re + si.im * si.im;
+    }
+    if (grid_reduce<1>(acc, rs, rs.result)) {
+        sc->ss = rs.result[0];
+        if (!isfinite(sc->ss)) sc->flags |= FLAG_NAN;
+    }
+}
+
+// omega = <t, s> / <t, t>
+__global__ void __launch_bounds__(kRedBlock) k_bicg_omega(long long n, const double2 *t, const double2 *s,
+                                                          ReduceScratch rs, SolverScalars *sc)
+{
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cx<double> a = ld(t, i), b = ld(s, i);
+        acc[0] += a.re * b.re + a.im * b.im;
+        acc[1] += a.re * b.im - a.im * b.re;
+        acc[2] += a.re * a.re + a.im * a.im;
+    }
+    if (grid_reduce<3>(acc, rs, rs.result)) {
+        const double tt = rs.result[2];
+        sc->tt = tt;
+        if (!isfinite(tt) || !isfinite(rs.result[0]) || !isfinite(rs.result[1])) sc->flags |= FLAG_NAN;
+        if (tt > 0.0)
+            sc->omega = make_double2(rs.result[0] / tt, rs.result[1] / tt);
+        else
+            sc->omega = make_double2(0.0, 0.0);
+    }
+}
+
+// x += alpha phat + omega shat;  r = s - omega t;  rho' = <rhat, r>, rr = |r|^2,
+// beta = (rho'/rho)(alpha/omega), rho0 = rho, rho = rho'
+__global__ void __launch_bounds__(kRedBlock) k_bicg_xr(long long n, double2 *x, const double2 *phat,
+                                                       const double2 *shat, const double2 *s, const double2 *t,
+                                                       double2 *r, const double2 *rhat, ReduceScratch rs,
+                                                       SolverScalars *sc)
+{
+    const cx<double> alpha = c_of(sc->alpha), omega = c_of(sc->omega);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        cx<double> xi = ld(x, i);
+        xi = cfma(alpha, ld(phat, i), xi);
+        xi = cfma(omega, ld(shat, i), xi);
+        st(x, i, xi);
+        const cx<double> ri = ld(s, i) - omega * ld(t, i);
+        st(r, i, ri);
+        const cx<double> h = ld(rhat, i);
+        acc[0] += h.re * ri.re + h.im * ri.im;
+        acc[1] += h.re * ri.im - h.im * ri.re;
+        acc[2] += ri.re * ri.re + ri.im * ri.im;
+    }
+    if (grid_reduce<3>(acc, rs, rs.result)) {
+        const cx<double> rho_new = mkc(rs.result[0], rs.result[1]);
+        const cx<double> rho = c_of(sc->rho);
+        sc->rr = rs.result[2];
+        if (!isfinite(sc->rr) || !finite2(rho_new)) sc->flags |= FLAG_NAN;
+        if ((omega.re == 0.0 && omega.im == 0.0) || (rho.re == 0.0 && rho.im == 0.0)) {
+            sc->flags |= FLAG_BREAKDOWN;
+        } else {
+            sc->beta = d2_of(cdiv(rho_new, rho) * cdiv(alpha, omega));
+        }
+        if (rho_new.re == 0.0 && rho_new.im == 0.0 && sc->rr > 0.0) sc->flags |= FLAG_BREAKDOWN;
+        sc->rho0 = sc->rho;
+        sc->rho = d2_of(rho_new);
+    }
+}
+
+// r = b - r (r holds M x);  rr = |r|^2  (true residual)
+__global__ void __launch_bounds__(kRedBlock) k_residual(long long n, const double2 *b, double2 *r,
+                                                        ReduceScratch rs, SolverScalars *sc)
+{
+    double acc[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cx<double> ri = ld(b, i) - ld(r, i);
+        st(r, i, ri);
+        acc[0] += ri.re * ri.re + ri.im * ri.im;
+    }
+    if (grid_reduce<1>(acc, rs, rs.result)) sc->rr = rs.result[0];
+}
+
+}  // namespace
+
+#define WC_GRID(n) reduce_grid(lat->red, (n)), kRedBlock, 0, lat->stream
+
+cudaError_t bicg_init(wc_lattice lat, const double2 *b, double2 *r, double2 *rhat, double2 *p, double2 *v)
+{
+    const long long n = 12LL * lat->g.V;
+    k_bicg_init<<<WC_GRID(n)>>>(n, b, r, rhat, p, v, lat->red, lat->scal);
+    return cudaGetLastError();
+}
+cudaError_t bicg_p(wc_lattice lat, const double2 *r, const double2 *v, double2 *p)
+{
+    const long long n = 12LL * lat->g.V;
+    k_bicg_p<<<WC_GRID(n)>>>(n, r, v, p, lat->red, lat->scal);
+    return cudaGetLastError();
+}
+cudaError_t bicg_alpha(wc_lattice lat, const double2 *rhat, const double2 *v)
+{
+    const long long n = 12LL * lat->g.V;
+    k_bicg_alpha<<<WC_GRID(n)>>>(n, rhat, v, lat->red, lat->scal);
+    return cudaGetLastError();
+}
+cudaError_t bicg_s(wc_lattice lat, const double2 *r, const double2 *v, double2 *s)
+{
+    const long long n = 12LL * lat->g.V;
+    k_bicg_s<<<WC_GRID(n)>>>(n, r, v, s, lat->red, lat->scal);
+    return cudaGetLastError();
+}
+cudaError_t bicg_omega(wc_lattice lat, const double2 *t, const double2 *s)
+{
+    const long long n = 12LL * lat->g.V;
+    k_bicg_omega<<<WC_GRID(n)>>>(n, t, s, lat->red, lat->scal);
+    return cudaGetLastError();
+}
+cudaError_t bicg_xr(wc_lattice lat, double2 *x, const double2 *phat, const double2 *shat, const double2 *s,
+                    const double2 *t, double2 *r, const double2 *rhat)
+{
+    const long long n = 12LL * lat->g.V;
+    k_bicg_xr<<<WC_GRID(n)>>>(n, x, phat, shat, s, t, r, rhat, lat->red, lat->scal);
+    return cudaGetLastError();
+}
+cudaError_t residual(wc_lattice lat, const double2 *b, double2 *r)
+{
+    const long long n = 12LL * lat->g.V;
+    k_residual<<<WC_GRID(n)>>>(n, b, r, lat->red, lat->scal);
+    return cudaGetLastError();
+}
+
+}  // namespace wc

@@ -1,0 +1,57 @@
+"""The C ABI library builds, loads, and exports every entry point that
+include/*.h declares.  CPU only: no kernel is launched."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w[\w\s\*]*?\b(wc_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_06556_gb300 as wc
+    return ctypes.CDLL(wc.LIB_PATH)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["wc_create_lattice", "wc_load_gauge", "wc_load_clover", "wc_apply_M",
+                     "wc_apply_Mdag", "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch",
+                     "wc_action_force", "wc_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_match_header():
+    import paper_1612_06556_gb300 as wc
+    assert sorted(wc.EXPORTED) == sorted(n for n in declared_functions() if n in wc.EXPORTED)
+    assert set(declared_functions()) <= set(wc.EXPORTED)
+
+
+def test_argument_errors_are_reported_without_a_gpu(lib):
+    import paper_1612_06556_gb300 as wc
+    with pytest.raises(wc.WCError) as e:
+        wc.Lattice((1, 4, 4, 4))
+    assert e.value.status == 1 and "extent" in str(e.value)
+    with pytest.raises(wc.WCError) as e:
+        wc.Lattice((4, 4, 4, 4), t_bc=3)
+    assert e.value.status == 1

@@ -1,0 +1,154 @@
+"""GPU RAS preconditioner and BiCGStab solvers against the CPU oracle.
+
+RAS (FP32 arithmetic) is compared element by element with the oracle's FP64
+RAS.  Solves are compared through what is unique: the solution of M x = b
+(M is nonsingular at these parameters), with the residual of the GPU
+solution recomputed by the oracle's own M, and the oracle's BiCGStab
+solution as a second reference.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import gpu_apply, make_lattice, rel_err, wc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dims,block,delta,k", [
+    ((8, 8, 8, 8), (4, 4, 4, 4), 1, 4),
+    ((8, 12, 8, 16), (4, 4, 4, 4), 1, 4),
+    ((6, 8, 6, 6), (2, 2, 2, 2), 1, 4),
+    ((8, 8, 8, 8), (4, 4, 4, 4), 0, 6),
+    ((12, 8, 8, 8), (3, 2, 2, 2), 1, 3),
+])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_ras_matches_oracle(dims, block, delta, k, prec):
+    kappa, csw, tbc = 0.125, 1.0, -1
+    U = synth.haar_links(dims, 7 + sum(dims))
+    v = synth.z2_source(dims, 8)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    op = oracle.Operator(dims, U, csw, kappa, tbc)
+    ref = op.ras(v, block=block, delta=delta, k=k)
+    fi, fo = lat.field(prec).load(v), lat.field(prec)
+    lat.ras(fo, fi, block=block, overlap=delta, mr_iters=k)
+    out = fo.store(np.zeros_like(v))
+    tol = 2e-5 if prec == 1 else 1e-2
+    assert rel_err(out, ref) <= tol
+    assert np.max(np.abs(out - ref)) <= tol * np.max(np.abs(ref))
+
+
+def test_ras_degenerate_cases():
+    dims = (8, 8, 8, 8)
+    U = synth.haar_links(dims, 1)
+    lat = make_lattice(dims, U, 1.0, 0.12, -1)
+    zero = np.zeros((synth.volume(dims), 4, 3), complex)
+    fo = lat.field(1)
+    lat.ras(fo, lat.field(1).load(zero))
+    assert np.count_nonzero(fo.store(np.zeros_like(zero))) == 0
+    v = synth.gaussian_source(dims, 2)
+    fo2 = lat.field(1).load(v)
+    lat.ras(fo2, lat.field(1).load(v), mr_iters=0)
+    assert np.count_nonzero(fo2.store(np.zeros_like(zero))) == 0
+    w = wc()
+    for bad in [dict(block=(3, 4, 4, 4)), dict(block=(4, 4, 4, 4), overlap=2), dict(block=(8, 4, 4, 4)),
+                dict(block=(4, 4, 4, 4), overlap=3)]:
+        with pytest.raises(w.WCError) as e:
+            lat.ras(lat.field(1), lat.field(1), **bad)
+        assert e.value.status == 1
+
+
+def test_fp64_bicgstab_point_source_8x8x8x8():
+    """Plain FP64 BiCGStab at the 8^3x8 point-source workload to 1e-12."""
+    w = wc()
+    dims, U, src, csw, kappa, tbc = synth.config_inputs(1)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    x, b = lat.field(0), lat.field(0).load(src)
+    info = lat.solve(x, b, tol=1e-12)
+    assert info.status == 0 and info.true_rel_resid <= 1e-12
+    sol = x.store(np.zeros_like(src))
+    r = src - oracle.apply_M(dims, tbc, kappa, csw, U, sol)
+    assert np.linalg.norm(r) <= 1.5e-12 * np.linalg.norm(src)
+    op = oracle.Operator(dims, U, csw, kappa, tbc)
+    ref = oracle.bicgstab(op.M, src, tol=1e-13)
+    assert rel_err(sol, ref.x) <= 1e-9
+
+
+@pytest.mark.parametrize("inner", [1, 2])
+def test_mixed_ras_bicgstab(inner):
+    dims, kappa, csw, tbc = (8, 8, 8, 16), 0.125, 1.0, -1
+    U = synth.haar_links(dims, 21)
+    src = synth.z2_source(dims, 22)
+    w = wc()
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    x, b = lat.field(0), lat.field(0).load(src)
+    info = lat.solve(x, b, tol=1e-10, precond=w.PRECOND_RAS, inner_prec=inner)
+    assert info.status == 0 and info.true_rel_resid <= 1e-10
+    sol = x.store(np.zeros_like(src))
+    r = src - oracle.apply_M(dims, tbc, kappa, csw, U, sol)
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+    # the preconditioner must help: fewer iterations than the plain solve
+    x2 = lat.field(0)
+    info2 = lat.solve(x2, b, tol=1e-10)
+    assert info.iters < info2.iters
+
+
+def test_solver_initial_guess_and_resume():
+    dims, kappa, csw, tbc = (4, 4, 4, 8), 0.12, 1.0, -1
+    U = synth.exp_links(dims, 0.3, 31)
+    src = synth.gaussian_source(dims, 32)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    x, b = lat.field(0), lat.field(0).load(src)
+    w = wc()
+    info = lat.solve(x, b, tol=1e-6, check=False)
+    assert info.status == 0
+    info2 = lat.solve(x, b, tol=1e-12)       # resume from the previous solution
+    assert info2.status == 0 and info2.true_rel_resid <= 1e-12
+    info3 = lat.solve(x, b, tol=1e-12)       # already converged: no iteration
+    assert info3.iters == 0 and info3.status == 0
+
+
+def test_solver_error_paths():
+    w = wc()
+    dims = (4, 4, 4, 8)
+    U = synth.exp_links(dims, 0.3, 41)
+    lat = make_lattice(dims, U, 1.0, 0.12, -1)
+    src = synth.gaussian_source(dims, 42)
+    x, b = lat.field(0), lat.field(0).load(src)
+    info = lat.solve(x, b, tol=1e-12, max_iter=1, max_restarts=0, check=False)
+    assert info.status == 4 and info.iters == 1
+    bad = src.copy()
+    bad[3, 1, 2] = np.nan
+    info = lat.solve(lat.field(0), lat.field(0).load(bad), tol=1e-10, check=False)
+    assert info.status == 6
+    with pytest.raises(w.WCError) as e:
+        lat.solve(lat.field(0), lat.field(1), tol=1e-10)
+    assert e.value.status == 1
+    with pytest.raises(w.WCError) as e:
+        lat.solve(x, b, tol=1e-10, precond=w.PRECOND_RAS, block=(3, 4, 4, 4))
+    assert e.value.status == 1
+    zero = lat.field(0)
+    info = lat.solve(x, zero, tol=1e-10)
+    assert info.status == 0 and np.count_nonzero(x.store(np.zeros_like(src))) == 0
+
+
+def test_batch_solve_uneven_lattices():
+    w = wc()
+    lats, xs, bs, srcs, ops = [], [], [], [], []
+    for i, dims in enumerate([(6, 6, 6, 8), (8, 8, 8, 8), (8, 6, 8, 12)]):
+        U = synth.exp_links(dims, 0.3, 1100 + 10 * i)
+        lat = make_lattice(dims, U, 1.0, 0.124, -1)
+        for spin in range(2):
+            src = synth.point_source(dims, spin=spin, colour=i % 3)
+            lats.append(lat)
+            xs.append(lat.field(0))
+            bs.append(lat.field(0).load(src))
+            srcs.append(src)
+            ops.append((dims, U))
+    infos = w.solve_batch(lats, xs, bs, tol=1e-10, precond=w.PRECOND_RAS, inner_prec=1, block=(2, 2, 2, 2))
+    for info, x, src, (dims, U) in zip(infos, xs, srcs, ops):
+        assert info.status == 0
+        sol = x.store(np.zeros_like(src))
+        r = src - oracle.apply_M(dims, -1, 0.124, 1.0, U, sol)
+        assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
