@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libwc.so")
 if not os.path.exists(LIB_PATH):
     raise ImportError(
         f"{LIB_PATH} is missing: build the CUDA library first "
-        "(python -m paper_1612_06556_gb300.build); there is no CPU fallback")
+        "(python paper_1612_06556_gb300/build.py); there is no CPU fallback")
 
 _lib = ctypes.CDLL(LIB_PATH)
 
