@@ -14,11 +14,16 @@
 // r -= alpha q (alpha = 0 when q = 0).  Only the core of x is written.
 //
 // GB300 mapping: the extended block's residual r lives in shared memory
-// (FP32, component-major [12][ne] so a warp's accesses are contiguous), the
-// core of x in shared memory too, and each thread keeps q of its SPT sites
-// in registers across the block-wide FP64 reduction of <q, r> and <q, q>.
-// Links and clover are read from global memory (L2-resident across the k
-// sweeps of a block).  Arithmetic is FP32 for FP32 and FP16 storage.
+// (FP32, component-major [12][ne] so a warp's accesses are contiguous), as
+// does the core of x.  Each thread owns two sites; the q of its first site
+// is parked in shared memory and the q of its second stays in registers
+// across the block-wide reduction of <q, r> and <q, q> (4^4 blocks with
+// overlap 1: 1296 sites, 672 threads, 211 KB of shared memory, one CTA per
+// SM).  Per-thread partial sums are FP32 (two sites); only the sums over
+// lanes and warps are FP64, which keeps the FP64 pipe -- 1/64 of the FP32
+// rate on GB300 -- out of the inner loop.  Links and clover are read from
+// global memory (L2-resident across the k sweeps of a block).  Arithmetic is
+// FP32 for FP32 and FP16 storage.
 #include "wc_internal.cuh"
 #include "wc_stencil.cuh"
 
@@ -26,8 +31,8 @@ namespace wc {
 
 namespace {
 
-constexpr int kRasSPT = 3;         // sites per thread
-constexpr int kRasMaxThreads = 448;
+constexpr int kRasSPT = 2;         // sites per thread
+constexpr int kRasMaxThreads = 672;
 
 struct RasGeom {
     int e[4];       // extended extents
@@ -40,8 +45,11 @@ struct RasGeom {
     int k;          // MR iterations
 };
 
-__device__ __forceinline__ void block_sum3(double v[3], double *sm /*[32*3]*/, double out[3])
+// Block sum of three per-thread FP32 partials, lanes and warps in FP64, the
+// warp partials added in a fixed order so every thread gets the same result.
+__device__ __forceinline__ void block_sum3(const float vf[3], double *sm /*[32*3]*/, double out[3])
 {
+    double v[3] = {vf[0], vf[1], vf[2]};
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -51,12 +59,11 @@ __device__ __forceinline__ void block_sum3(double v[3], double *sm /*[32*3]*/, d
 #pragma unroll
         for (int i = 0; i < 3; ++i) sm[wid * 3 + i] = v[i];
     __syncthreads();
-    // every thread sums the warp partials in the same order: same result
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += sm[w * 3 + i];
-        out[i] = s;
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sm[w * 3 + i];
+        out[i] = t;
     }
 }
 
@@ -72,13 +79,11 @@ __device__ __forceinline__ void ras_hops(const Geom &g, const RasGeom &rg, const
     if (lm + 1 < rg.e[MU]) {
         const int lf = l + stl;
         const float coef = (MU == 3 && (wbits & (16u << 3))) ? mk * (float)g.tbc : mk;
-        cx<float> p[12], h[6], u[6], r2[3], w[6];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
+        cx<float> h[6], u[6], r2[3], w[6];
+        project_from<MU, SF, float>([&](int k) {
             const float2 v = r[k * rg.ne + lf];
-            p[k] = mkc(v.x, v.y);
-        }
-        project<MU, SF>(p, h);
+            return mkc(v.x, v.y);
+        }, h);
         P::load_link(U, g.V, MU, site, u);
         reconstruct_row2(u, r2);
         su3_mul(u, r2, h, coef, w);
@@ -88,13 +93,11 @@ __device__ __forceinline__ void ras_hops(const Geom &g, const RasGeom &rg, const
         const int lb = l - stl;
         const int sb = (wbits & (1u << MU)) ? site + (g.L[MU] - 1) * g.stride[MU] : site - g.stride[MU];
         const float coef = (MU == 3 && (wbits & (1u << 3))) ? mk * (float)g.tbc : mk;
-        cx<float> p[12], h[6], u[6], r2[3], w[6];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
+        cx<float> h[6], u[6], r2[3], w[6];
+        project_from<MU, -SF, float>([&](int k) {
             const float2 v = r[k * rg.ne + lb];
-            p[k] = mkc(v.x, v.y);
-        }
-        project<MU, -SF>(p, h);
+            return mkc(v.x, v.y);
+        }, h);
         P::load_link(U, g.V, MU, sb, u);
         reconstruct_row2(u, r2);
         su3_adj_mul(u, r2, h, coef, w);
@@ -109,7 +112,8 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
 {
     extern __shared__ float4 smem_raw[];
     float2 *r = reinterpret_cast<float2 *>(smem_raw);               // [12][ne]
-    float2 *xc = r + 12 * rg.ne;                                     // [12][ncore]
+    float2 *qs = r + 12 * rg.ne;                                     // [12][blockDim.x]
+    float2 *xc = qs + 12 * blockDim.x;                               // [12][ncore]
     __shared__ double red[32 * 3];
 
     // block origin
@@ -170,36 +174,42 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
     __syncthreads();
 
     const float mk = -kappa;
+    const int nt = blockDim.x;
     for (int it = 0; it < rg.k; ++it) {
-        cx<float> q[kRasSPT][12];
-        double acc[3] = {0.0, 0.0, 0.0};
+        cx<float> q[12];   // q of this thread's last valid site
+        float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < kRasSPT; ++j) {
-            const int l = threadIdx.x + j * blockDim.x;
+            const int l = threadIdx.x + j * nt;
             if (gs[j] < 0) continue;
-            cx<float> rl[12];
+            if (j > 0 && gs[0] >= 0) {
+                // park the first site's q in shared memory
 #pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                const float2 v = r[k * rg.ne + l];
-                rl[k] = mkc(v.x, v.y);
+                for (int k = 0; k < 12; ++k) qs[k * nt + threadIdx.x] = make_float2(q[k].re, q[k].im);
             }
             // q = A r_l - kappa (hops inside the extended block)
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
+                cx<float> rl[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const float2 v = r[(6 * b + k) * rg.ne + l];
+                    rl[k] = mkc(v.x, v.y);
+                }
                 float cl[36];
                 P::load_clover(C, V, gs[j], b, cl);
-                clover_block_mul(cl, rl + 6 * b, q[j] + 6 * b);
+                clover_block_mul(cl, rl, q + 6 * b);
             }
-            ras_hops<P, 0, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q[j]);
-            ras_hops<P, 1, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q[j]);
-            ras_hops<P, 2, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q[j]);
-            ras_hops<P, 3, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q[j]);
+            ras_hops<P, 0, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q);
+            ras_hops<P, 1, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q);
+            ras_hops<P, 2, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q);
+            ras_hops<P, 3, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q);
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
-                const double qr = q[j][k].re, qi = q[j][k].im, rr = rl[k].re, ri = rl[k].im;
-                acc[0] += qr * rr + qi * ri;   // <q, r>
-                acc[1] += qr * ri - qi * rr;
-                acc[2] += qr * qr + qi * qi;   // <q, q>
+                const float2 v = r[k * rg.ne + l];
+                acc[0] = fmaf(q[k].re, v.x, fmaf(q[k].im, v.y, acc[0]));    // Re <q, r>
+                acc[1] = fmaf(q[k].re, v.y, fmaf(-q[k].im, v.x, acc[1]));   // Im <q, r>
+                acc[2] = fmaf(q[k].re, q[k].re, fmaf(q[k].im, q[k].im, acc[2]));
             }
         }
         double tot[3];
@@ -207,20 +217,29 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
         const float ar = tot[2] > 0.0 ? (float)(tot[0] / tot[2]) : 0.f;
         const float ai = tot[2] > 0.0 ? (float)(tot[1] / tot[2]) : 0.f;
         const cx<float> alpha = mkc(ar, ai);
+        // x += alpha r, r -= alpha q on this thread's sites
 #pragma unroll
         for (int j = 0; j < kRasSPT; ++j) {
-            const int l = threadIdx.x + j * blockDim.x;
+            const int l = threadIdx.x + j * nt;
             if (gs[j] < 0) continue;
+            const bool last = (j == kRasSPT - 1) || gs[kRasSPT - 1] < 0;
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
                 const float2 v = r[k * rg.ne + l];
                 const cx<float> rk = mkc(v.x, v.y);
+                cx<float> qk;
+                if (last) {
+                    qk = q[k];
+                } else {
+                    const float2 w = qs[k * nt + threadIdx.x];
+                    qk = mkc(w.x, w.y);
+                }
                 if (core[j] >= 0) {
                     float2 *xp = xc + k * rg.ncore + core[j];
                     const cx<float> xn = cfma(alpha, rk, mkc(xp->x, xp->y));
                     *xp = make_float2(xn.re, xn.im);
                 }
-                const cx<float> rn = rk - alpha * q[j][k];
+                const cx<float> rn = rk - alpha * qk;
                 r[k * rg.ne + l] = make_float2(rn.re, rn.im);
             }
         }
@@ -243,6 +262,8 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
 
 }  // namespace
 
+int ras_threads(const wc_ras_params &p);
+
 size_t ras_smem_bytes(const wc_ras_params &p)
 {
     size_t ne = 1, nc = 1;
@@ -250,7 +271,7 @@ size_t ras_smem_bytes(const wc_ras_params &p)
         ne *= (size_t)(p.block[m] + 2 * p.overlap);
         nc *= (size_t)p.block[m];
     }
-    return (ne + nc) * 12 * sizeof(float2);
+    return (ne + (size_t)ras_threads(p) + nc) * 12 * sizeof(float2);
 }
 
 int ras_threads(const wc_ras_params &p)
@@ -263,7 +284,7 @@ int ras_threads(const wc_ras_params &p)
 
 bool ras_fits(const wc_ras_params &p)
 {
-    return ras_threads(p) <= kRasMaxThreads && ras_smem_bytes(p) <= 220 * 1024;
+    return ras_threads(p) <= kRasMaxThreads && ras_smem_bytes(p) <= 226 * 1024;
 }
 
 template <class P, int SF>

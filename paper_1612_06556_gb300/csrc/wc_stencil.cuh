@@ -17,12 +17,14 @@
 
 namespace wc {
 
-template <int MU, int S, class R>
-__device__ __forceinline__ void project(const cx<R> p[12], cx<R> h[6])
+// Two-spinor h of (1 + S gamma_mu) psi, reading the four spin components of
+// one colour at a time through ld(k) (k = 3*spin + colour).
+template <int MU, int S, class R, class Load>
+__device__ __forceinline__ void project_from(Load ld, cx<R> h[6])
 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const cx<R> u0 = p[c], u1 = p[3 + c], d0 = p[6 + c], d1 = p[9 + c];
+        const cx<R> u0 = ld(c), u1 = ld(3 + c), d0 = ld(6 + c), d1 = ld(9 + c);
         const R s = R(S);
         if (MU == 0) {
             h[c] = u0 + s * times_i(d1);
@@ -38,6 +40,12 @@ __device__ __forceinline__ void project(const cx<R> p[12], cx<R> h[6])
             h[3 + c] = u1 + s * d1;
         }
     }
+}
+
+template <int MU, int S, class R>
+__device__ __forceinline__ void project(const cx<R> p[12], cx<R> h[6])
+{
+    project_from<MU, S, R>([&](int k) { return p[k]; }, h);
 }
 
 template <int MU, int S, class R>
