@@ -156,6 +156,25 @@ wc_status wc_norm2(wc_lattice lat, wc_field a, double *out);
 wc_status wc_axpy_norm(wc_lattice lat, const double *a, wc_field x, wc_field y,
                        double *norm2_y);
 
+/* ---- allocation-free variant ------------------------------------------ */
+
+/* out[0] + i out[1] = <a, b> = sum_i conj(a_i) b_i over n complex128 values.
+ * The paper has no counterpart: this is wc_dot for callers that must not
+ * allocate device memory (a framework that owns the memory pool, a
+ * latency-critical path where cudaMalloc would synchronise the device).
+ * a, b: device pointers to n interleaved (re, im) doubles; out: device
+ * pointer to 2 doubles, written on the given CUDA stream (NULL = legacy
+ * default stream); the call returns without waiting for the result.
+ * It allocates nothing: its scratch is a fixed 32 KiB array in the
+ * library's device memory, held by every GPU that loads the library until
+ * the process exits.  n may be at most 8,388,608 (WC_ERR_ARG beyond).
+ * The first call on a device looks up that array's device address (with
+ * that device current) and must come before any stream capture that
+ * includes this call.  Every call shares the one array, so calls whose
+ * kernels overlap on the GPU (e.g. on two streams) race and give wrong
+ * sums; calls ordered on one stream are safe.  Deterministic for fixed n. */
+wc_status wc_dot_noalloc(const double *a, const double *b, long long n, double *out, void *cuda_stream);
+
 /* ---- preconditioner and solvers --------------------------------------- */
 
 /* out = RAS(in) (see wc_ras_params).  FP32 arithmetic on FP32 or FP16

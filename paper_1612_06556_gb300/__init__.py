@@ -5,7 +5,7 @@ it only marshals arguments.  Every step of the operator, the reductions, the
 preconditioner and the solvers runs in the library's CUDA kernels; PyTorch
 (when used) only supplies device memory and the CUDA stream.  There is no
 CPU fallback: importing this package fails if the library is not built
-(``python -m paper_1612_06556_gb300.build`` or ``__graft_entry__.build()``).
+(``python paper_1612_06556_gb300/build.py`` or ``__graft_entry__.build()``).
 
 Arrays crossing the boundary use the canonical complex128 layouts of
 ``include/wc.h``: gauge U[V,4,3,3], spinor psi[V,4,3], force F[V,4,3,3],
@@ -37,6 +37,7 @@ EXPORTED = [
     "wc_field_create", "wc_field_destroy", "wc_field_import", "wc_field_export", "wc_field_copy",
     "wc_apply_M", "wc_apply_Mdag", "wc_apply_hop", "wc_dot", "wc_norm2", "wc_axpy_norm",
     "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
+    "wc_dot_noalloc",
 ]
 
 
@@ -82,6 +83,7 @@ _L.wc_solve_bicgstab.argtypes = [_vp, _vp, _vp, ctypes.POINTER(SolveParams), cty
 _L.wc_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                               ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]
 _L.wc_action_force.argtypes = [_vp, _vp, _dp, _vp, ctypes.POINTER(SolveParams)]
+_L.wc_dot_noalloc.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
 _L.wc_last_error.argtypes = [_vp]
 _L.wc_last_error.restype = ctypes.c_char_p
 for _n in EXPORTED:
@@ -259,6 +261,25 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+def dot_noalloc(a, b, out, stream=None):
+    """out[0] + i out[1] = <a, b> for CUDA complex128 tensors a, b (same
+    number of elements) into the CUDA float64 tensor out (2 elements), with
+    no device allocation (see wc_dot_noalloc in wc.h).  Asynchronous on
+    stream (default: the legacy default stream)."""
+    import torch
+    if not (a.is_cuda and b.is_cuda and out.is_cuda):
+        raise ValueError("a, b and out must be CUDA tensors")
+    if a.dtype != torch.complex128 or b.dtype != torch.complex128 or out.dtype != torch.float64:
+        raise ValueError("a and b must be complex128, out float64")
+    if a.numel() != b.numel() or out.numel() < 2:
+        raise ValueError("a and b must have the same size; out needs 2 elements")
+    if not (a.is_contiguous() and b.is_contiguous() and out.is_contiguous()):
+        raise ValueError("tensors must be contiguous")
+    s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(_L.wc_dot_noalloc(_vp(a.data_ptr()), _vp(b.data_ptr()), a.numel(), _vp(out.data_ptr()), _vp(s)))
+    return out
 
 
 def solve_batch(lattices, xs, bs, params: SolveParams | None = None, **kw):
