@@ -187,9 +187,25 @@ wc_status wc_solve_bicgstab(wc_lattice lat, wc_field x, wc_field b, const wc_sol
                             wc_solve_info *info);
 
 /* Solve M_i x_i = b_i for n right-hand sides on possibly different
- * lattices in one batched solve.  Blocking; fills infos[0..n-1]. */
+ * lattices (each x_i, b_i FP64 fields of lats[i]; x_i distinct) with the
+ * parameters p.  All BiCGStab iterations of all right-hand sides run inside
+ * one CUDA graph launch (a device-side loop with one convergence mask per
+ * right-hand side; right-hand sides proceed concurrently), queued on
+ * internal streams; the true residual of each is then recomputed in FP64 and
+ * any that misses tol is continued by the host-driven solver.  With
+ * p->precond = WC_PRECOND_RAS and p->ras.block = {0,0,0,0} the RAS block
+ * shape of each lattice is chosen by wc_ras_autotune.  Blocking; fills
+ * infos[0..n-1] (seconds: wall time of the whole batch); returns the first
+ * non-OK status of any right-hand side. */
 wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs, wc_field *bs,
                          const wc_solve_params *p, wc_solve_info *infos);
+
+/* Choose the RAS block shape (core extents from {2, 4, 8}, 128 to 512
+ * sites, fitting one CTA and the lattice) that reduces the residual of
+ * M x = b fastest in a short timed trial solve with p's overlap, mr_iters
+ * and inner precision; the result is cached per lattice extent for the
+ * process.  b: an FP64 field of lat.  Blocking; writes *out. */
+wc_status wc_ras_autotune(wc_lattice lat, wc_field b, const wc_solve_params *p, wc_ras_params *out);
 
 /* S = phi^+ (M^+ M)^-1 phi and its force F = dS/dU per link as traceless
  * anti-Hermitian 3x3 matrices (canonical force layout, data = device or

@@ -37,7 +37,7 @@ EXPORTED = [
     "wc_field_create", "wc_field_destroy", "wc_field_import", "wc_field_export", "wc_field_copy",
     "wc_apply_M", "wc_apply_Mdag", "wc_apply_hop", "wc_dot", "wc_norm2", "wc_axpy_norm",
     "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
-    "wc_dot_noalloc",
+    "wc_dot_noalloc", "wc_ras_autotune",
 ]
 
 
@@ -83,6 +83,7 @@ _L.wc_solve_bicgstab.argtypes = [_vp, _vp, _vp, ctypes.POINTER(SolveParams), cty
 _L.wc_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                               ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]
 _L.wc_action_force.argtypes = [_vp, _vp, _dp, _vp, ctypes.POINTER(SolveParams)]
+_L.wc_ras_autotune.argtypes = [_vp, _vp, ctypes.POINTER(SolveParams), ctypes.POINTER(RasParams)]
 _L.wc_dot_noalloc.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
 _L.wc_last_error.argtypes = [_vp]
 _L.wc_last_error.restype = ctypes.c_char_p
@@ -239,6 +240,14 @@ class Lattice:
             _check(st, self.handle)
         return info
 
+    def ras_autotune(self, b: Field, params: SolveParams | None = None, **kw):
+        """Block shape, overlap and MR steps the batched solver's autotuner
+        picks for this lattice (see wc_ras_autotune)."""
+        p = params if params is not None else solve_params(**kw)
+        out = RasParams()
+        _check(_L.wc_ras_autotune(self.handle, b.handle, ctypes.byref(p), ctypes.byref(out)), self.handle)
+        return tuple(out.block), out.overlap, out.mr_iters
+
     def action_force(self, phi: Field, force_out, params: SolveParams | None = None, **kw) -> float:
         p = params if params is not None else solve_params(**kw)
         if _nbytes(force_out) != self.volume * 36 * 16:
@@ -282,7 +291,7 @@ def dot_noalloc(a, b, out, stream=None):
     return out
 
 
-def solve_batch(lattices, xs, bs, params: SolveParams | None = None, **kw):
+def solve_batch(lattices, xs, bs, params: SolveParams | None = None, check=True, **kw):
     """Solve M_i x_i = b_i for all i in one batched call; returns SolveInfos."""
     n = len(xs)
     p = params if params is not None else solve_params(**kw)
@@ -291,6 +300,48 @@ def solve_batch(lattices, xs, bs, params: SolveParams | None = None, **kw):
     B = (_vp * n)(*[b.handle for b in bs])
     infos = (SolveInfo * n)()
     st = _L.wc_solve_batch(n, L, X, B, ctypes.byref(p), infos)
-    if st != 0:
+    if st != 0 and check:
         _check(st, None)
     return list(infos)
+
+
+def _torch_autograd_function():
+    import torch
+
+    class PseudofermionAction(torch.autograd.Function):
+        """S = phi^+ (M^+ M)^-1 phi as a differentiable function of the gauge
+        field U (CUDA complex128 tensor [V,4,3,3], special unitary links).
+
+        forward: loads U into the lattice, builds the clover term, and calls
+        wc_action_force (two FP64 solves M^+ Y = phi, M X = Y; S = |Y|^2; F
+        the traceless anti-Hermitian force per link).  backward: returns
+        grad_U = grad_S * F^+ U = -grad_S * F U, the gradient on the tangent
+        space of SU(3): for U -> exp(eps L) U with L in su(3),
+        dS/deps = Re sum tr(grad_U^+ L U) = sum tr(L F).  phi is not
+        differentiated (its gradient is None)."""
+
+        @staticmethod
+        def forward(ctx, U, phi, lattice, csw, kappa, params):
+            if not (U.is_cuda and U.dtype == torch.complex128 and U.is_contiguous()):
+                raise ValueError("U must be a contiguous CUDA complex128 tensor")
+            lattice.load_gauge(U).load_clover(csw, kappa)
+            f_phi = lattice.field(F64).load(phi.contiguous())
+            F = torch.empty_like(U)
+            S = lattice.action_force(f_phi, F, params)
+            ctx.save_for_backward(U, F)
+            return torch.tensor(S, dtype=torch.float64, device=U.device)
+
+        @staticmethod
+        def backward(ctx, grad_S):
+            U, F = ctx.saved_tensors
+            grad_U = -(F @ U) * grad_S.to(U.dtype)
+            return grad_U, None, None, None, None, None
+
+    return PseudofermionAction
+
+
+def pseudofermion_action(U, phi, lattice: Lattice, csw: float, kappa: float, params: SolveParams | None = None,
+                         **kw):
+    """Differentiable S = phi^+ (M^+ M)^-1 phi (see PseudofermionAction)."""
+    p = params if params is not None else solve_params(**kw)
+    return _torch_autograd_function().apply(U, phi, lattice, float(csw), float(kappa), p)

@@ -328,6 +328,54 @@ wc_status check_field(wc_lattice lat, wc_field f, const char *name)
 }
 
 }  // namespace
+
+wc_status state_init(wc_lattice lat, SolverState &s)
+{
+    const int max_blocks = 8 * sm_count();
+    s.red.max_blocks = max_blocks;
+    wc_status st = check_cuda(lat, dalloc(&s.red.partials, sizeof(double) * 8 * max_blocks), "cudaMalloc");
+    if (st == WC_OK) st = check_cuda(lat, dalloc(&s.red.ticket, sizeof(unsigned)), "cudaMalloc");
+    if (st == WC_OK) st = check_cuda(lat, dalloc(&s.red.result, sizeof(double) * 8), "cudaMalloc");
+    if (st == WC_OK)
+        st = check_cuda(lat, cudaMallocHost(reinterpret_cast<void **>(&s.red.host_result), sizeof(double) * 8),
+                        "cudaMallocHost");
+    if (st == WC_OK) st = check_cuda(lat, dalloc(&s.scal, sizeof(SolverScalars)), "cudaMalloc");
+    if (st == WC_OK)
+        st = check_cuda(lat, cudaMallocHost(reinterpret_cast<void **>(&s.scal_host), sizeof(SolverScalars)),
+                        "cudaMallocHost");
+    if (st == WC_OK) st = check_cuda(lat, cudaMemset(s.red.ticket, 0, sizeof(unsigned)), "cudaMemset");
+    if (st == WC_OK) st = check_cuda(lat, cudaMemset(s.scal, 0, sizeof(SolverScalars)), "cudaMemset");
+    if (st != WC_OK) state_free(s);
+    return st;
+}
+
+void state_free(SolverState &s)
+{
+    for (auto &w : s.work) {
+        wc_field_destroy(w);
+        w = nullptr;
+    }
+    cudaFree(s.red.partials);
+    cudaFree(s.red.ticket);
+    cudaFree(s.red.result);
+    cudaFreeHost(s.red.host_result);
+    cudaFree(s.scal);
+    cudaFreeHost(s.scal_host);
+    s = SolverState{};
+}
+
+wc_field state_work(wc_lattice lat, SolverState &s, int slot, wc_prec prec, wc_status *st)
+{
+    if (!s.work[slot]) {
+        *st = wc_field_create(lat, prec, &s.work[slot]);
+        if (*st != WC_OK) return nullptr;
+    }
+    *st = WC_OK;
+    return s.work[slot];
+}
+
+namespace {
+}  // namespace
 }  // namespace wc
 
 using namespace wc;
@@ -355,19 +403,7 @@ wc_status wc_create_lattice(const int dims[4], int t_bc, void *cuda_stream, wc_l
     lat->g.V = (int)V;
     lat->g.tbc = t_bc;
     lat->stream = static_cast<cudaStream_t>(cuda_stream);
-    const int max_blocks = 8 * sm_count();
-    lat->red.max_blocks = max_blocks;
-    wc_status st = check_cuda(lat, dalloc(&lat->red.partials, sizeof(double) * 8 * max_blocks), "cudaMalloc");
-    if (st == WC_OK) st = check_cuda(lat, dalloc(&lat->red.ticket, sizeof(unsigned)), "cudaMalloc");
-    if (st == WC_OK) st = check_cuda(lat, dalloc(&lat->red.result, sizeof(double) * 8), "cudaMalloc");
-    if (st == WC_OK)
-        st = check_cuda(lat, cudaMallocHost(reinterpret_cast<void **>(&lat->red.host_result), sizeof(double) * 8),
-                        "cudaMallocHost");
-    if (st == WC_OK) st = check_cuda(lat, dalloc(&lat->scal, sizeof(SolverScalars)), "cudaMalloc");
-    if (st == WC_OK)
-        st = check_cuda(lat, cudaMallocHost(reinterpret_cast<void **>(&lat->scal_host), sizeof(SolverScalars)),
-                        "cudaMallocHost");
-    if (st == WC_OK) st = check_cuda(lat, cudaMemset(lat->red.ticket, 0, sizeof(unsigned)), "cudaMemset");
+    wc_status st = state_init(lat, lat->st);
     if (st != WC_OK) {
         set_error(nullptr, st, lat->err);
         wc_destroy_lattice(lat);
@@ -381,18 +417,9 @@ wc_status wc_destroy_lattice(wc_lattice lat)
 {
     if (!lat) return WC_OK;
     cudaStreamSynchronize(lat->stream);
-    for (auto &w : lat->work) {
-        wc_field_destroy(w);
-        w = nullptr;
-    }
+    state_free(lat->st);
     free_gauge(lat->gauge);
     free_clover(lat->clover);
-    cudaFree(lat->red.partials);
-    cudaFree(lat->red.ticket);
-    cudaFree(lat->red.result);
-    cudaFreeHost(lat->red.host_result);
-    cudaFree(lat->scal);
-    cudaFreeHost(lat->scal_host);
     cudaFree(lat->staging);
     delete lat;
     return WC_OK;
@@ -570,7 +597,7 @@ wc_status wc_field_copy(wc_field dst, wc_field src, double scale)
     wc_lattice lat = dst->lat;
     if (src->lat != lat) return set_error(lat, WC_ERR_ARG, "fields belong to different lattices");
     if (!isfinite(scale)) return set_error(lat, WC_ERR_ARG, "scale must be finite");
-    return check_cuda(lat, launch_copy(lat, dst, src, scale, nullptr, 0), "field_copy");
+    return check_cuda(lat, launch_copy(lat, dst, src, scale, nullptr, 0, lat->stream), "field_copy");
 }
 
 static wc_status apply_common(wc_lattice lat, wc_field out, wc_field in, int kind)
@@ -583,7 +610,7 @@ static wc_status apply_common(wc_lattice lat, wc_field out, wc_field in, int kin
     if (out->prec != in->prec) return set_error(lat, WC_ERR_ARG, "out and in must have the same precision");
     if (!lat->gauge_loaded) return set_error(lat, WC_ERR_STATE, "gauge field not loaded");
     if (kind != 2 && !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "clover term not loaded");
-    return check_cuda(lat, launch_apply(lat, out, in, kind), "apply");
+    return check_cuda(lat, launch_apply(lat, out, in, kind, lat->stream), "apply");
 }
 
 wc_status wc_apply_M(wc_lattice lat, wc_field out, wc_field in) { return apply_common(lat, out, in, 0); }

@@ -1,9 +1,195 @@
-// Batched solves over several lattices / right-hand sides.
+// Batched solves: many right-hand sides on possibly different lattices in
+// one CUDA graph launch.
+//
+// The paper's host proxy exists so that the accelerator never returns to the
+// host between solver steps (Sec. 2, reverse offloading).  Here the whole
+// BiCGStab iteration loop of every right-hand side runs inside one graph:
+//
+//   WHILE (any RHS active)                      <- device-side condition
+//     IF (RHS 0 active) { one BiCGStab step }   \
+//     IF (RHS 1 active) { one BiCGStab step }    > independent branches,
+//     ...                                       /  run concurrently
+//     check: per RHS, stop at |r| <= tol |b|, breakdown, NaN or max_iter;
+//            set the IF conditions and the WHILE condition
+//
+// Each branch is captured from the same enqueue_iteration() the single-RHS
+// solve uses, on that RHS's own solver state (scalars, reduction scratch,
+// work vectors), so the branches share nothing but the read-only gauge field
+// and clover term of their lattice.  No host round trip happens until every
+// RHS has stopped; then the true residual of each RHS is recomputed in FP64
+// and any RHS that misses tol is restarted by the host-driven solver.
+//
+// RAS block shapes: with ras.block = {0,0,0,0} the shape is chosen per
+// lattice extent and inner precision by a small autotuner (candidate shapes
+// timed on a short trial solve, result cached for the process).
+#include <math.h>
+
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "wc_internal.cuh"
+#include "wc_solver.cuh"
+#include "wc_solver_kernels.cuh"
 
 namespace wc {
-wc_status bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p, wc_solve_info *info);
-wc_status check_solve_args(wc_lattice lat, wc_field x, wc_field b, const wc_solve_params *p);
+
+bool ras_fits(const wc_ras_params &p);
+
+namespace {
+
+struct BatchItem {
+    const SolverScalars *scal;
+    double tol2;
+    int max_iter;
+    int pad;
+};
+
+__global__ void k_batch_check(const BatchItem *items, int n, int *iters, int *active,
+                              const cudaGraphConditionalHandle *ifh, cudaGraphConditionalHandle wh)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int a = active[i];
+        if (a) {
+            const int it = ++iters[i];
+            const SolverScalars &s = *items[i].scal;
+            if (!(s.rr > items[i].tol2) || s.flags != 0 || it >= items[i].max_iter) a = 0;
+            active[i] = a;
+        }
+        cudaGraphSetConditional(ifh[i], a ? 1u : 0u);
+        if (a) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(wh, any ? 1u : 0u);
+}
+
+struct Resources {
+    std::vector<SolverState> S;
+    std::vector<SolverVecs> W;
+    std::vector<cudaStream_t> streams;
+    BatchItem *d_items = nullptr;
+    int *d_iters = nullptr, *d_active = nullptr;
+    cudaGraphConditionalHandle *d_handles = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+
+    ~Resources()
+    {
+        for (auto s : streams)
+            if (s) cudaStreamSynchronize(s);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(d_items);
+        cudaFree(d_iters);
+        cudaFree(d_active);
+        cudaFree(d_handles);
+        for (auto &s : S) state_free(s);
+        for (auto s : streams)
+            if (s) cudaStreamDestroy(s);
+    }
+};
+
+// ---- RAS block-shape autotuner ------------------------------------------
+
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int, int, int>, wc_ras_params> g_tuned;
+
+std::vector<wc_ras_params> ras_candidates(wc_lattice lat, const wc_ras_params &base)
+{
+    std::vector<wc_ras_params> out;
+    const int opts[3] = {2, 4, 8};
+    for (int a : opts)
+        for (int b : opts)
+            for (int c : opts)
+                for (int d : opts) {
+                    const int core = a * b * c * d;
+                    if (core < 128 || core > 512) continue;
+                    wc_ras_params q = base;
+                    q.block[0] = a;
+                    q.block[1] = b;
+                    q.block[2] = c;
+                    q.block[3] = d;
+                    bool ok = ras_fits(q);
+                    for (int m = 0; m < 4 && ok; ++m)
+                        ok = lat->g.L[m] % q.block[m] == 0 && lat->g.L[m] > q.block[m] + 2 * q.overlap;
+                    if (ok) out.push_back(q);
+                }
+    return out;
+}
+
+// Pick the block shape that reduces the residual fastest on a short trial
+// solve of M x = b from x = 0 (log of the residual reduction per second).
+wc_status autotune_ras(wc_lattice lat, wc_field b, const wc_solve_params &p, wc_ras_params *out)
+{
+    const auto key = std::make_tuple(lat->g.L[0], lat->g.L[1], lat->g.L[2], lat->g.L[3], (int)p.inner_prec,
+                                     p.ras.overlap * 1000 + p.ras.mr_iters);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            *out = it->second;
+            return WC_OK;
+        }
+    }
+    wc_ras_params base = p.ras;
+    std::vector<wc_ras_params> cands = ras_candidates(lat, base);
+    if (cands.empty()) return set_error(lat, WC_ERR_ARG, "RAS autotuner: no block shape fits this lattice");
+    wc_field x = nullptr;
+    wc_status st = wc_field_create(lat, WC_F64, &x);
+    if (st != WC_OK) return st;
+    double best = -1.0;
+    wc_ras_params best_p = cands[0];
+    // the first trial also creates the solver's work fields: run it twice
+    std::vector<wc_ras_params> trials;
+    trials.push_back(cands[0]);
+    trials.insert(trials.end(), cands.begin(), cands.end());
+    for (size_t ti = 0; ti < trials.size(); ++ti) {
+        const wc_ras_params &c = trials[ti];
+        wc_solve_params q = p;
+        q.ras = c;
+        q.max_iter = 2;
+        q.max_restarts = 0;
+        q.tol = 1e-30;
+        st = check_cuda(lat, cudaMemsetAsync(x->data, 0, spinor_bytes(WC_F64, lat->g.V), lat->stream), "memset");
+        if (st != WC_OK) break;
+        wc_solve_info info{};
+        const wc_status r = bicgstab(lat, 0, x, b, q, &info);
+        if (r != WC_OK && r != WC_ERR_NOT_CONVERGED) continue;
+        if (ti == 0 || !(info.true_rel_resid > 0.0) || info.seconds <= 0.0) continue;
+        const double rate = -log(info.true_rel_resid) / info.seconds;
+        if (rate > best) {
+            best = rate;
+            best_p = c;
+        }
+    }
+    wc_field_destroy(x);
+    if (st != WC_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tuned[key] = best_p;
+    }
+    *out = best_p;
+    return WC_OK;
+}
+
+}  // namespace
+
+// The RAS parameters a solve on lat uses: p.ras, or the autotuned shape
+// when p.ras.block is all zero (needs a right-hand side to tune on).
+wc_status resolve_ras(wc_lattice lat, wc_field b, const wc_solve_params &p, wc_ras_params *out)
+{
+    if (p.precond != WC_PRECOND_RAS || p.ras.block[0] != 0) {
+        *out = p.ras;
+        return WC_OK;
+    }
+    return autotune_ras(lat, b, p, out);
+}
+
 }  // namespace wc
 
 using namespace wc;
@@ -13,14 +199,222 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
 {
     if (n < 0 || (n > 0 && (!lats || !xs || !bs || !p || !infos)))
         return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: bad arguments");
+    if (n == 0) return WC_OK;
     for (int i = 0; i < n; ++i) {
-        wc_status st = check_solve_args(lats[i], xs[i], bs[i], p);
+        // the RAS shape is checked after autotuning when it is left to it
+        wc_solve_params q = *p;
+        if (q.precond == WC_PRECOND_RAS && q.ras.block[0] == 0) q.precond = WC_PRECOND_NONE;
+        if (!lats[i]) return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: NULL lattice");
+        const wc_status st = check_solve_args(lats[i], xs[i], bs[i], &q);
+        if (st != WC_OK)
+            return set_error(nullptr, st, "wc_solve_batch: RHS " + std::to_string(i) + ": " + lats[i]->err);
+        if (p->precond == WC_PRECOND_RAS && (p->inner_prec != WC_F32 && p->inner_prec != WC_F16))
+            return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: RAS inner precision must be WC_F32 or WC_F16");
+        for (int j = 0; j < i; ++j)
+            if (xs[j] == xs[i] || xs[i] == bs[j])
+                return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: solution fields must be distinct");
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    Resources R;
+    R.S.resize(n);
+    R.W.resize(n);
+    R.streams.assign(n, nullptr);
+    std::vector<wc_solve_params> P(n, *p);
+    wc_status st = check_cuda(nullptr, ras_prepare(), "ras_prepare");
+    // RAS shapes (autotuned per lattice when requested)
+    for (int i = 0; i < n && st == WC_OK; ++i) {
+        st = resolve_ras(lats[i], bs[i], *p, &P[i].ras);
+        if (st == WC_OK && P[i].precond == WC_PRECOND_RAS) st = check_ras_params(lats[i], &P[i].ras);
+        if (st != WC_OK) return set_error(nullptr, st, std::string("wc_solve_batch: ") + lats[i]->err);
+    }
+    for (int i = 0; i < n && st == WC_OK; ++i) {
+        st = state_init(lats[i], R.S[i]);
+        if (st == WC_OK) st = check_cuda(lats[i], cudaStreamCreateWithFlags(&R.streams[i], cudaStreamNonBlocking),
+                                         "cudaStreamCreate");
+        if (st == WC_OK) {
+            R.S[i].stream = R.streams[i];
+            st = solver_vectors(lats[i], R.S[i], P[i], &R.W[i]);
+        }
+    }
+    if (st != WC_OK) return st;
+
+    // |b|^2 and r = b - M x for every RHS, one synchronisation for all
+    std::vector<double> bb(n), tol2(n);
+    for (int i = 0; i < n && st == WC_OK; ++i) {
+        SolverState &S = R.S[i];
+        st = check_cuda(lats[i], norm2_to_result(lats[i], S, static_cast<const double2 *>(bs[i]->data)), "norm2");
+        if (st == WC_OK)
+            st = check_cuda(lats[i], cudaMemcpyAsync(S.red.host_result, S.red.result, sizeof(double),
+                                                     cudaMemcpyDeviceToHost, S.stream), "copy");
+        if (st == WC_OK) st = enqueue_init(lats[i], S, 0, xs[i], bs[i], R.W[i]);
+        if (st == WC_OK)
+            st = check_cuda(lats[i], cudaMemcpyAsync(S.scal_host, S.scal, sizeof(SolverScalars),
+                                                     cudaMemcpyDeviceToHost, S.stream), "copy");
+    }
+    for (int i = 0; i < n && st == WC_OK; ++i) st = check_cuda(lats[i], cudaStreamSynchronize(R.streams[i]), "sync");
+    if (st != WC_OK) return st;
+    std::vector<int> active(n, 0), iters(n, 0);
+    int any = 0;
+    for (int i = 0; i < n; ++i) {
+        infos[i] = wc_solve_info{};
+        bb[i] = R.S[i].red.host_result[0];
+        tol2[i] = P[i].tol * P[i].tol * bb[i];
+        const SolverScalars &h = *R.S[i].scal_host;
+        if (!isfinite(bb[i]) || (h.flags & FLAG_NAN)) {
+            infos[i].status = WC_ERR_NAN;
+        } else if (bb[i] == 0.0 || h.rr <= tol2[i]) {
+            infos[i].status = WC_OK;   // settled below (zero source: x = 0)
+        } else if (P[i].max_iter > 0) {
+            active[i] = 1;
+            any = 1;
+        }
+    }
+
+    if (any) {
+        std::vector<BatchItem> items(n);
+        for (int i = 0; i < n; ++i) items[i] = BatchItem{R.S[i].scal, tol2[i], P[i].max_iter, 0};
+        cudaStream_t s0 = R.streams[0];
+        st = check_cuda(nullptr, cudaMalloc(&R.d_items, sizeof(BatchItem) * n), "cudaMalloc");
+        if (st == WC_OK) st = check_cuda(nullptr, cudaMalloc(&R.d_iters, sizeof(int) * n), "cudaMalloc");
+        if (st == WC_OK) st = check_cuda(nullptr, cudaMalloc(&R.d_active, sizeof(int) * n), "cudaMalloc");
+        if (st == WC_OK)
+            st = check_cuda(nullptr, cudaMalloc(&R.d_handles, sizeof(cudaGraphConditionalHandle) * n), "cudaMalloc");
+        if (st == WC_OK)
+            st = check_cuda(nullptr, cudaMemcpy(R.d_items, items.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice),
+                            "copy");
+        if (st == WC_OK)
+            st = check_cuda(nullptr, cudaMemcpy(R.d_iters, iters.data(), sizeof(int) * n, cudaMemcpyHostToDevice), "copy");
+        if (st == WC_OK)
+            st = check_cuda(nullptr, cudaMemcpy(R.d_active, active.data(), sizeof(int) * n, cudaMemcpyHostToDevice),
+                            "copy");
+        // graph: WHILE { IF_i { iteration_i } ... ; check }
+        if (st == WC_OK) st = check_cuda(nullptr, cudaGraphCreate(&R.graph, 0), "cudaGraphCreate");
+        cudaGraphConditionalHandle wh = 0;
+        cudaGraph_t body = nullptr;
+        if (st == WC_OK)
+            st = check_cuda(nullptr, cudaGraphConditionalHandleCreate(&wh, R.graph, 1, cudaGraphCondAssignDefault),
+                            "cudaGraphConditionalHandleCreate");
+        if (st == WC_OK) {
+            cudaGraphNodeParams wp = {};
+            wp.type = cudaGraphNodeTypeConditional;
+            wp.conditional.handle = wh;
+            wp.conditional.type = cudaGraphCondTypeWhile;
+            wp.conditional.size = 1;
+            cudaGraphNode_t wnode;
+            st = check_cuda(nullptr, cudaGraphAddNode(&wnode, R.graph, nullptr, nullptr, 0, &wp), "add while node");
+            if (st == WC_OK) body = wp.conditional.phGraph_out[0];
+        }
+        std::vector<cudaGraphConditionalHandle> handles(n, 0);
+        std::vector<cudaGraphNode_t> ifnodes;
+        for (int i = 0; i < n && st == WC_OK; ++i) {
+            st = check_cuda(nullptr, cudaGraphConditionalHandleCreate(&handles[i], body, active[i] ? 1u : 0u,
+                                                                      cudaGraphCondAssignDefault),
+                            "cudaGraphConditionalHandleCreate");
+            if (st != WC_OK) break;
+            cudaGraphNodeParams ip = {};
+            ip.type = cudaGraphNodeTypeConditional;
+            ip.conditional.handle = handles[i];
+            ip.conditional.type = cudaGraphCondTypeIf;
+            ip.conditional.size = 1;
+            cudaGraphNode_t inode;
+            st = check_cuda(nullptr, cudaGraphAddNode(&inode, body, nullptr, nullptr, 0, &ip), "add if node");
+            if (st != WC_OK) break;
+            ifnodes.push_back(inode);
+            cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+            SolverState &S = R.S[i];
+            st = check_cuda(nullptr, cudaStreamBeginCaptureToGraph(S.stream, ibody, nullptr, nullptr, 0,
+                                                                   cudaStreamCaptureModeRelaxed),
+                            "cudaStreamBeginCaptureToGraph");
+            if (st != WC_OK) break;
+            const wc_status est = enqueue_iteration(lats[i], S, P[i], 0, xs[i], R.W[i]);
+            cudaGraph_t captured = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(S.stream, &captured);
+            if (est != WC_OK) st = set_error(nullptr, est, lats[i]->err);
+            if (st == WC_OK) st = check_cuda(nullptr, ce, "cudaStreamEndCapture");
+        }
+        if (st == WC_OK)
+            st = check_cuda(nullptr, cudaMemcpy(R.d_handles, handles.data(), sizeof(cudaGraphConditionalHandle) * n,
+                                                cudaMemcpyHostToDevice),
+                            "copy");
+        if (st == WC_OK) {
+            void *args[] = {&R.d_items, &n, &R.d_iters, &R.d_active, &R.d_handles, &wh};
+            cudaKernelNodeParams kp = {};
+            kp.func = reinterpret_cast<void *>(k_batch_check);
+            kp.gridDim = dim3(1);
+            kp.blockDim = dim3(256);
+            kp.sharedMemBytes = 0;
+            kp.kernelParams = args;
+            cudaGraphNode_t cnode;
+            st = check_cuda(nullptr, cudaGraphAddKernelNode(&cnode, body, ifnodes.data(), ifnodes.size(), &kp),
+                            "add check node");
+        }
+        if (st == WC_OK) st = check_cuda(nullptr, cudaGraphInstantiate(&R.exec, R.graph, 0), "cudaGraphInstantiate");
+        if (st == WC_OK) st = check_cuda(nullptr, cudaGraphLaunch(R.exec, s0), "cudaGraphLaunch");
+        if (st == WC_OK) st = check_cuda(nullptr, cudaStreamSynchronize(s0), "sync(graph)");
+        if (st == WC_OK)
+            st = check_cuda(nullptr, cudaMemcpy(iters.data(), R.d_iters, sizeof(int) * n, cudaMemcpyDeviceToHost),
+                            "copy");
         if (st != WC_OK) return st;
     }
+
+    // true residuals in FP64 for every RHS, then host-driven restarts
+    for (int i = 0; i < n && st == WC_OK; ++i) {
+        if (infos[i].status == WC_ERR_NAN) continue;
+        SolverState &S = R.S[i];
+        if (bb[i] == 0.0) {
+            st = check_cuda(lats[i], cudaMemsetAsync(xs[i]->data, 0, spinor_bytes(WC_F64, lats[i]->g.V), S.stream),
+                            "memset");
+            continue;
+        }
+        st = enqueue_true_residual(lats[i], S, 0, xs[i], bs[i], R.W[i]);
+        if (st == WC_OK)
+            st = check_cuda(lats[i], cudaMemcpyAsync(S.scal_host, S.scal, sizeof(SolverScalars),
+                                                     cudaMemcpyDeviceToHost, S.stream), "copy");
+    }
+    for (int i = 0; i < n && st == WC_OK; ++i) st = check_cuda(lats[i], cudaStreamSynchronize(R.streams[i]), "sync");
+    if (st != WC_OK) return st;
+    const double batch_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     wc_status worst = WC_OK;
     for (int i = 0; i < n; ++i) {
-        wc_status st = bicgstab(lats[i], 0, xs[i], bs[i], *p, &infos[i]);
-        if (st != WC_OK && worst == WC_OK) worst = st;
+        wc_solve_info &inf = infos[i];
+        inf.iters = iters[i];
+        if (inf.status != WC_ERR_NAN && bb[i] > 0.0) {
+            const double rr = R.S[i].scal_host->rr;
+            inf.true_rel_resid = sqrt(rr / bb[i]);
+            if (!isfinite(rr)) {
+                inf.status = WC_ERR_NAN;
+            } else if (rr <= tol2[i]) {
+                inf.status = WC_OK;
+            } else if (iters[i] >= P[i].max_iter) {
+                inf.status = WC_ERR_NOT_CONVERGED;
+            } else {
+                // missed tol (drift of the recursive residual or breakdown):
+                // continue from x with the host-driven solver
+                wc_solve_params q = P[i];
+                q.max_restarts = p->max_restarts > 0 ? p->max_restarts - 1 : 0;
+                const wc_status r = bicgstab(lats[i], R.S[i], 0, xs[i], bs[i], q, &inf, iters[i], bb[i]);
+                inf.restarts += 1;
+                (void)r;
+            }
+        }
+        inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (inf.status == WC_OK) inf.seconds = batch_seconds;
+        if (inf.status != WC_OK && worst == WC_OK) worst = inf.status;
     }
     return worst;
+}
+
+extern "C" wc_status wc_ras_autotune(wc_lattice lat, wc_field b, const wc_solve_params *p, wc_ras_params *out)
+{
+    if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
+    if (!b || !p || !out) return set_error(lat, WC_ERR_ARG, "NULL argument");
+    if (b->lat != lat || b->prec != WC_F64) return set_error(lat, WC_ERR_ARG, "b must be an FP64 field of lat");
+    if (!lat->gauge_loaded || !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "gauge/clover not loaded");
+    if (p->inner_prec != WC_F32 && p->inner_prec != WC_F16) return set_error(lat, WC_ERR_ARG, "bad inner precision");
+    if (p->ras.overlap < 0 || p->ras.mr_iters < 0) return set_error(lat, WC_ERR_ARG, "bad RAS overlap / mr_iters");
+    wc_solve_params q = *p;
+    q.precond = WC_PRECOND_RAS;
+    for (int m = 0; m < 4; ++m) q.ras.block[m] = 0;
+    if (!(q.tol > 0.0)) q.tol = 1e-10;
+    return resolve_ras(lat, b, q, out);
 }

@@ -130,16 +130,16 @@ template <class PA>
 cudaError_t launch_dot_a(wc_lattice lat, wc_field a, wc_field b)
 {
     const int V = lat->g.V;
-    const int grid = reduce_grid(lat->red, V);
+    const int grid = reduce_grid(lat->st.red, V);
     switch (b->prec) {
     case WC_F64:
-        k_dot<PA, P64><<<grid, kRedBlock, 0, lat->stream>>>(V, a->data, a->nrm, b->data, b->nrm, lat->red);
+        k_dot<PA, P64><<<grid, kRedBlock, 0, lat->stream>>>(V, a->data, a->nrm, b->data, b->nrm, lat->st.red);
         break;
     case WC_F32:
-        k_dot<PA, P32><<<grid, kRedBlock, 0, lat->stream>>>(V, a->data, a->nrm, b->data, b->nrm, lat->red);
+        k_dot<PA, P32><<<grid, kRedBlock, 0, lat->stream>>>(V, a->data, a->nrm, b->data, b->nrm, lat->st.red);
         break;
     default:
-        k_dot<PA, P16><<<grid, kRedBlock, 0, lat->stream>>>(V, a->data, a->nrm, b->data, b->nrm, lat->red);
+        k_dot<PA, P16><<<grid, kRedBlock, 0, lat->stream>>>(V, a->data, a->nrm, b->data, b->nrm, lat->st.red);
     }
     return cudaGetLastError();
 }
@@ -147,12 +147,12 @@ cudaError_t launch_dot_a(wc_lattice lat, wc_field a, wc_field b)
 wc_status fetch_result(wc_lattice lat, int n, double *out)
 {
     wc_status st = check_cuda(lat,
-                              cudaMemcpyAsync(lat->red.host_result, lat->red.result, sizeof(double) * n,
+                              cudaMemcpyAsync(lat->st.red.host_result, lat->st.red.result, sizeof(double) * n,
                                               cudaMemcpyDeviceToHost, lat->stream),
                               "cudaMemcpyAsync(reduce)");
     if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync(reduce)");
     if (st == WC_OK)
-        for (int i = 0; i < n; ++i) out[i] = lat->red.host_result[i];
+        for (int i = 0; i < n; ++i) out[i] = lat->st.red.host_result[i];
     return st;
 }
 
@@ -182,19 +182,19 @@ wc_status reduce_norm2(wc_lattice lat, wc_field a, double *out)
 wc_status axpy_norm(wc_lattice lat, const double a[2], wc_field x, wc_field y, double *norm2)
 {
     const int V = lat->g.V;
-    const int grid = reduce_grid(lat->red, V);
+    const int grid = reduce_grid(lat->st.red, V);
     switch (y->prec) {
     case WC_F64:
         k_axpy_norm<P64><<<grid, kRedBlock, 0, lat->stream>>>(V, a[0], a[1], x->data, x->nrm, y->data, y->nrm,
-                                                              lat->red);
+                                                              lat->st.red);
         break;
     case WC_F32:
         k_axpy_norm<P32><<<grid, kRedBlock, 0, lat->stream>>>(V, a[0], a[1], x->data, x->nrm, y->data, y->nrm,
-                                                              lat->red);
+                                                              lat->st.red);
         break;
     default:
         k_axpy_norm<P16><<<grid, kRedBlock, 0, lat->stream>>>(V, a[0], a[1], x->data, x->nrm, y->data, y->nrm,
-                                                              lat->red);
+                                                              lat->st.red);
     }
     wc_status st = check_launch(lat, "axpy_norm");
     if (st != WC_OK) return st;
@@ -224,6 +224,18 @@ __device__ __forceinline__ cx<double> cdiv(cx<double> a, cx<double> b)
     return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
 }
 __device__ __forceinline__ bool finite2(cx<double> a) { return isfinite(a.re) && isfinite(a.im); }
+
+// result[0] = |a|^2 (FP64 field as a flat array)
+__global__ void __launch_bounds__(kRedBlock) k_norm2_flat(long long n, const double2 *a, ReduceScratch rs)
+{
+    double acc[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cx<double> ai = ld(a, i);
+        acc[0] += ai.re * ai.re + ai.im * ai.im;
+    }
+    grid_reduce<1>(acc, rs, rs.result);
+}
 
 // r = b - r (r holds M x on entry), rhat = r, p = v = 0;  rr = |r|^2
 __global__ void __launch_bounds__(kRedBlock) k_bicg_init(long long n, const double2 *b, double2 *r, double2 *rhat,
@@ -389,49 +401,56 @@ __global__ void __launch_bounds__(kRedBlock) k_residual(long long n, const doubl
 
 }  // namespace
 
-#define WC_GRID(n) reduce_grid(lat->red, (n)), kRedBlock, 0, lat->stream
+#define WC_GRID(n) reduce_grid(S.red, (n)), kRedBlock, 0, S.stream
 
-cudaError_t bicg_init(wc_lattice lat, const double2 *b, double2 *r, double2 *rhat, double2 *p, double2 *v)
+cudaError_t bicg_init(wc_lattice lat, SolverState &S, const double2 *b, double2 *r, double2 *rhat, double2 *p,
+                      double2 *v)
 {
     const long long n = 12LL * lat->g.V;
-    k_bicg_init<<<WC_GRID(n)>>>(n, b, r, rhat, p, v, lat->red, lat->scal);
+    k_bicg_init<<<WC_GRID(n)>>>(n, b, r, rhat, p, v, S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t bicg_p(wc_lattice lat, const double2 *r, const double2 *v, double2 *p)
+cudaError_t bicg_p(wc_lattice lat, SolverState &S, const double2 *r, const double2 *v, double2 *p)
 {
     const long long n = 12LL * lat->g.V;
-    k_bicg_p<<<WC_GRID(n)>>>(n, r, v, p, lat->red, lat->scal);
+    k_bicg_p<<<WC_GRID(n)>>>(n, r, v, p, S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t bicg_alpha(wc_lattice lat, const double2 *rhat, const double2 *v)
+cudaError_t bicg_alpha(wc_lattice lat, SolverState &S, const double2 *rhat, const double2 *v)
 {
     const long long n = 12LL * lat->g.V;
-    k_bicg_alpha<<<WC_GRID(n)>>>(n, rhat, v, lat->red, lat->scal);
+    k_bicg_alpha<<<WC_GRID(n)>>>(n, rhat, v, S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t bicg_s(wc_lattice lat, const double2 *r, const double2 *v, double2 *s)
+cudaError_t bicg_s(wc_lattice lat, SolverState &S, const double2 *r, const double2 *v, double2 *s)
 {
     const long long n = 12LL * lat->g.V;
-    k_bicg_s<<<WC_GRID(n)>>>(n, r, v, s, lat->red, lat->scal);
+    k_bicg_s<<<WC_GRID(n)>>>(n, r, v, s, S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t bicg_omega(wc_lattice lat, const double2 *t, const double2 *s)
+cudaError_t bicg_omega(wc_lattice lat, SolverState &S, const double2 *t, const double2 *s)
 {
     const long long n = 12LL * lat->g.V;
-    k_bicg_omega<<<WC_GRID(n)>>>(n, t, s, lat->red, lat->scal);
+    k_bicg_omega<<<WC_GRID(n)>>>(n, t, s, S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t bicg_xr(wc_lattice lat, double2 *x, const double2 *phat, const double2 *shat, const double2 *s,
-                    const double2 *t, double2 *r, const double2 *rhat)
+cudaError_t bicg_xr(wc_lattice lat, SolverState &S, double2 *x, const double2 *phat, const double2 *shat,
+                    const double2 *s, const double2 *t, double2 *r, const double2 *rhat)
 {
     const long long n = 12LL * lat->g.V;
-    k_bicg_xr<<<WC_GRID(n)>>>(n, x, phat, shat, s, t, r, rhat, lat->red, lat->scal);
+    k_bicg_xr<<<WC_GRID(n)>>>(n, x, phat, shat, s, t, r, rhat, S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t residual(wc_lattice lat, const double2 *b, double2 *r)
+cudaError_t residual(wc_lattice lat, SolverState &S, const double2 *b, double2 *r)
 {
     const long long n = 12LL * lat->g.V;
-    k_residual<<<WC_GRID(n)>>>(n, b, r, lat->red, lat->scal);
+    k_residual<<<WC_GRID(n)>>>(n, b, r, S.red, S.scal);
+    return cudaGetLastError();
+}
+cudaError_t norm2_to_result(wc_lattice lat, SolverState &S, const double2 *a)
+{
+    const long long n = 12LL * lat->g.V;
+    k_norm2_flat<<<WC_GRID(n)>>>(n, a, S.red);
     return cudaGetLastError();
 }
 

@@ -87,18 +87,18 @@ __global__ void __launch_bounds__(kApplyBlock) k_apply(Geom g, GaugeStore U, Clo
 }
 
 template <class P>
-cudaError_t launch_apply_p(wc_lattice lat, wc_field out, wc_field in, int kind)
+cudaError_t launch_apply_p(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t stream)
 {
     const int V = lat->g.V;
     dim3 grid((V + kApplyBlock - 1) / kApplyBlock), block(kApplyBlock);
     if (kind == 0)
-        k_apply<P, 0><<<grid, block, 0, lat->stream>>>(lat->g, lat->gauge, lat->clover, in->data, in->nrm,
+        k_apply<P, 0><<<grid, block, 0, stream>>>(lat->g, lat->gauge, lat->clover, in->data, in->nrm,
                                                        out->data, out->nrm, lat->kappa);
     else if (kind == 1)
-        k_apply<P, 1><<<grid, block, 0, lat->stream>>>(lat->g, lat->gauge, lat->clover, in->data, in->nrm,
+        k_apply<P, 1><<<grid, block, 0, stream>>>(lat->g, lat->gauge, lat->clover, in->data, in->nrm,
                                                        out->data, out->nrm, lat->kappa);
     else
-        k_apply<P, 2><<<grid, block, 0, lat->stream>>>(lat->g, lat->gauge, lat->clover, in->data, in->nrm,
+        k_apply<P, 2><<<grid, block, 0, stream>>>(lat->g, lat->gauge, lat->clover, in->data, in->nrm,
                                                        out->data, out->nrm, lat->kappa);
     return cudaGetLastError();
 }
@@ -132,41 +132,42 @@ __global__ void k_copy(int V, const void *src, const float *src_nrm, void *dst, 
 }
 
 template <class PS>
-cudaError_t launch_copy_s(wc_lattice lat, wc_field dst, wc_field src, double scale, const double *dn, int inv)
+cudaError_t launch_copy_s(wc_lattice lat, wc_field dst, wc_field src, double scale, const double *dn, int inv,
+                          cudaStream_t stream)
 {
     const int V = lat->g.V;
     dim3 grid((V + 255) / 256), block(256);
     switch (dst->prec) {
     case WC_F64:
-        k_copy<PS, P64><<<grid, block, 0, lat->stream>>>(V, src->data, src->nrm, dst->data, dst->nrm, scale, dn, inv);
+        k_copy<PS, P64><<<grid, block, 0, stream>>>(V, src->data, src->nrm, dst->data, dst->nrm, scale, dn, inv);
         break;
     case WC_F32:
-        k_copy<PS, P32><<<grid, block, 0, lat->stream>>>(V, src->data, src->nrm, dst->data, dst->nrm, scale, dn, inv);
+        k_copy<PS, P32><<<grid, block, 0, stream>>>(V, src->data, src->nrm, dst->data, dst->nrm, scale, dn, inv);
         break;
     default:
-        k_copy<PS, P16><<<grid, block, 0, lat->stream>>>(V, src->data, src->nrm, dst->data, dst->nrm, scale, dn, inv);
+        k_copy<PS, P16><<<grid, block, 0, stream>>>(V, src->data, src->nrm, dst->data, dst->nrm, scale, dn, inv);
     }
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind)
+cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t stream)
 {
     switch (in->prec) {
-    case WC_F64: return launch_apply_p<P64>(lat, out, in, kind);
-    case WC_F32: return launch_apply_p<P32>(lat, out, in, kind);
-    default: return launch_apply_p<P16>(lat, out, in, kind);
+    case WC_F64: return launch_apply_p<P64>(lat, out, in, kind, stream);
+    case WC_F32: return launch_apply_p<P32>(lat, out, in, kind, stream);
+    default: return launch_apply_p<P16>(lat, out, in, kind, stream);
     }
 }
 
 cudaError_t launch_copy(wc_lattice lat, wc_field dst, wc_field src, double scale, const double *dev_scale,
-                        int invert_scale)
+                        int invert_scale, cudaStream_t stream)
 {
     switch (src->prec) {
-    case WC_F64: return launch_copy_s<P64>(lat, dst, src, scale, dev_scale, invert_scale);
-    case WC_F32: return launch_copy_s<P32>(lat, dst, src, scale, dev_scale, invert_scale);
-    default: return launch_copy_s<P16>(lat, dst, src, scale, dev_scale, invert_scale);
+    case WC_F64: return launch_copy_s<P64>(lat, dst, src, scale, dev_scale, invert_scale, stream);
+    case WC_F32: return launch_copy_s<P32>(lat, dst, src, scale, dev_scale, invert_scale, stream);
+    default: return launch_copy_s<P16>(lat, dst, src, scale, dev_scale, invert_scale, stream);
     }
 }
 

@@ -26,12 +26,11 @@
 #include <math.h>
 
 #include "wc_internal.cuh"
+#include "wc_solver.cuh"
 #include "wc_solver_kernels.cuh"
 
 namespace wc {
 
-wc_status bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p, wc_solve_info *info);
-wc_status check_solve_args(wc_lattice lat, wc_field x, wc_field b, const wc_solve_params *p);
 
 namespace {
 

@@ -362,6 +362,22 @@ int sm_count();
 // handle definitions
 // ------------------------------------------------------------------------
 
+namespace wc {
+
+// Per-solve state: device scalars and their pinned host mirror, reduction
+// scratch, solver work fields (created on first use: slots 0-9 FP64, 10-11
+// FP32, 12-13 FP16) and the stream the solve is queued on.  A lattice owns
+// one for its single-RHS calls; a batched solve creates one per RHS.
+struct SolverState {
+    SolverScalars *scal = nullptr;
+    SolverScalars *scal_host = nullptr;
+    ReduceScratch red;
+    wc_field_s *work[16] = {};
+    cudaStream_t stream = nullptr;
+};
+
+}  // namespace wc
+
 struct wc_lattice_s {
     wc::Geom g{};
     cudaStream_t stream = nullptr;
@@ -370,14 +386,9 @@ struct wc_lattice_s {
     double csw = 0.0, kappa = 0.0;
     wc::GaugeStore gauge;
     wc::CloverStore clover;
-    wc::ReduceScratch red;
-    wc::SolverScalars *scal = nullptr;        // device
-    wc::SolverScalars *scal_host = nullptr;   // pinned mirror
+    wc::SolverState st;                       // scratch of single-RHS calls
     double2 *staging = nullptr;               // canonical-size device buffer
     size_t staging_bytes = 0;
-    // solver work fields, created on first use: slots 0-9 FP64,
-    // 10-11 FP32, 12-13 FP16
-    wc_field_s *work[16] = {};
     std::string err;
 };
 
@@ -397,13 +408,20 @@ inline size_t spinor_bytes(wc_prec p, int V)
                        : (size_t)V * 3 * sizeof(uint4);
 }
 
-// launchers implemented in the .cu files
-cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind /*0 M, 1 Mdag, 2 H*/);
-cudaError_t launch_copy(wc_lattice lat, wc_field dst, wc_field src, double scale,
-                        const double *dev_scale, int invert_scale);
-cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params &p, int dagger);
+// launchers implemented in the .cu files (all asynchronous on `stream`)
+cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind /*0 M, 1 Mdag, 2 H*/,
+                         cudaStream_t stream);
+cudaError_t launch_copy(wc_lattice lat, wc_field dst, wc_field src, double scale, const double *dev_scale,
+                        int invert_scale, cudaStream_t stream);
+cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params &p, int dagger,
+                       cudaStream_t stream);
 
-// reductions over FP64 or FP32 fields (blocking variants return on host)
+// solver states
+wc_status state_init(wc_lattice lat, SolverState &s);
+void state_free(SolverState &s);
+wc_field state_work(wc_lattice lat, SolverState &s, int slot, wc_prec prec, wc_status *st);
+
+// reductions over fields of any precision (blocking, on the lattice's stream)
 wc_status reduce_dot(wc_lattice lat, wc_field a, wc_field b, double out[2]);
 wc_status reduce_norm2(wc_lattice lat, wc_field a, double *out);
 wc_status axpy_norm(wc_lattice lat, const double a[2], wc_field x, wc_field y, double *norm2);

@@ -19,9 +19,9 @@
 // is parked in shared memory and the q of its second stays in registers
 // across the block-wide reduction of <q, r> and <q, q> (4^4 blocks with
 // overlap 1: 1296 sites, 672 threads, 211 KB of shared memory, one CTA per
-// SM).  Per-thread partial sums are FP32 (two sites); only the sums over
-// lanes and warps are FP64, which keeps the FP64 pipe -- 1/64 of the FP32
-// rate on GB300 -- out of the inner loop.  Links and clover are read from
+// SM).  <q, r> and <q, q> are summed in FP32 within warps and in FP64 over
+// the warps by a single thread, which keeps the FP64 pipe -- 1/64 of the
+// FP32 rate on GB300 -- out of the inner loop.  Links and clover are read from
 // global memory (L2-resident across the k sweeps of a block).  Arithmetic is
 // FP32 for FP32 and FP16 storage.
 #include "wc_internal.cuh"
@@ -45,26 +45,32 @@ struct RasGeom {
     int k;          // MR iterations
 };
 
-// Block sum of three per-thread FP32 partials, lanes and warps in FP64, the
-// warp partials added in a fixed order so every thread gets the same result.
-__device__ __forceinline__ void block_sum3(const float vf[3], double *sm /*[32*3]*/, double out[3])
+// alpha = <q, r> / <q, q> from per-thread FP32 partials: lanes are summed
+// in FP32, the warp sums in FP64 by one thread, which also divides and
+// broadcasts alpha (FP32) through shared memory.  On GB300 the FP64 pipe
+// runs at 1/64 of the FP32 rate, so no other thread touches FP64.
+__device__ __forceinline__ cx<float> block_alpha(const float v[3], double *sm /*[32*3]*/, float2 *bcast)
 {
-    double v[3] = {vf[0], vf[1], vf[2]};
+    float w[3] = {v[0], v[1], v[2]};
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+        for (int o = 16; o > 0; o >>= 1) w[i] += __shfl_down_sync(0xffffffffu, w[i], o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) sm[wid * 3 + i] = v[i];
+        for (int i = 0; i < 3; ++i) sm[wid * 3 + i] = (double)w[i];
     __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < nw; ++k)
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        double t = 0.0;
-        for (int w = 0; w < nw; ++w) t += sm[w * 3 + i];
-        out[i] = t;
+            for (int i = 0; i < 3; ++i) t[i] += sm[k * 3 + i];
+        *bcast = t[2] > 0.0 ? make_float2((float)(t[0] / t[2]), (float)(t[1] / t[2])) : make_float2(0.f, 0.f);
     }
+    __syncthreads();
+    const float2 a = *bcast;
+    return mkc(a.x, a.y);
 }
 
 // q += -kappa * (forward and backward hop in direction MU), both dropped
@@ -115,6 +121,7 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
     float2 *qs = r + 12 * rg.ne;                                     // [12][blockDim.x]
     float2 *xc = qs + 12 * blockDim.x;                               // [12][ncore]
     __shared__ double red[32 * 3];
+    __shared__ float2 alpha_bcast;
 
     // block origin
     int bc[4];
@@ -212,11 +219,8 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
                 acc[2] = fmaf(q[k].re, q[k].re, fmaf(q[k].im, q[k].im, acc[2]));
             }
         }
-        double tot[3];
-        block_sum3(acc, red, tot);   // contains __syncthreads: every read of r is done
-        const float ar = tot[2] > 0.0 ? (float)(tot[0] / tot[2]) : 0.f;
-        const float ai = tot[2] > 0.0 ? (float)(tot[1] / tot[2]) : 0.f;
-        const cx<float> alpha = mkc(ar, ai);
+        // contains __syncthreads: every read of r is done after it
+        const cx<float> alpha = block_alpha(acc, red, &alpha_bcast);
         // x += alpha r, r -= alpha q on this thread's sites
 #pragma unroll
         for (int j = 0; j < kRasSPT; ++j) {
@@ -287,18 +291,43 @@ bool ras_fits(const wc_ras_params &p)
     return ras_threads(p) <= kRasMaxThreads && ras_smem_bytes(p) <= 226 * 1024;
 }
 
+// The shared-memory opt-in is set once per device and kernel (outside any
+// stream capture that later launches it), to the largest size allowed.
+template <class P, int SF>
+cudaError_t ras_smem_optin()
+{
+    static unsigned long long done_mask = 0;   // bit d: device d
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && (done_mask >> dev) & 1ull) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_ras<P, SF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+    if (e == cudaSuccess && dev < 64) done_mask |= 1ull << dev;
+    return e;
+}
+
 template <class P, int SF>
 cudaError_t launch_ras_k(wc_lattice lat, const RasGeom &rg, int nblocks, int threads, size_t smem, wc_field out,
-                         wc_field in)
+                         wc_field in, cudaStream_t stream)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_ras<P, SF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ras_smem_optin<P, SF>();
     if (e != cudaSuccess) return e;
-    k_ras<P, SF><<<nblocks, threads, smem, lat->stream>>>(lat->g, rg, lat->gauge, lat->clover, in->data, in->nrm,
-                                                          out->data, out->nrm, (float)lat->kappa);
+    k_ras<P, SF><<<nblocks, threads, smem, stream>>>(lat->g, rg, lat->gauge, lat->clover, in->data, in->nrm,
+                                                     out->data, out->nrm, (float)lat->kappa);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params &p, int dagger)
+cudaError_t ras_prepare()
+{
+    cudaError_t e = ras_smem_optin<P32, -1>();
+    if (e == cudaSuccess) e = ras_smem_optin<P32, +1>();
+    if (e == cudaSuccess) e = ras_smem_optin<P16, -1>();
+    if (e == cudaSuccess) e = ras_smem_optin<P16, +1>();
+    return e;
+}
+
+cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params &p, int dagger,
+                       cudaStream_t stream)
 {
     RasGeom rg;
     rg.ne = 1;
@@ -318,10 +347,10 @@ cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_p
     const size_t smem = ras_smem_bytes(p);
     const int threads = ras_threads(p);
     if (in->prec == WC_F16)
-        return dagger ? launch_ras_k<P16, +1>(lat, rg, nblocks, threads, smem, out, in)
-                      : launch_ras_k<P16, -1>(lat, rg, nblocks, threads, smem, out, in);
-    return dagger ? launch_ras_k<P32, +1>(lat, rg, nblocks, threads, smem, out, in)
-                  : launch_ras_k<P32, -1>(lat, rg, nblocks, threads, smem, out, in);
+        return dagger ? launch_ras_k<P16, +1>(lat, rg, nblocks, threads, smem, out, in, stream)
+                      : launch_ras_k<P16, -1>(lat, rg, nblocks, threads, smem, out, in, stream);
+    return dagger ? launch_ras_k<P32, +1>(lat, rg, nblocks, threads, smem, out, in, stream)
+                  : launch_ras_k<P32, -1>(lat, rg, nblocks, threads, smem, out, in, stream);
 }
 
 }  // namespace wc

@@ -25,6 +25,7 @@
 
 #include "wc_internal.cuh"
 #include "wc_solver_kernels.cuh"
+#include "wc_solver.cuh"
 
 namespace wc {
 
@@ -50,141 +51,166 @@ wc_status check_ras_params(wc_lattice lat, const wc_ras_params *p)
 
 namespace {
 
-wc_field work_field(wc_lattice lat, int slot, wc_prec prec, wc_status *st)
-{
-    if (!lat->work[slot]) {
-        *st = wc_field_create(lat, prec, &lat->work[slot]);
-        if (*st != WC_OK) return nullptr;
-    }
-    *st = WC_OK;
-    return lat->work[slot];
-}
-
 double2 *d2(wc_field f) { return static_cast<double2 *>(f->data); }
-
-wc_status read_scalars(wc_lattice lat)
-{
-    wc_status st = check_cuda(lat,
-                              cudaMemcpyAsync(lat->scal_host, lat->scal, sizeof(SolverScalars),
-                                              cudaMemcpyDeviceToHost, lat->stream),
-                              "cudaMemcpyAsync(scalars)");
-    if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync(scalars)");
-    return st;
-}
-
-struct Precond {
-    wc_precond kind = WC_PRECOND_NONE;
-    wc_ras_params ras{};
-    wc_field lo_in = nullptr, lo_out = nullptr;   // inner-precision fields
-    int dagger = 0;
-};
-
-// uhat = K^-1 u.  norm2_dev: |u|^2 on the device (written by the update kernel).
-wc_status apply_precond(wc_lattice lat, const Precond &K, wc_field u, wc_field uhat, const double *norm2_dev)
-{
-    if (K.kind == WC_PRECOND_NONE) return WC_OK;   // callers use u itself
-    wc_status st = check_cuda(lat, launch_copy(lat, K.lo_in, u, 1.0, norm2_dev, 1), "defect cast down");
-    if (st == WC_OK) st = check_cuda(lat, launch_ras(lat, K.lo_out, K.lo_in, K.ras, K.dagger), "ras");
-    if (st == WC_OK) st = check_cuda(lat, launch_copy(lat, uhat, K.lo_out, 1.0, norm2_dev, 0), "defect cast up");
-    return st;
-}
 
 }  // namespace
 
-// Solve op x = b (op = M for kind 0, M^+ for kind 1); x, b FP64 fields.
-static wc_status bicgstab_impl(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p,
-                               wc_solve_info *info);
-
-wc_status bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p, wc_solve_info *info)
+wc_status read_scalars(wc_lattice lat, SolverState &S)
 {
-    wc_solve_info local{};
-    local.status = WC_ERR_CUDA;
-    wc_solve_info *out = info ? info : &local;
-    *out = local;
-    const wc_status st = bicgstab_impl(lat, kind, x, b, p, out);
-    if (st != WC_OK && out->status == WC_OK) out->status = st;
-    if (st != WC_OK && out->status == WC_ERR_CUDA && st != WC_ERR_CUDA) out->status = st;
+    wc_status st = check_cuda(lat,
+                              cudaMemcpyAsync(S.scal_host, S.scal, sizeof(SolverScalars), cudaMemcpyDeviceToHost,
+                                              S.stream),
+                              "cudaMemcpyAsync(scalars)");
+    if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(S.stream), "sync(scalars)");
     return st;
 }
 
-static wc_status bicgstab_impl(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p,
-                               wc_solve_info *info)
+wc_status solver_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &p, SolverVecs *w)
+{
+    wc_status st = WC_OK;
+    w->r = state_work(lat, S, 0, WC_F64, &st);
+    if (st == WC_OK) w->rhat = state_work(lat, S, 1, WC_F64, &st);
+    if (st == WC_OK) w->p = state_work(lat, S, 2, WC_F64, &st);
+    if (st == WC_OK) w->v = state_work(lat, S, 3, WC_F64, &st);
+    if (st == WC_OK) w->s = state_work(lat, S, 4, WC_F64, &st);
+    if (st == WC_OK) w->t = state_work(lat, S, 5, WC_F64, &st);
+    w->phat = w->p;
+    w->shat = w->s;
+    w->lo_in = w->lo_out = nullptr;
+    if (st == WC_OK && p.precond == WC_PRECOND_RAS) {
+        w->phat = state_work(lat, S, 6, WC_F64, &st);
+        if (st == WC_OK) w->shat = state_work(lat, S, 7, WC_F64, &st);
+        const int lo = p.inner_prec == WC_F16 ? 12 : 10;
+        if (st == WC_OK) w->lo_in = state_work(lat, S, lo, p.inner_prec, &st);
+        if (st == WC_OK) w->lo_out = state_work(lat, S, lo + 1, p.inner_prec, &st);
+    }
+    return st;
+}
+
+// uhat = K^-1 u = |u| RAS(u / |u|); norm2_dev: |u|^2 on the device
+static wc_status apply_precond(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind,
+                               const SolverVecs &w, wc_field u, wc_field uhat, const double *norm2_dev)
+{
+    if (p.precond == WC_PRECOND_NONE) return WC_OK;   // uhat aliases u
+    wc_status st = check_cuda(lat, launch_copy(lat, w.lo_in, u, 1.0, norm2_dev, 1, S.stream), "defect cast down");
+    if (st == WC_OK) st = check_cuda(lat, launch_ras(lat, w.lo_out, w.lo_in, p.ras, kind, S.stream), "ras");
+    if (st == WC_OK)
+        st = check_cuda(lat, launch_copy(lat, uhat, w.lo_out, 1.0, norm2_dev, 0, S.stream), "defect cast up");
+    return st;
+}
+
+wc_status enqueue_init(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, const SolverVecs &w)
+{
+    wc_status st = check_cuda(lat, launch_apply(lat, w.r, x, kind, S.stream), "apply");
+    if (st == WC_OK)
+        st = check_cuda(lat, bicg_init(lat, S, d2(b), d2(w.r), d2(w.rhat), d2(w.p), d2(w.v)), "bicg_init");
+    return st;
+}
+
+wc_status enqueue_iteration(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind, wc_field x,
+                            const SolverVecs &w)
+{
+    wc_status st = check_cuda(lat, bicg_p(lat, S, d2(w.r), d2(w.v), d2(w.p)), "bicg_p");
+    if (st == WC_OK) st = apply_precond(lat, S, p, kind, w, w.p, w.phat, &S.scal->pp);
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.v, w.phat, kind, S.stream), "apply");
+    if (st == WC_OK) st = check_cuda(lat, bicg_alpha(lat, S, d2(w.rhat), d2(w.v)), "bicg_alpha");
+    if (st == WC_OK) st = check_cuda(lat, bicg_s(lat, S, d2(w.r), d2(w.v), d2(w.s)), "bicg_s");
+    if (st == WC_OK) st = apply_precond(lat, S, p, kind, w, w.s, w.shat, &S.scal->ss);
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.t, w.shat, kind, S.stream), "apply");
+    if (st == WC_OK) st = check_cuda(lat, bicg_omega(lat, S, d2(w.t), d2(w.s)), "bicg_omega");
+    if (st == WC_OK)
+        st = check_cuda(lat, bicg_xr(lat, S, d2(x), d2(w.phat), d2(w.shat), d2(w.s), d2(w.t), d2(w.r), d2(w.rhat)),
+                        "bicg_xr");
+    return st;
+}
+
+wc_status enqueue_true_residual(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
+                                const SolverVecs &w)
+{
+    wc_status st = check_cuda(lat, launch_apply(lat, w.r, x, kind, S.stream), "apply");
+    if (st == WC_OK) st = check_cuda(lat, residual(lat, S, d2(b), d2(w.r)), "residual");
+    return st;
+}
+
+static wc_status bicgstab_impl(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
+                               const wc_solve_params &p, double bb, wc_solve_info *info, int iters_done);
+
+// Solve op x = b (op = M for kind 0, M^+ for kind 1); x, b FP64 fields.
+// S: solver state (scratch); S.stream: the stream everything is queued on.
+wc_status bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, const wc_solve_params &p,
+                   wc_solve_info *info, int iters_done, double bb)
+{
+    wc_solve_info local{};
+    wc_solve_info *out = info ? info : &local;
+    *out = wc_solve_info{};
+    out->status = WC_ERR_CUDA;
+    const wc_status st = bicgstab_impl(lat, S, kind, x, b, p, bb, out, iters_done);
+    if (st != WC_OK && (out->status == WC_OK || out->status == WC_ERR_CUDA)) out->status = st;
+    return st;
+}
+
+wc_status bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p, wc_solve_info *info)
+{
+    lat->st.stream = lat->stream;
+    return bicgstab(lat, lat->st, kind, x, b, p, info, 0, -1.0);
+}
+
+static wc_status bicgstab_impl(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
+                               const wc_solve_params &p, double bb, wc_solve_info *info, int iters_done)
 {
     auto t0 = std::chrono::steady_clock::now();
-    wc_solve_info inf{};
+    wc_solve_info &inf = *info;
+    inf.iters = iters_done;
     inf.status = WC_ERR_NOT_CONVERGED;
-    wc_status st = WC_OK;
-    wc_field r = work_field(lat, 0, WC_F64, &st);
-    wc_field rhat = st == WC_OK ? work_field(lat, 1, WC_F64, &st) : nullptr;
-    wc_field pv = st == WC_OK ? work_field(lat, 2, WC_F64, &st) : nullptr;
-    wc_field v = st == WC_OK ? work_field(lat, 3, WC_F64, &st) : nullptr;
-    wc_field s = st == WC_OK ? work_field(lat, 4, WC_F64, &st) : nullptr;
-    wc_field t = st == WC_OK ? work_field(lat, 5, WC_F64, &st) : nullptr;
-    Precond K;
-    K.kind = p.precond;
-    K.ras = p.ras;
-    K.dagger = kind;
-    wc_field phat = pv, shat = s;
-    if (st == WC_OK && K.kind == WC_PRECOND_RAS) {
-        phat = work_field(lat, 6, WC_F64, &st);
-        if (st == WC_OK) shat = work_field(lat, 7, WC_F64, &st);
-        const int lo = p.inner_prec == WC_F16 ? 12 : 10;
-        if (st == WC_OK) K.lo_in = work_field(lat, lo, p.inner_prec, &st);
-        if (st == WC_OK) K.lo_out = work_field(lat, lo + 1, p.inner_prec, &st);
+    SolverVecs w;
+    wc_status st = solver_vectors(lat, S, p, &w);
+    if (st != WC_OK) return st;
+    if (bb < 0.0) {
+        st = check_cuda(lat, norm2_to_result(lat, S, d2(b)), "norm2");
+        if (st == WC_OK)
+            st = check_cuda(lat,
+                            cudaMemcpyAsync(S.red.host_result, S.red.result, sizeof(double), cudaMemcpyDeviceToHost,
+                                            S.stream),
+                            "cudaMemcpyAsync(norm)");
+        if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(S.stream), "sync(norm)");
+        if (st != WC_OK) return st;
+        bb = S.red.host_result[0];
     }
-    if (st != WC_OK) return st;
-
-    double bb = 0.0;
-    st = reduce_norm2(lat, b, &bb);
-    if (st != WC_OK) return st;
     if (!isfinite(bb)) {
         inf.status = WC_ERR_NAN;
-        if (info) *info = inf;
         return set_error(lat, WC_ERR_NAN, "source has non-finite entries");
     }
     if (bb == 0.0) {
-        st = check_cuda(lat, cudaMemsetAsync(x->data, 0, spinor_bytes(WC_F64, lat->g.V), lat->stream), "memset");
-        inf.status = WC_OK;
+        st = check_cuda(lat, cudaMemsetAsync(x->data, 0, spinor_bytes(WC_F64, lat->g.V), S.stream), "memset");
+        if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(S.stream), "sync");
+        inf.status = st;
         inf.true_rel_resid = 0.0;
-        if (info) *info = inf;
         return st;
     }
     const double tol2 = p.tol * p.tol * bb;
-    const int apply_kind = kind;   // 0: M, 1: M^+
     wc_status result = WC_ERR_NOT_CONVERGED;
 
     for (int restart = 0; restart <= p.max_restarts; ++restart) {
         inf.restarts = restart;
-        // r = b - op x
-        st = check_cuda(lat, launch_apply(lat, r, x, apply_kind), "apply");
-        if (st == WC_OK) st = check_cuda(lat, bicg_init(lat, d2(b), d2(r), d2(rhat), d2(pv), d2(v)), "bicg_init");
-        if (st == WC_OK) st = read_scalars(lat);
+        st = enqueue_init(lat, S, kind, x, b, w);
+        if (st == WC_OK) st = read_scalars(lat, S);
         if (st != WC_OK) return st;
-        if (lat->scal_host->flags & FLAG_NAN) {
+        if (S.scal_host->flags & FLAG_NAN) {
             result = set_error(lat, WC_ERR_NAN, "non-finite residual");
             break;
         }
-        if (lat->scal_host->rr <= tol2) {
+        inf.true_rel_resid = sqrt(S.scal_host->rr / bb);
+        if (S.scal_host->rr <= tol2) {
             result = WC_OK;
             break;
         }
         bool breakdown = false;
         while (inf.iters < p.max_iter) {
-            st = check_cuda(lat, bicg_p(lat, d2(r), d2(v), d2(pv)), "bicg_p");
-            if (st == WC_OK) st = apply_precond(lat, K, pv, phat, &lat->scal->pp);
-            if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, v, phat, apply_kind), "apply");
-            if (st == WC_OK) st = check_cuda(lat, bicg_alpha(lat, d2(rhat), d2(v)), "bicg_alpha");
-            if (st == WC_OK) st = check_cuda(lat, bicg_s(lat, d2(r), d2(v), d2(s)), "bicg_s");
-            if (st == WC_OK) st = apply_precond(lat, K, s, shat, &lat->scal->ss);
-            if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, t, shat, apply_kind), "apply");
-            if (st == WC_OK) st = check_cuda(lat, bicg_omega(lat, d2(t), d2(s)), "bicg_omega");
-            if (st == WC_OK)
-                st = check_cuda(lat, bicg_xr(lat, d2(x), d2(phat), d2(shat), d2(s), d2(t), d2(r), d2(rhat)),
-                                "bicg_xr");
-            if (st == WC_OK) st = read_scalars(lat);
+            st = enqueue_iteration(lat, S, p, kind, x, w);
+            if (st == WC_OK) st = read_scalars(lat, S);
             if (st != WC_OK) return st;
             ++inf.iters;
-            const SolverScalars &h = *lat->scal_host;
+            const SolverScalars &h = *S.scal_host;
             if (h.flags & FLAG_NAN) {
                 result = set_error(lat, WC_ERR_NAN, "non-finite value in BiCGStab");
                 break;
@@ -196,17 +222,15 @@ static wc_status bicgstab_impl(wc_lattice lat, int kind, wc_field x, wc_field b,
             }
         }
         if (result == WC_ERR_NAN) break;
-        // true residual in FP64
-        st = check_cuda(lat, launch_apply(lat, r, x, apply_kind), "apply");
-        if (st == WC_OK) st = check_cuda(lat, residual(lat, d2(b), d2(r)), "residual");
-        if (st == WC_OK) st = read_scalars(lat);
+        st = enqueue_true_residual(lat, S, kind, x, b, w);
+        if (st == WC_OK) st = read_scalars(lat, S);
         if (st != WC_OK) return st;
-        inf.true_rel_resid = sqrt(lat->scal_host->rr / bb);
+        inf.true_rel_resid = sqrt(S.scal_host->rr / bb);
         if (!isfinite(inf.true_rel_resid)) {
             result = set_error(lat, WC_ERR_NAN, "non-finite true residual");
             break;
         }
-        if (lat->scal_host->rr <= tol2) {
+        if (S.scal_host->rr <= tol2) {
             result = WC_OK;
             break;
         }
@@ -214,20 +238,11 @@ static wc_status bicgstab_impl(wc_lattice lat, int kind, wc_field x, wc_field b,
             result = set_error(lat, WC_ERR_NOT_CONVERGED, "max_iter reached");
             break;
         }
-        if (breakdown && restart == p.max_restarts) {
-            result = set_error(lat, WC_ERR_BREAKDOWN, "BiCGStab breakdown");
-            break;
-        }
         result = set_error(lat, breakdown ? WC_ERR_BREAKDOWN : WC_ERR_NOT_CONVERGED,
                            breakdown ? "BiCGStab breakdown" : "true residual above tol after all restarts");
     }
-    if (result == WC_OK && inf.true_rel_resid == 0.0) {
-        // converged at the initial residual check: report it
-        inf.true_rel_resid = sqrt(lat->scal_host->rr / bb);
-    }
     inf.status = result;
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (info) *info = inf;
     return result;
 }
 
@@ -291,7 +306,7 @@ wc_status wc_ras_precond(wc_lattice lat, wc_field out, wc_field in, const wc_ras
     wc_status st = check_ras_params(lat, p);
     if (st != WC_OK) return st;
     if (!lat->gauge_loaded || !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "gauge/clover not loaded");
-    return check_cuda(lat, launch_ras(lat, out, in, *p, 0), "ras");
+    return check_cuda(lat, launch_ras(lat, out, in, *p, 0, lat->stream), "ras");
 }
 
 wc_status wc_solve_bicgstab(wc_lattice lat, wc_field x, wc_field b, const wc_solve_params *p, wc_solve_info *info)

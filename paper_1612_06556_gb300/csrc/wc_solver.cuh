@@ -1,0 +1,40 @@
+// BiCGStab building blocks shared by the single-RHS solve, the batched
+// graph-captured solve and the action/force call (wc_solver.cu).
+#pragma once
+
+#include "wc_internal.cuh"
+
+namespace wc {
+
+// FP64 work vectors of one solve (phat/shat alias p/s without a
+// preconditioner) and the two inner-precision fields of the RAS defect
+// correction.
+struct SolverVecs {
+    wc_field r, rhat, p, v, s, t, phat, shat, lo_in, lo_out;
+};
+
+wc_status check_ras_params(wc_lattice lat, const wc_ras_params *p);
+wc_status check_solve_args(wc_lattice lat, wc_field x, wc_field b, const wc_solve_params *p);
+wc_status solver_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &p, SolverVecs *w);
+wc_status read_scalars(wc_lattice lat, SolverState &S);
+
+// Queue (no host synchronisation) on S.stream:
+//   init: r = b - op x, rhat = r, p = v = 0, scalars reset
+//   iteration: one flexible BiCGStab step, scalars updated on the device
+//   true residual: r = b - op x, S.scal->rr = |r|^2
+wc_status enqueue_init(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, const SolverVecs &w);
+wc_status enqueue_iteration(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind, wc_field x,
+                            const SolverVecs &w);
+wc_status enqueue_true_residual(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
+                                const SolverVecs &w);
+
+// Host-driven solve of op x = b (kind 0: M, 1: M^+) with state S, counting
+// iters_done iterations already spent; bb = |b|^2 or < 0 to compute it.
+wc_status bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, const wc_solve_params &p,
+                   wc_solve_info *info, int iters_done, double bb);
+// Same with the lattice's own state and stream.
+wc_status bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p, wc_solve_info *info);
+
+cudaError_t ras_prepare();
+
+}  // namespace wc

@@ -59,3 +59,34 @@ def test_force_finite_differences_16x16x16x32():
         fd = (Ss[0] - Ss[1]) / (2 * h)
         an = np.real(np.einsum("lij,lji->", Lam.reshape(-1, 3, 3), F.reshape(-1, 3, 3)))
         assert abs(fd - an) <= 1e-5 * abs(an) + 1e-9 * S0, (fd, an)
+
+
+def test_autograd_gradient_matches_oracle_and_tangent_derivative():
+    """torch.autograd through the action: U.grad = -F U with the oracle's F,
+    and the directional derivative along exp(h L) U matches finite
+    differences of the forward."""
+    import torch
+    w = wc()
+    dims, kappa, csw, tbc = (4, 4, 4, 8), 0.12, 1.0, -1
+    U = synth.exp_links(dims, 0.3, 91)
+    phi = synth.gaussian_source(dims, 92)
+    lat = w.Lattice(dims, tbc)
+    Ut = torch.from_numpy(U).cuda().requires_grad_(True)
+    pt = torch.from_numpy(phi).cuda()
+    S = w.pseudofermion_action(Ut, pt, lat, csw, kappa, tol=1e-13)
+    S.backward()
+    op = oracle.Operator(dims, U, csw, kappa, tbc)
+    S_ref, F_ref, _, _ = oracle.action_and_force(op, phi, tol=1e-14)
+    assert abs(S.item() - S_ref) <= 1e-11 * S_ref
+    g = Ut.grad.cpu().numpy()
+    assert np.max(np.abs(g + F_ref @ U)) <= 1e-9 * np.max(np.abs(F_ref))
+    rng = np.random.default_rng(93)
+    Lam = synth.random_su3_algebra((synth.volume(dims), 4), rng)
+    h = 1e-5
+    Sp = w.pseudofermion_action(torch.from_numpy(_expm_antiherm(h * Lam) @ U).cuda(), pt, lat, csw, kappa,
+                                tol=1e-13).item()
+    Sm = w.pseudofermion_action(torch.from_numpy(_expm_antiherm(-h * Lam) @ U).cuda(), pt, lat, csw, kappa,
+                                tol=1e-13).item()
+    fd = (Sp - Sm) / (2 * h)
+    an = np.real(np.sum(np.conj(g) * (Lam @ U)))
+    assert abs(fd - an) <= 1e-6 * abs(an) + 1e-10 * S_ref

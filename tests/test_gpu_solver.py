@@ -133,22 +133,71 @@ def test_solver_error_paths():
     assert info.status == 0 and np.count_nonzero(x.store(np.zeros_like(src))) == 0
 
 
-def test_batch_solve_uneven_lattices():
-    w = wc()
+def _batch_problem(w, dims_list, nrhs, csw=1.0, kappa=0.124):
     lats, xs, bs, srcs, ops = [], [], [], [], []
-    for i, dims in enumerate([(6, 6, 6, 8), (8, 8, 8, 8), (8, 6, 8, 12)]):
+    for i, dims in enumerate(dims_list):
         U = synth.exp_links(dims, 0.3, 1100 + 10 * i)
-        lat = make_lattice(dims, U, 1.0, 0.124, -1)
-        for spin in range(2):
-            src = synth.point_source(dims, spin=spin, colour=i % 3)
+        lat = make_lattice(dims, U, csw, kappa, -1)
+        for k in range(nrhs):
+            src = synth.point_source(dims, spin=k % 4, colour=(k // 4) % 3)
             lats.append(lat)
             xs.append(lat.field(0))
             bs.append(lat.field(0).load(src))
             srcs.append(src)
             ops.append((dims, U))
+    return lats, xs, bs, srcs, ops
+
+
+def test_batch_solve_uneven_lattices():
+    """One graph launch over 3 uneven lattices x 3 point sources each; every
+    solution checked against the oracle's M, and against the single-RHS
+    solver's solution."""
+    w = wc()
+    lats, xs, bs, srcs, ops = _batch_problem(w, [(6, 6, 6, 8), (8, 8, 8, 8), (8, 6, 8, 12)], 3)
     infos = w.solve_batch(lats, xs, bs, tol=1e-10, precond=w.PRECOND_RAS, inner_prec=1, block=(2, 2, 2, 2))
-    for info, x, src, (dims, U) in zip(infos, xs, srcs, ops):
+    for info, lat, x, b, src, (dims, U) in zip(infos, lats, xs, bs, srcs, ops):
+        assert info.status == 0 and info.true_rel_resid <= 1e-10
+        sol = x.store(np.zeros_like(src))
+        r = src - oracle.apply_M(dims, -1, 0.124, 1.0, U, sol)
+        assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+        x1 = lat.field(0)
+        lat.solve(x1, b, tol=1e-10, precond=w.PRECOND_RAS, inner_prec=1, block=(2, 2, 2, 2))
+        assert rel_err(sol, x1.store(np.zeros_like(src))) <= 1e-8
+
+
+def test_batch_solve_plain_fp64_and_autotuned_ras():
+    w = wc()
+    lats, xs, bs, srcs, ops = _batch_problem(w, [(8, 8, 8, 16), (16, 8, 8, 8)], 2)
+    infos = w.solve_batch(lats, xs, bs, tol=1e-11)
+    assert all(i.status == 0 and i.true_rel_resid <= 1e-11 for i in infos)
+    xs2 = [lat.field(0) for lat in lats]
+    infos2 = w.solve_batch(lats, xs2, bs, tol=1e-10, precond=w.PRECOND_RAS, inner_prec=2, block=(0, 0, 0, 0))
+    for info, x, src, (dims, U) in zip(infos2, xs2, srcs, ops):
         assert info.status == 0
         sol = x.store(np.zeros_like(src))
         r = src - oracle.apply_M(dims, -1, 0.124, 1.0, U, sol)
         assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+    blk, ov, k = lats[0].ras_autotune(bs[0], inner_prec=2)
+    assert np.prod(blk) >= 128 and all(d % b == 0 for d, b in zip(lats[0].dims, blk)) and ov == 1 and k == 4
+
+
+def test_batch_solve_masks_and_errors():
+    """A zero source, an already-solved RHS and an iteration cap in one batch."""
+    w = wc()
+    dims = (8, 8, 8, 8)
+    U = synth.exp_links(dims, 0.3, 77)
+    lat = make_lattice(dims, U, 1.0, 0.12, -1)
+    src = synth.gaussian_source(dims, 78)
+    zero = np.zeros_like(src)
+    xs = [lat.field(0) for _ in range(3)]
+    bs = [lat.field(0).load(src), lat.field(0).load(zero), lat.field(0).load(src)]
+    lat.solve(xs[2], bs[2], tol=1e-12)
+    infos = w.solve_batch([lat] * 3, xs, bs, tol=1e-10)
+    assert [i.status for i in infos] == [0, 0, 0]
+    assert infos[1].iters == 0 and infos[2].iters == 0 and infos[0].iters > 0
+    assert np.count_nonzero(xs[1].store(np.zeros_like(src))) == 0
+    xs = [lat.field(0) for _ in range(2)]
+    infos = w.solve_batch([lat] * 2, xs, [bs[0], bs[2]], tol=1e-12, max_iter=2, check=False)
+    assert [i.status for i in infos] == [4, 4] and [i.iters for i in infos] == [2, 2]
+    with pytest.raises(w.WCError):
+        w.solve_batch([lat, lat], [xs[0], xs[0]], [bs[0], bs[2]], tol=1e-10)
