@@ -124,6 +124,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def reduce_max(x: float, world: int, device: str = "cuda") -> float:
+    """Max of x over all ranks (all_reduce MAX); x itself when world == 1."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Throughput of the whole job: every rank's units over the slowest
+    rank's time (weak scaling: each rank runs its own replica)."""
+    return units_per_rank * world / (max_ms * 1e-3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -222,12 +239,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, "cuda")
 
     for i in range(args.warmup):
         lat.apply_M(outs[i % nring], ins[i % nring])
@@ -260,11 +272,15 @@ def run_ours(args, world, rank, local):
         e2e_ms = max_over_ranks(1000 * (time.perf_counter() - t0) / args.e2e_steps)
         solve = solve_comparison(wc, lat, src, args) if not args.skip_solves else None
     clk = clocks.summary()
+    shape = lat.apply_shape(wc.F32, 0)
+    mdag_ms = time_applies(lat, outs, ins, "Mdag", 500, stream)
+    large = large_lattice(wc, args) if not args.skip_large else None
+    batch = batch_comparison(wc, args) if not args.skip_batch else None
+    force = force_timing(wc, args) if not args.skip_force else None
 
     per_launch_ms = ms / args.steps
     flops = FLOPS_PER_SITE * V
-    gflops_rank = flops / (per_launch_ms * 1e-3) / 1e9
-    value = gflops_rank * world
+    value = whole_job_rate(flops, world, per_launch_ms) / 1e9
     peak, peak_kind = measured_peaks()
     bytes_alg = BYTES_PER_SITE["f32"] * V
     achieved = bytes_alg / (per_launch_ms * 1e-3) / 1e9
@@ -281,11 +297,12 @@ def run_ours(args, world, rank, local):
         "config": {"workload": "Wilson-Clover M apply, 24^3x32, FP32 storage and arithmetic, csw=1.0, "
                                "kappa=0.125, antiperiodic t",
                    "lattice": list(dims), "l2": "inputs 297 MB per step > 129 MB L2; 4 rotating field pairs",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}",
+                   "launch_shape": {"threads": shape[0], "tile": list(shape[1]), "reg_capped": shape[2]}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_apply<P32, M>",
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_alg},
-        "e2e": {"value": flops * world / (e2e_ms * 1e-3) / 1e9, "unit": "GFlop/s",
+        "e2e": {"value": whole_job_rate(flops, world, e2e_ms) / 1e9, "unit": "GFlop/s",
                 "h2d_bytes_per_step": V * 12 * 16, "d2h_bytes_per_step": V * 12 * 16,
                 "ms_per_step": e2e_ms},
         "gpu_launches": args.steps,
@@ -293,12 +310,153 @@ def run_ours(args, world, rank, local):
     }
     if solve is not None:
         line["solve"] = solve
+    line["apply_mdag"] = {"ms": mdag_ms, "gflops": flops / (mdag_ms * 1e-3) / 1e9,
+                          "roofline_frac": bytes_alg / (mdag_ms * 1e-3) / 1e9 / peak}
+    if large is not None:
+        line["large_32x32x32x64"] = large
+    if batch is not None:
+        line["batch"] = batch
+    if force is not None:
+        line["force"] = force
     if world == 1 and not args.skip_cpu:
         smp = OracleSampler(dims, U, src, csw, kappa, tbc, args.ref_seconds)
         g, dt = smp.step()
         line["cpu_baseline"] = {"value": g, "unit": "GFlop/s", "cores": smp.cores, "kind": "oracle",
                                 "sample": smp.describe(dt)}
     print(json.dumps(line), flush=True)
+
+
+def batch_comparison(wc, args):
+    """36 right-hand sides (12 spin-colour point sources on each of
+    24^3x48, 16^3x32 and 32^3x32, each lattice with its own exp(0.3 iH)
+    gauge field) to 1e-10 with FP32 RAS (block shapes from the autotuner):
+    one graph-launched batch (reliable-update solver; also the flexible FP64
+    outer solver) vs 36 sequential solves on the same GPU."""
+    import synth
+    cfg = synth.CONFIGS[4]
+    lats, bs, srcs = [], [], []
+    for i, dims in enumerate(cfg["dims"]):
+        U = synth.gauge_for(cfg["gauge"], dims, 1100 + 10 * i)
+        lat = wc.Lattice(dims, cfg["tbc"]).load_gauge(U).load_clover(cfg["csw"], cfg["kappa"])
+        del U
+        for spin in range(4):
+            for colour in range(3):
+                lats.append(lat)
+                bs.append(lat.field(wc.F64).load(synth.point_source(dims, spin, colour)))
+    params = wc.solve_params(tol=1e-10, max_iter=2000, precond=wc.PRECOND_RAS, inner_prec=wc.F32,
+                             block=(0, 0, 0, 0), solver=wc.SOLVER_RELIABLE, delta=0.1)
+    shapes = {}
+    for lat, b in zip(lats[::12], bs[::12]):
+        shapes["x".join(map(str, lat.dims))] = list(lat.ras_autotune(b, params)[0])
+
+    def run_batch(prm):
+        xs = [lat.field(wc.F64) for lat in lats]
+        t0 = time.perf_counter()
+        infos = wc.solve_batch(lats, xs, bs, prm, check=False)
+        dt = time.perf_counter() - t0
+        for x in xs:
+            x.close()
+        return infos, dt
+
+    run_batch(params)                       # warm-up: allocations, launch-shape tuning
+    infos, t_batch = run_batch(params)
+    flex = wc.solve_params(tol=1e-10, max_iter=2000, precond=wc.PRECOND_RAS, inner_prec=wc.F32,
+                           block=(0, 0, 0, 0), solver=wc.SOLVER_FLEXIBLE)
+    infos_flex, t_flex = run_batch(flex)
+    t0 = time.perf_counter()
+    seq = []
+    for lat, b in zip(lats, bs):
+        x = lat.field(wc.F64)
+        blk = shapes["x".join(map(str, lat.dims))]
+        seq.append(lat.solve(x, b, tol=1e-10, max_iter=2000, precond=wc.PRECOND_RAS, inner_prec=wc.F32,
+                             block=blk, solver=wc.SOLVER_RELIABLE, delta=0.1, check=False))
+        x.close()
+    t_seq = time.perf_counter() - t0
+    return {"rhs": len(lats), "lattices": [list(d) for d in cfg["dims"]],
+            "solver": "reliable update (FP32 BiCGStab + FP32 RAS, FP64 refreshes, delta 0.1), tol 1e-10",
+            "batch_seconds": t_batch, "sequential_seconds": t_seq, "speedup_vs_sequential": t_seq / t_batch,
+            "max_true_rel_resid": max(i.true_rel_resid for i in infos),
+            "all_ok": all(i.status == 0 for i in infos),
+            "steps": [min(i.iters for i in infos), max(i.iters for i in infos)],
+            "sequential_all_ok": all(i.status == 0 for i in seq),
+            "flexible_batch_seconds": t_flex, "flexible_all_ok": all(i.status == 0 for i in infos_flex),
+            "flexible_steps": [min(i.iters for i in infos_flex), max(i.iters for i in infos_flex)],
+            "ras_blocks_autotuned": shapes}
+
+
+def time_applies(lat, outs, ins, kind, steps, stream):
+    """Average device time (ms) of `steps` applies rotating over the field
+    pairs, CUDA events on the lattice's stream."""
+    import torch
+    fn = {"M": lat.apply_M, "Mdag": lat.apply_Mdag}[kind]
+    for i in range(3):
+        fn(outs[i % len(outs)], ins[i % len(ins)])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        fn(outs[i % len(outs)], ins[i % len(ins)])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def large_lattice(wc, args):
+    """The 32^3x64 workload (exp(0.25 iH) links, csw 1.6, kappa 0.128,
+    Gaussian source): FP32 and FP16-storage applies with their roofline
+    fractions and sampled errors against the FP64 oracle, and the
+    reliable-update solve with FP16 storage to 1e-10."""
+    import torch
+    import oracle
+    import synth
+    dims, U, src, csw, kappa, tbc = synth.config_inputs(3)
+    V = int(np.prod(dims))
+    stream = torch.cuda.current_stream()
+    lat = wc.Lattice(dims, tbc, stream=stream).load_gauge(U).load_clover(csw, kappa)
+    peak, _ = measured_peaks()
+    out = {"lattice": list(dims)}
+    rng = np.random.default_rng(3)
+    sites = rng.choice(V, 2000, replace=False)
+    ref = oracle.apply_M(dims, tbc, kappa, csw, U, src, sites=sites)
+    for name, prec, bps in (("f32", wc.F32, BYTES_PER_SITE["f32"]), ("f16", wc.F16, BYTES_PER_SITE["f16"])):
+        ins = [lat.field(prec).load(src) for _ in range(2)]
+        outs = [lat.field(prec) for _ in range(2)]
+        ms = time_applies(lat, outs, ins, "M", 200, stream)
+        lat.apply_M(outs[0], ins[0])
+        res = outs[0].store(np.zeros_like(src))[sites]
+        err = float(np.linalg.norm(res - ref) / np.linalg.norm(ref))
+        gbs = bps * V / (ms * 1e-3) / 1e9
+        out["apply_" + name] = {"ms": ms, "gflops": FLOPS_PER_SITE * V / (ms * 1e-3) / 1e9, "algorithmic_gbs": gbs,
+                                "roofline_frac": gbs / peak, "bytes_per_site": bps,
+                                "rel_err_vs_oracle_2000_sites": err}
+        for f in ins + outs:
+            f.close()
+    b = lat.field(wc.F64).load(src)
+    x = lat.field(wc.F64)
+    info = lat.solve(x, b, tol=1e-10, max_iter=5000, precond=wc.PRECOND_RAS, inner_prec=wc.F16,
+                     solver=wc.SOLVER_RELIABLE, delta=0.1, check=False)
+    out["solve_reliable_f16"] = {"seconds": info.seconds, "steps": info.iters,
+                                 "true_rel_resid": info.true_rel_resid,
+                                 "status": wc.STATUS.get(info.status, info.status)}
+    return out
+
+
+def force_timing(wc, args):
+    """S = phi^+ (M^+ M)^-1 phi and its force on 16^3x32 (kappa 0.12,
+    csw 1.0, exp(0.3 iH) links, Gaussian phi): two FP64 flexible BiCGStab
+    solves with FP32 RAS to 1e-12, then the force kernels."""
+    import synth
+    dims, U, phi, csw, kappa, tbc = synth.config_inputs(5)
+    lat = wc.Lattice(dims, tbc).load_gauge(U).load_clover(csw, kappa)
+    f_phi = lat.field(wc.F64).load(phi)
+    F = np.zeros((int(np.prod(dims)), 4, 3, 3), dtype=np.complex128)
+    kw = dict(tol=1e-12, precond=wc.PRECOND_RAS, inner_prec=wc.F32)
+    lat.action_force(f_phi, F, **kw)
+    t0 = time.perf_counter()
+    S = lat.action_force(f_phi, F, **kw)
+    dt = time.perf_counter() - t0
+    return {"lattice": list(dims), "seconds": dt, "S": S,
+            "solves": "M^+ Y = phi then M X = Y, FP64 flexible BiCGStab + FP32 RAS, tol 1e-12"}
 
 
 def solve_comparison(wc, lat, src, args):
@@ -308,6 +466,10 @@ def solve_comparison(wc, lat, src, args):
     out = {}
     for name, kw in (("mixed_ras_f32", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F32)),
                      ("mixed_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16)),
+                     ("reliable_ras_f32", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F32,
+                                               solver=wc.SOLVER_RELIABLE, delta=0.1)),
+                     ("reliable_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
+                                               solver=wc.SOLVER_RELIABLE, delta=0.1)),
                      ("fp64_plain", dict(precond=wc.PRECOND_NONE))):
         x = lat.field(wc.F64)
         lat.solve(x, b, tol=1e-10, max_iter=20000, check=False, **kw)   # warm-up (allocations)
@@ -318,6 +480,10 @@ def solve_comparison(wc, lat, src, args):
                      "status": wc.STATUS.get(info.status, info.status)}
         x.close()
     out["speedup_mixed_f32_vs_fp64"] = out["fp64_plain"]["seconds"] / out["mixed_ras_f32"]["seconds"]
+    best = min((k for k, v in out.items() if isinstance(v, dict) and k != "fp64_plain"),
+               key=lambda k: out[k]["seconds"])
+    out["fastest_mixed"] = best
+    out["speedup_fastest_mixed_vs_fp64"] = out["fp64_plain"]["seconds"] / out[best]["seconds"]
     out["ras"] = "4^4 blocks, overlap 1, 4 MR iterations"
     return out
 
@@ -332,6 +498,9 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--skip-solves", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-force", action="store_true")
+    ap.add_argument("--skip-large", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -82,6 +82,21 @@ typedef struct {
     int mr_iters;
 } wc_ras_params;
 
+/* How a preconditioned solve splits its precisions.
+ * FLEXIBLE (defect correction): FP64 flexible BiCGStab -- every vector,
+ *   inner product and operator application in FP64 -- with the
+ *   preconditioner K^-1 u = |u| RAS(u / |u|) evaluated in FP32 arithmetic on
+ *   inner_prec storage.
+ * RELIABLE: BiCGStab itself runs in FP32 (FP32 vectors, FP32 operator, RAS
+ *   on inner_prec storage, FP64 sums of FP32 partials); the solution is held
+ *   in FP64 and every time the FP32 residual falls below delta times its
+ *   largest value since the last refresh, the correction is added to the FP64
+ *   solution and the residual is recomputed as b - M x in FP64 (a "reliable
+ *   update").  This trades FP64 work, slow on GB300, for FP32 work.
+ * The true residual |b - M x| / |b| reported and tested against tol is FP64
+ * in both. */
+typedef enum { WC_SOLVER_FLEXIBLE = 0, WC_SOLVER_RELIABLE = 1 } wc_solver_kind;
+
 typedef struct {
     double tol;            /* stop when |b - M x| / |b| <= tol (true residual) */
     int max_iter;          /* total outer iterations over all restarts */
@@ -89,6 +104,8 @@ typedef struct {
     wc_precond precond;    /* NONE: plain FP64 BiCGStab; RAS: mixed precision */
     wc_prec inner_prec;    /* storage of the RAS preconditioner: WC_F32 or WC_F16 */
     wc_ras_params ras;
+    wc_solver_kind solver; /* FLEXIBLE or RELIABLE (RELIABLE needs precond RAS) */
+    double delta;          /* RELIABLE refresh threshold, 0 < delta < 1 (0: 0.1) */
 } wc_solve_params;
 
 typedef struct {
@@ -146,6 +163,20 @@ wc_status wc_apply_M(wc_lattice lat, wc_field out, wc_field in);
 wc_status wc_apply_Mdag(wc_lattice lat, wc_field out, wc_field in);
 /* out = H in (hopping term only, no clover, no kappa).  Same rules. */
 wc_status wc_apply_hop(wc_lattice lat, wc_field out, wc_field in);
+
+/* Launch shape of the operator kernels.  The site-to-thread mapping
+ * (lexicographic or 4-D tiles), CTA size and register cap of wc_apply_M /
+ * wc_apply_Mdag / wc_apply_hop are chosen per lattice extent, precision and
+ * kind (0 M, 1 M^+, 2 H) by timing the candidates on the first apply (that
+ * first call blocks; not done while the stream is being captured, where the
+ * default shape is used).  force_index >= 0 pins candidate #force_index
+ * (0..15; WC_ERR_ARG if its tile does not divide the lattice or it is a
+ * register-capped shape with FP64); -1 only reports.  shape_out receives
+ * {threads per CTA, tile x, y, z, t (all 0: lexicographic), register cap
+ * (0 none, 1: 64, 2: 85 registers per thread)}, all -1 if nothing was
+ * chosen yet.  The choice is shared by lattices of equal
+ * extent in the process. */
+wc_status wc_apply_shape(wc_lattice lat, wc_prec prec, int kind, int force_index, int shape_out[6]);
 
 /* ---- fused BLAS-1 (FP64 accumulation; blocking) ---------------------- */
 

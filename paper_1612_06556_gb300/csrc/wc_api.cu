@@ -97,7 +97,15 @@ __global__ void k_pack_gauge(int V, const double2 *U, GaugeStore g)
 #pragma unroll
     for (int k = 0; k < 6; ++k) a[k] = u[k];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) g.u64[((size_t)mu * 6 + k) * V + x] = a[k];
+    for (int k = 0; k < 6; ++k) g.u64[((size_t)mu * 9 + k) * V + x] = a[k];
+    {
+        cx<double> r01[6], r2[3];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r01[k] = mkc(a[k].x, a[k].y);
+        reconstruct_row2(r01, r2);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) g.u64[((size_t)mu * 9 + 6 + k) * V + x] = make_double2(r2[k].re, r2[k].im);
+    }
 #pragma unroll
     for (int j = 0; j < 3; ++j)
         g.u32[((size_t)mu * 3 + j) * V + x] =
@@ -150,8 +158,7 @@ __device__ M3 m3_dag(const M3 &a)
 __device__ M3 load_u(const GaugeStore &g, int V, int mu, int x)
 {
     cx<double> u[6], r2[3];
-    P64::load_link(g, V, mu, x, u);
-    reconstruct_row2(u, r2);
+    P64::load_link(g, V, mu, x, u, r2);
     M3 r;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -440,7 +447,7 @@ wc_status wc_load_gauge(wc_lattice lat, const double *data)
     GaugeStore &g = lat->gauge;
     wc_status st = WC_OK;
     if (!g.u64) {
-        st = check_cuda(lat, dalloc(&g.u64, sizeof(double2) * 24 * (size_t)V), "cudaMalloc(gauge)");
+        st = check_cuda(lat, dalloc(&g.u64, sizeof(double2) * 36 * (size_t)V), "cudaMalloc(gauge)");
         if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u32, sizeof(float4) * 12 * (size_t)V), "cudaMalloc(gauge)");
         if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u16a, sizeof(uint4) * 4 * (size_t)V), "cudaMalloc(gauge)");
         if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u16b, sizeof(uint2) * 4 * (size_t)V), "cudaMalloc(gauge)");
@@ -616,6 +623,18 @@ static wc_status apply_common(wc_lattice lat, wc_field out, wc_field in, int kin
 wc_status wc_apply_M(wc_lattice lat, wc_field out, wc_field in) { return apply_common(lat, out, in, 0); }
 wc_status wc_apply_Mdag(wc_lattice lat, wc_field out, wc_field in) { return apply_common(lat, out, in, 1); }
 wc_status wc_apply_hop(wc_lattice lat, wc_field out, wc_field in) { return apply_common(lat, out, in, 2); }
+
+wc_status wc_apply_shape(wc_lattice lat, wc_prec prec, int kind, int force_index, int shape_out[6])
+{
+    if (!lat || !shape_out) return set_error(lat, WC_ERR_ARG, "lattice and shape_out must not be NULL");
+    if (prec != WC_F64 && prec != WC_F32 && prec != WC_F16) return set_error(lat, WC_ERR_ARG, "bad precision");
+    if (kind < 0 || kind > 2) return set_error(lat, WC_ERR_ARG, "kind must be 0 (M), 1 (M^+) or 2 (H)");
+    if (force_index < -1 || force_index >= apply_shape_count())
+        return set_error(lat, WC_ERR_ARG, "force_index out of range");
+    if (!apply_shape(lat, prec, kind, force_index, shape_out))
+        return set_error(lat, WC_ERR_ARG, "launch shape does not fit this lattice / precision");
+    return WC_OK;
+}
 
 const char *wc_last_error(wc_lattice lat)
 {

@@ -5,19 +5,29 @@
 // host between solver steps (Sec. 2, reverse offloading).  Here the whole
 // BiCGStab iteration loop of every right-hand side runs inside one graph:
 //
-//   WHILE (any RHS active)                      <- device-side condition
-//     IF (RHS 0 active) { one BiCGStab step }   \
-//     IF (RHS 1 active) { one BiCGStab step }    > independent branches,
-//     ...                                       /  run concurrently
-//     check: per RHS, stop at |r| <= tol |b|, breakdown, NaN or max_iter;
-//            set the IF conditions and the WHILE condition
+//   flexible (FP64 BiCGStab, FP32/FP16 RAS defect correction):
+//     WHILE (any RHS active)                      <- device-side condition
+//       IF (RHS 0 active) { one BiCGStab step }   \
+//       IF (RHS 1 active) { one BiCGStab step }    > independent branches,
+//       ...                                       /  run concurrently
+//       check: per RHS, stop at |r| <= tol |b|, breakdown, NaN or max_iter
 //
-// Each branch is captured from the same enqueue_iteration() the single-RHS
-// solve uses, on that RHS's own solver state (scalars, reduction scratch,
-// work vectors), so the branches share nothing but the read-only gauge field
-// and clover term of their lattice.  No host round trip happens until every
-// RHS has stopped; then the true residual of each RHS is recomputed in FP64
-// and any RHS that misses tol is restarted by the host-driven solver.
+//   reliable update (FP32 BiCGStab, FP64 refreshes):
+//     WHILE (any RHS active)
+//       IF (RHS i active)  { one FP32 BiCGStab step }        for every i
+//       check 1: refresh due?  (|r| <= delta max|r|, |r| <= tol |b|, or
+//                max_iter reached)
+//       IF (RHS i refresh) { x += x_lo; r = b - M x in FP64; r32 = r;
+//                            rho, beta recomputed }            for every i
+//       check 2: converged (true residual) or max_iter -> inactive
+//
+// Each branch is captured from the same enqueue code the single-RHS solves
+// use, on that RHS's own solver state (scalars, reduction scratch, work
+// vectors), so branches share nothing but the read-only gauge field and
+// clover term of their lattice.  No host round trip happens until every RHS
+// has stopped; then the true residual of each RHS is recomputed in FP64 and
+// any RHS that missed tol (breakdown, drift) is continued by the host-driven
+// solver.
 //
 // RAS block shapes: with ras.block = {0,0,0,0} the shape is chosen per
 // lattice extent and inner precision by a small autotuner (candidate shapes
@@ -42,26 +52,76 @@ namespace {
 
 struct BatchItem {
     const SolverScalars *scal;
-    double tol2;
+    double tol2;    // tol^2 |b|^2
+    double d2;      // delta^2 (reliable update)
     int max_iter;
     int pad;
 };
 
-__global__ void k_batch_check(const BatchItem *items, int n, int *iters, int *active,
-                              const cudaGraphConditionalHandle *ifh, cudaGraphConditionalHandle wh)
+// Device-side per-RHS state of the loop.
+struct BatchDev {
+    const BatchItem *items;
+    int *iters;
+    int *active;
+    int *refresh;
+    double *rmax2;
+    const cudaGraphConditionalHandle *h_iter;
+    const cudaGraphConditionalHandle *h_ref;
+};
+
+// After the BiCGStab steps.  Flexible: decide which RHS continue and set
+// the WHILE condition.  Reliable: decide which RHS refresh now.
+__global__ void k_batch_check_iter(BatchDev d, int n, int reliable, cudaGraphConditionalHandle wh)
 {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        int a = active[i];
+        const BatchItem &it = d.items[i];
+        int a = d.active[i];
+        int ref = 0;
         if (a) {
-            const int it = ++iters[i];
-            const SolverScalars &s = *items[i].scal;
-            if (!(s.rr > items[i].tol2) || s.flags != 0 || it >= items[i].max_iter) a = 0;
-            active[i] = a;
+            const int k = ++d.iters[i];
+            const SolverScalars &s = *it.scal;
+            if (!reliable) {
+                if (!(s.rr > it.tol2) || s.flags != 0 || k >= it.max_iter) a = 0;
+            } else if (s.flags != 0) {
+                a = 0;   // breakdown / NaN: the host takes over
+            } else {
+                if (s.rr > d.rmax2[i]) d.rmax2[i] = s.rr;
+                ref = (s.rr <= it.d2 * d.rmax2[i] || s.rr <= it.tol2 || k >= it.max_iter) ? 1 : 0;
+            }
+            d.active[i] = a;
         }
-        cudaGraphSetConditional(ifh[i], a ? 1u : 0u);
+        if (reliable) {
+            d.refresh[i] = ref;
+            cudaGraphSetConditional(d.h_ref[i], ref ? 1u : 0u);
+        } else {
+            cudaGraphSetConditional(d.h_iter[i], a ? 1u : 0u);
+            if (a) atomicOr(&any, 1);
+        }
+    }
+    __syncthreads();
+    if (!reliable && threadIdx.x == 0) cudaGraphSetConditional(wh, any ? 1u : 0u);
+}
+
+// Reliable update only, after the refreshes: stop converged RHS (FP64 true
+// residual) and RHS at max_iter; set the IF and WHILE conditions.
+__global__ void k_batch_check_refresh(BatchDev d, int n, cudaGraphConditionalHandle wh)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const BatchItem &it = d.items[i];
+        int a = d.active[i];
+        if (a && d.refresh[i]) {
+            const double rr = it.scal->rr;   // FP64 true residual of the refresh
+            if (!(rr > it.tol2) || d.iters[i] >= it.max_iter) a = 0;
+            d.rmax2[i] = rr;
+            d.active[i] = a;
+        }
+        cudaGraphSetConditional(d.h_iter[i], a ? 1u : 0u);
         if (a) atomicOr(&any, 1);
     }
     __syncthreads();
@@ -71,10 +131,12 @@ __global__ void k_batch_check(const BatchItem *items, int n, int *iters, int *ac
 struct Resources {
     std::vector<SolverState> S;
     std::vector<SolverVecs> W;
+    std::vector<LoVecs> LW;
     std::vector<cudaStream_t> streams;
     BatchItem *d_items = nullptr;
-    int *d_iters = nullptr, *d_active = nullptr;
-    cudaGraphConditionalHandle *d_handles = nullptr;
+    int *d_iters = nullptr, *d_active = nullptr, *d_refresh = nullptr;
+    double *d_rmax2 = nullptr;
+    cudaGraphConditionalHandle *d_hiter = nullptr, *d_href = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 
@@ -87,12 +149,84 @@ struct Resources {
         cudaFree(d_items);
         cudaFree(d_iters);
         cudaFree(d_active);
-        cudaFree(d_handles);
+        cudaFree(d_refresh);
+        cudaFree(d_rmax2);
+        cudaFree(d_hiter);
+        cudaFree(d_href);
         for (auto &s : S) state_free(s);
         for (auto s : streams)
             if (s) cudaStreamDestroy(s);
     }
 };
+
+template <class T>
+cudaError_t to_device(T **dst, const std::vector<T> &src)
+{
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), sizeof(T) * src.size());
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// n IF-condition handles of graph `parent` with default values initial[i]
+wc_status create_handles(cudaGraph_t parent, int n, const std::vector<int> &initial,
+                         std::vector<cudaGraphConditionalHandle> *handles)
+{
+    handles->assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        wc_status st = check_cuda(nullptr, cudaGraphConditionalHandleCreate(&(*handles)[i], parent,
+                                                                            initial[i] ? 1u : 0u,
+                                                                            cudaGraphCondAssignDefault),
+                                  "cudaGraphConditionalHandleCreate");
+        if (st != WC_OK) return st;
+    }
+    return WC_OK;
+}
+
+// One IF node per handle, each depending on deps, whose body holds the
+// launches `enqueue(i)` queues on stream i while that stream is captured.
+template <class Enqueue>
+wc_status add_if_nodes(cudaGraph_t parent, const std::vector<cudaGraphNode_t> &deps,
+                       const std::vector<cudaGraphConditionalHandle> &handles, Resources &R, Enqueue enqueue,
+                       std::vector<cudaGraphNode_t> *nodes)
+{
+    nodes->clear();
+    for (size_t i = 0; i < handles.size(); ++i) {
+        cudaGraphNodeParams ip = {};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = handles[i];
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t node;
+        wc_status st = check_cuda(nullptr, cudaGraphAddNode(&node, parent, deps.empty() ? nullptr : deps.data(),
+                                                            nullptr, deps.size(), &ip), "add IF node");
+        if (st != WC_OK) return st;
+        nodes->push_back(node);
+        cudaStream_t s = R.streams[i];
+        st = check_cuda(nullptr, cudaStreamBeginCaptureToGraph(s, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                               cudaStreamCaptureModeRelaxed),
+                        "cudaStreamBeginCaptureToGraph");
+        if (st != WC_OK) return st;
+        const wc_status est = enqueue((int)i);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(s, &captured);
+        if (est != WC_OK) return est;
+        st = check_cuda(nullptr, ce, "cudaStreamEndCapture");
+        if (st != WC_OK) return st;
+    }
+    return WC_OK;
+}
+
+wc_status add_kernel_node(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, void *func, void **args,
+                          cudaGraphNode_t *node)
+{
+    cudaKernelNodeParams kp = {};
+    kp.func = func;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(256);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    return check_cuda(nullptr, cudaGraphAddKernelNode(node, g, deps.data(), deps.size(), &kp), "add check node");
+}
 
 // ---- RAS block-shape autotuner ------------------------------------------
 
@@ -203,25 +337,27 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
     for (int i = 0; i < n; ++i) {
         // the RAS shape is checked after autotuning when it is left to it
         wc_solve_params q = *p;
-        if (q.precond == WC_PRECOND_RAS && q.ras.block[0] == 0) q.precond = WC_PRECOND_NONE;
+        if (q.precond == WC_PRECOND_RAS && q.ras.block[0] == 0) {
+            for (int m = 0; m < 4; ++m) q.ras.block[m] = 1;
+            q.ras.overlap = 0;
+        }
         if (!lats[i]) return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: NULL lattice");
         const wc_status st = check_solve_args(lats[i], xs[i], bs[i], &q);
         if (st != WC_OK)
             return set_error(nullptr, st, "wc_solve_batch: RHS " + std::to_string(i) + ": " + lats[i]->err);
-        if (p->precond == WC_PRECOND_RAS && (p->inner_prec != WC_F32 && p->inner_prec != WC_F16))
-            return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: RAS inner precision must be WC_F32 or WC_F16");
         for (int j = 0; j < i; ++j)
             if (xs[j] == xs[i] || xs[i] == bs[j])
                 return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: solution fields must be distinct");
     }
+    const bool reliable = p->precond == WC_PRECOND_RAS && p->solver == WC_SOLVER_RELIABLE;
     auto t0 = std::chrono::steady_clock::now();
     Resources R;
     R.S.resize(n);
     R.W.resize(n);
+    R.LW.resize(n);
     R.streams.assign(n, nullptr);
     std::vector<wc_solve_params> P(n, *p);
     wc_status st = check_cuda(nullptr, ras_prepare(), "ras_prepare");
-    // RAS shapes (autotuned per lattice when requested)
     for (int i = 0; i < n && st == WC_OK; ++i) {
         st = resolve_ras(lats[i], bs[i], *p, &P[i].ras);
         if (st == WC_OK && P[i].precond == WC_PRECOND_RAS) st = check_ras_params(lats[i], &P[i].ras);
@@ -229,16 +365,17 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
     }
     for (int i = 0; i < n && st == WC_OK; ++i) {
         st = state_init(lats[i], R.S[i]);
-        if (st == WC_OK) st = check_cuda(lats[i], cudaStreamCreateWithFlags(&R.streams[i], cudaStreamNonBlocking),
-                                         "cudaStreamCreate");
+        if (st == WC_OK)
+            st = check_cuda(lats[i], cudaStreamCreateWithFlags(&R.streams[i], cudaStreamNonBlocking), "stream");
         if (st == WC_OK) {
             R.S[i].stream = R.streams[i];
             st = solver_vectors(lats[i], R.S[i], P[i], &R.W[i]);
         }
+        if (st == WC_OK && reliable) st = lo_vectors(lats[i], R.S[i], P[i], &R.LW[i]);
     }
     if (st != WC_OK) return st;
 
-    // |b|^2 and r = b - M x for every RHS, one synchronisation for all
+    // |b|^2 and the start of every solve, one synchronisation for all
     std::vector<double> bb(n), tol2(n);
     for (int i = 0; i < n && st == WC_OK; ++i) {
         SolverState &S = R.S[i];
@@ -246,21 +383,25 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
         if (st == WC_OK)
             st = check_cuda(lats[i], cudaMemcpyAsync(S.red.host_result, S.red.result, sizeof(double),
                                                      cudaMemcpyDeviceToHost, S.stream), "copy");
-        if (st == WC_OK) st = enqueue_init(lats[i], S, 0, xs[i], bs[i], R.W[i]);
+        if (st == WC_OK)
+            st = reliable ? enqueue_lo_start(lats[i], S, 0, xs[i], bs[i], R.W[i].r, R.LW[i])
+                          : enqueue_init(lats[i], S, 0, xs[i], bs[i], R.W[i]);
         if (st == WC_OK)
             st = check_cuda(lats[i], cudaMemcpyAsync(S.scal_host, S.scal, sizeof(SolverScalars),
                                                      cudaMemcpyDeviceToHost, S.stream), "copy");
     }
     for (int i = 0; i < n && st == WC_OK; ++i) st = check_cuda(lats[i], cudaStreamSynchronize(R.streams[i]), "sync");
     if (st != WC_OK) return st;
-    std::vector<int> active(n, 0), iters(n, 0);
+    std::vector<int> active(n, 0), iters(n, 0), zeros(n, 0);
+    std::vector<double> rmax2(n, 0.0);
     int any = 0;
     for (int i = 0; i < n; ++i) {
         infos[i] = wc_solve_info{};
         bb[i] = R.S[i].red.host_result[0];
         tol2[i] = P[i].tol * P[i].tol * bb[i];
         const SolverScalars &h = *R.S[i].scal_host;
-        if (!isfinite(bb[i]) || (h.flags & FLAG_NAN)) {
+        rmax2[i] = h.rr;
+        if (!isfinite(bb[i]) || (h.flags & FLAG_NAN) || !isfinite(h.rr)) {
             infos[i].status = WC_ERR_NAN;
         } else if (bb[i] == 0.0 || h.rr <= tol2[i]) {
             infos[i].status = WC_OK;   // settled below (zero source: x = 0)
@@ -272,22 +413,16 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
 
     if (any) {
         std::vector<BatchItem> items(n);
-        for (int i = 0; i < n; ++i) items[i] = BatchItem{R.S[i].scal, tol2[i], P[i].max_iter, 0};
-        cudaStream_t s0 = R.streams[0];
-        st = check_cuda(nullptr, cudaMalloc(&R.d_items, sizeof(BatchItem) * n), "cudaMalloc");
-        if (st == WC_OK) st = check_cuda(nullptr, cudaMalloc(&R.d_iters, sizeof(int) * n), "cudaMalloc");
-        if (st == WC_OK) st = check_cuda(nullptr, cudaMalloc(&R.d_active, sizeof(int) * n), "cudaMalloc");
-        if (st == WC_OK)
-            st = check_cuda(nullptr, cudaMalloc(&R.d_handles, sizeof(cudaGraphConditionalHandle) * n), "cudaMalloc");
-        if (st == WC_OK)
-            st = check_cuda(nullptr, cudaMemcpy(R.d_items, items.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice),
-                            "copy");
-        if (st == WC_OK)
-            st = check_cuda(nullptr, cudaMemcpy(R.d_iters, iters.data(), sizeof(int) * n, cudaMemcpyHostToDevice), "copy");
-        if (st == WC_OK)
-            st = check_cuda(nullptr, cudaMemcpy(R.d_active, active.data(), sizeof(int) * n, cudaMemcpyHostToDevice),
-                            "copy");
-        // graph: WHILE { IF_i { iteration_i } ... ; check }
+        for (int i = 0; i < n; ++i) {
+            const double dl = (P[i].delta > 0.0 && P[i].delta < 1.0) ? P[i].delta : 0.1;
+            items[i] = BatchItem{R.S[i].scal, tol2[i], dl * dl, P[i].max_iter, 0};
+        }
+        st = check_cuda(nullptr, to_device(&R.d_items, items), "copy");
+        if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_iters, iters), "copy");
+        if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_active, active), "copy");
+        if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_refresh, zeros), "copy");
+        if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_rmax2, rmax2), "copy");
+        // top level: one WHILE node
         if (st == WC_OK) st = check_cuda(nullptr, cudaGraphCreate(&R.graph, 0), "cudaGraphCreate");
         cudaGraphConditionalHandle wh = 0;
         cudaGraph_t body = nullptr;
@@ -301,63 +436,48 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
             wp.conditional.type = cudaGraphCondTypeWhile;
             wp.conditional.size = 1;
             cudaGraphNode_t wnode;
-            st = check_cuda(nullptr, cudaGraphAddNode(&wnode, R.graph, nullptr, nullptr, 0, &wp), "add while node");
+            st = check_cuda(nullptr, cudaGraphAddNode(&wnode, R.graph, nullptr, nullptr, 0, &wp), "add WHILE node");
             if (st == WC_OK) body = wp.conditional.phGraph_out[0];
         }
-        std::vector<cudaGraphConditionalHandle> handles(n, 0);
-        std::vector<cudaGraphNode_t> ifnodes;
-        for (int i = 0; i < n && st == WC_OK; ++i) {
-            st = check_cuda(nullptr, cudaGraphConditionalHandleCreate(&handles[i], body, active[i] ? 1u : 0u,
-                                                                      cudaGraphCondAssignDefault),
-                            "cudaGraphConditionalHandleCreate");
-            if (st != WC_OK) break;
-            cudaGraphNodeParams ip = {};
-            ip.type = cudaGraphNodeTypeConditional;
-            ip.conditional.handle = handles[i];
-            ip.conditional.type = cudaGraphCondTypeIf;
-            ip.conditional.size = 1;
-            cudaGraphNode_t inode;
-            st = check_cuda(nullptr, cudaGraphAddNode(&inode, body, nullptr, nullptr, 0, &ip), "add if node");
-            if (st != WC_OK) break;
-            ifnodes.push_back(inode);
-            cudaGraph_t ibody = ip.conditional.phGraph_out[0];
-            SolverState &S = R.S[i];
-            st = check_cuda(nullptr, cudaStreamBeginCaptureToGraph(S.stream, ibody, nullptr, nullptr, 0,
-                                                                   cudaStreamCaptureModeRelaxed),
-                            "cudaStreamBeginCaptureToGraph");
-            if (st != WC_OK) break;
-            const wc_status est = enqueue_iteration(lats[i], S, P[i], 0, xs[i], R.W[i]);
-            cudaGraph_t captured = nullptr;
-            const cudaError_t ce = cudaStreamEndCapture(S.stream, &captured);
-            if (est != WC_OK) st = set_error(nullptr, est, lats[i]->err);
-            if (st == WC_OK) st = check_cuda(nullptr, ce, "cudaStreamEndCapture");
-        }
+        // body: IF(active_i){step_i} -> check_iter [-> IF(refresh_i){refresh_i} -> check_refresh]
+        std::vector<cudaGraphConditionalHandle> h_iter, h_ref;
+        std::vector<cudaGraphNode_t> iter_nodes, ref_nodes;
+        if (st == WC_OK) st = create_handles(body, n, active, &h_iter);
+        if (st == WC_OK && reliable) st = create_handles(body, n, zeros, &h_ref);
+        if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_hiter, h_iter), "copy");
+        if (st == WC_OK && reliable) st = check_cuda(nullptr, to_device(&R.d_href, h_ref), "copy");
+        BatchDev dev{R.d_items, R.d_iters, R.d_active, R.d_refresh, R.d_rmax2, R.d_hiter, R.d_href};
+        int reliable_i = reliable ? 1 : 0;
+        void *args1[] = {&dev, &n, &reliable_i, &wh};
+        void *args2[] = {&dev, &n, &wh};
         if (st == WC_OK)
-            st = check_cuda(nullptr, cudaMemcpy(R.d_handles, handles.data(), sizeof(cudaGraphConditionalHandle) * n,
-                                                cudaMemcpyHostToDevice),
-                            "copy");
-        if (st == WC_OK) {
-            void *args[] = {&R.d_items, &n, &R.d_iters, &R.d_active, &R.d_handles, &wh};
-            cudaKernelNodeParams kp = {};
-            kp.func = reinterpret_cast<void *>(k_batch_check);
-            kp.gridDim = dim3(1);
-            kp.blockDim = dim3(256);
-            kp.sharedMemBytes = 0;
-            kp.kernelParams = args;
-            cudaGraphNode_t cnode;
-            st = check_cuda(nullptr, cudaGraphAddKernelNode(&cnode, body, ifnodes.data(), ifnodes.size(), &kp),
-                            "add check node");
+            st = add_if_nodes(body, {}, h_iter, R, [&](int i) {
+                return reliable ? enqueue_lo_iteration(lats[i], R.S[i], P[i], 0, R.LW[i])
+                                : enqueue_iteration(lats[i], R.S[i], P[i], 0, xs[i], R.W[i]);
+            }, &iter_nodes);
+        cudaGraphNode_t check1 = nullptr, check2 = nullptr;
+        if (st == WC_OK)
+            st = add_kernel_node(body, iter_nodes, reinterpret_cast<void *>(k_batch_check_iter), args1, &check1);
+        if (st == WC_OK && reliable) {
+            st = add_if_nodes(body, {check1}, h_ref, R, [&](int i) {
+                return enqueue_refresh_full(lats[i], R.S[i], 0, xs[i], bs[i], R.W[i].r, R.LW[i]);
+            }, &ref_nodes);
+            if (st == WC_OK)
+                st = add_kernel_node(body, ref_nodes, reinterpret_cast<void *>(k_batch_check_refresh), args2,
+                                     &check2);
         }
         if (st == WC_OK) st = check_cuda(nullptr, cudaGraphInstantiate(&R.exec, R.graph, 0), "cudaGraphInstantiate");
-        if (st == WC_OK) st = check_cuda(nullptr, cudaGraphLaunch(R.exec, s0), "cudaGraphLaunch");
-        if (st == WC_OK) st = check_cuda(nullptr, cudaStreamSynchronize(s0), "sync(graph)");
+        if (st == WC_OK) st = check_cuda(nullptr, cudaGraphLaunch(R.exec, R.streams[0]), "cudaGraphLaunch");
+        if (st == WC_OK) st = check_cuda(nullptr, cudaStreamSynchronize(R.streams[0]), "sync(graph)");
         if (st == WC_OK)
             st = check_cuda(nullptr, cudaMemcpy(iters.data(), R.d_iters, sizeof(int) * n, cudaMemcpyDeviceToHost),
                             "copy");
         if (st != WC_OK) return st;
     }
 
-    // true residuals in FP64 for every RHS, then host-driven restarts
+    // true residuals in FP64 for every RHS (the reliable solver folded its
+    // FP32 correction into x at its last refresh), then host-driven
+    // continuation of any RHS that missed tol
     for (int i = 0; i < n && st == WC_OK; ++i) {
         if (infos[i].status == WC_ERR_NAN) continue;
         SolverState &S = R.S[i];
@@ -366,7 +486,10 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
                             "memset");
             continue;
         }
-        st = enqueue_true_residual(lats[i], S, 0, xs[i], bs[i], R.W[i]);
+        if (reliable)
+            st = check_cuda(lats[i], hp_add_lo(lats[i], S, static_cast<double2 *>(xs[i]->data),
+                                               static_cast<float4 *>(R.LW[i].xlo->data)), "hp_add_lo");
+        if (st == WC_OK) st = enqueue_true_residual(lats[i], S, 0, xs[i], bs[i], R.W[i]);
         if (st == WC_OK)
             st = check_cuda(lats[i], cudaMemcpyAsync(S.scal_host, S.scal, sizeof(SolverScalars),
                                                      cudaMemcpyDeviceToHost, S.stream), "copy");
@@ -392,9 +515,9 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
                 // continue from x with the host-driven solver
                 wc_solve_params q = P[i];
                 q.max_restarts = p->max_restarts > 0 ? p->max_restarts - 1 : 0;
-                const wc_status r = bicgstab(lats[i], R.S[i], 0, xs[i], bs[i], q, &inf, iters[i], bb[i]);
+                const int done = iters[i];
+                bicgstab(lats[i], R.S[i], 0, xs[i], bs[i], q, &inf, done, bb[i]);
                 inf.restarts += 1;
-                (void)r;
             }
         }
         inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

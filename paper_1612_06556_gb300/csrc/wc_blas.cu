@@ -401,6 +401,268 @@ __global__ void __launch_bounds__(kRedBlock) k_residual(long long n, const doubl
 
 }  // namespace
 
+// ------------------------------------------------------------------------
+// Low-precision BiCGStab vector updates (FP32 fields, FP32 arithmetic) for
+// the reliable-update solver.  Per-thread partial sums are FP32; blocks add
+// them in FP32 and the last block adds the block partials in FP64, so the
+// FP64 pipe is used once per block rather than once per element.
+// ------------------------------------------------------------------------
+
+namespace {
+
+__device__ __forceinline__ cx<float> f2c(float2 a) { return {a.x, a.y}; }
+
+// Fields are flat arrays of n = 6 V float4 (two complex each).
+__device__ __forceinline__ void ld4(const float4 *p, long long i, cx<float> &a, cx<float> &b)
+{
+    const float4 v = p[i];
+    a = {v.x, v.y};
+    b = {v.z, v.w};
+}
+__device__ __forceinline__ void st4(float4 *p, long long i, cx<float> a, cx<float> b)
+{
+    p[i] = make_float4(a.re, a.im, b.re, b.im);
+}
+
+// Grid sum of per-thread FP32 partials: lanes and warps in FP32, the block
+// partials (one per block) in FP64 by the last block, in block order.
+// Returns true in thread 0 of the last block once out[0..N) is final.
+template <int N>
+__device__ __forceinline__ bool grid_reduce_f(float (&v)[N], const ReduceScratch &rs, double *out)
+{
+    __shared__ float sm[32][N];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) sm[wid][i] = v[i];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            float t = lane < nw ? sm[lane][i] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) rs.partials[(size_t)blockIdx.x * 8 + i] = (double)t;
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(rs.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double t = 0.0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(rs.partials + (size_t)b * 8 + i);
+            t = warp_sum(t);
+            if (lane == 0) out[i] = t;
+        }
+        if (lane == 0) *rs.ticket = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
+__device__ __forceinline__ cx<double> c_of2(double2 a) { return {a.x, a.y}; }
+__device__ __forceinline__ double2 d2_of2(cx<double> a) { return make_double2(a.re, a.im); }
+__device__ __forceinline__ cx<double> cdiv2(cx<double> a, cx<double> b)
+{
+    const double d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+
+// rhat = r, p = v = 0, xlo = 0; rr = |r|^2, rho = rr, alpha = omega = rho0 = 1
+__global__ void __launch_bounds__(kRedBlock) k_lo_init(long long n, const float4 *r, float4 *rhat, float4 *p,
+                                                       float4 *v, float4 *xlo, ReduceScratch rs, SolverScalars *sc)
+{
+    float acc[1] = {0.f};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 ri = r[i];
+        rhat[i] = ri;
+        p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        xlo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        acc[0] = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, fmaf(ri.z, ri.z, fmaf(ri.w, ri.w, acc[0]))));
+    }
+    if (grid_reduce_f<1>(acc, rs, rs.result)) {
+        const double rr = rs.result[0];
+        sc->rr = rr;
+        sc->rho = make_double2(rr, 0.0);
+        sc->rho0 = make_double2(1.0, 0.0);
+        sc->alpha = make_double2(1.0, 0.0);
+        sc->omega = make_double2(1.0, 0.0);
+        sc->beta = make_double2(rr, 0.0);
+        sc->flags = isfinite(rr) ? 0 : FLAG_NAN;
+        if (rr == 0.0) sc->flags |= FLAG_BREAKDOWN;
+    }
+}
+
+// p = r + beta (p - omega v)
+__global__ void __launch_bounds__(kRedBlock) k_lo_p(long long n, const float4 *r, const float4 *v, float4 *p,
+                                                    const SolverScalars *sc)
+{
+    const cx<float> beta = mkc((float)sc->beta.x, (float)sc->beta.y);
+    const cx<float> omega = mkc((float)sc->omega.x, (float)sc->omega.y);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        cx<float> r0, r1, v0, v1, p0, p1;
+        ld4(r, i, r0, r1);
+        ld4(v, i, v0, v1);
+        ld4(p, i, p0, p1);
+        p0 = r0 + beta * (p0 - omega * v0);
+        p1 = r1 + beta * (p1 - omega * v1);
+        st4(p, i, p0, p1);
+    }
+}
+
+// alpha = rho / <rhat, v>
+__global__ void __launch_bounds__(kRedBlock) k_lo_alpha(long long n, const float4 *rhat, const float4 *v,
+                                                        ReduceScratch rs, SolverScalars *sc)
+{
+    float acc[2] = {0.f, 0.f};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 a = rhat[i], b = v[i];
+        acc[0] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc[0]))));
+        acc[1] = fmaf(a.x, b.y, fmaf(-a.y, b.x, fmaf(a.z, b.w, fmaf(-a.w, b.z, acc[1]))));
+    }
+    if (grid_reduce_f<2>(acc, rs, rs.result)) {
+        const cx<double> rv = mkc(rs.result[0], rs.result[1]);
+        if (!isfinite(rv.re) || !isfinite(rv.im)) sc->flags |= FLAG_NAN;
+        if (rv.re == 0.0 && rv.im == 0.0) {
+            sc->flags |= FLAG_BREAKDOWN;
+            sc->alpha = make_double2(0.0, 0.0);
+        } else {
+            sc->alpha = d2_of2(cdiv2(c_of2(sc->rho), rv));
+        }
+    }
+}
+
+// s = r - alpha v
+__global__ void __launch_bounds__(kRedBlock) k_lo_s(long long n, const float4 *r, const float4 *v, float4 *s,
+                                                    const SolverScalars *sc)
+{
+    const cx<float> alpha = mkc((float)sc->alpha.x, (float)sc->alpha.y);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        cx<float> r0, r1, v0, v1;
+        ld4(r, i, r0, r1);
+        ld4(v, i, v0, v1);
+        st4(s, i, r0 - alpha * v0, r1 - alpha * v1);
+    }
+}
+
+// omega = <t, s> / <t, t>
+__global__ void __launch_bounds__(kRedBlock) k_lo_omega(long long n, const float4 *t, const float4 *s,
+                                                        ReduceScratch rs, SolverScalars *sc)
+{
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 a = t[i], b = s[i];
+        acc[0] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc[0]))));
+        acc[1] = fmaf(a.x, b.y, fmaf(-a.y, b.x, fmaf(a.z, b.w, fmaf(-a.w, b.z, acc[1]))));
+        acc[2] = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, acc[2]))));
+    }
+    if (grid_reduce_f<3>(acc, rs, rs.result)) {
+        const double tt = rs.result[2];
+        sc->tt = tt;
+        if (!isfinite(tt) || !isfinite(rs.result[0]) || !isfinite(rs.result[1])) sc->flags |= FLAG_NAN;
+        sc->omega = tt > 0.0 ? make_double2(rs.result[0] / tt, rs.result[1] / tt) : make_double2(0.0, 0.0);
+    }
+}
+
+// xlo += alpha phat + omega shat; r = s - omega t; rho' = <rhat, r>, rr = |r|^2
+__global__ void __launch_bounds__(kRedBlock) k_lo_xr(long long n, float4 *xlo, const float4 *phat,
+                                                     const float4 *shat, const float4 *s, const float4 *t,
+                                                     float4 *r, const float4 *rhat, ReduceScratch rs,
+                                                     SolverScalars *sc)
+{
+    const cx<float> alpha = mkc((float)sc->alpha.x, (float)sc->alpha.y);
+    const cx<float> omega = mkc((float)sc->omega.x, (float)sc->omega.y);
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        cx<float> x0, x1, a0, a1, b0, b1, s0, s1, t0, t1, h0, h1;
+        ld4(xlo, i, x0, x1);
+        ld4(phat, i, a0, a1);
+        ld4(shat, i, b0, b1);
+        x0 = cfma(omega, b0, cfma(alpha, a0, x0));
+        x1 = cfma(omega, b1, cfma(alpha, a1, x1));
+        st4(xlo, i, x0, x1);
+        ld4(s, i, s0, s1);
+        ld4(t, i, t0, t1);
+        const cx<float> r0 = s0 - omega * t0, r1 = s1 - omega * t1;
+        st4(r, i, r0, r1);
+        ld4(rhat, i, h0, h1);
+        acc[0] += h0.re * r0.re + h0.im * r0.im + h1.re * r1.re + h1.im * r1.im;
+        acc[1] += h0.re * r0.im - h0.im * r0.re + h1.re * r1.im - h1.im * r1.re;
+        acc[2] += r0.re * r0.re + r0.im * r0.im + r1.re * r1.re + r1.im * r1.im;
+    }
+    if (grid_reduce_f<3>(acc, rs, rs.result)) {
+        const cx<double> rho_new = mkc(rs.result[0], rs.result[1]);
+        const cx<double> rho = c_of2(sc->rho), om = c_of2(sc->omega), al = c_of2(sc->alpha);
+        sc->rr = rs.result[2];
+        if (!isfinite(sc->rr) || !isfinite(rho_new.re) || !isfinite(rho_new.im)) sc->flags |= FLAG_NAN;
+        if ((om.re == 0.0 && om.im == 0.0) || (rho.re == 0.0 && rho.im == 0.0))
+            sc->flags |= FLAG_BREAKDOWN;
+        else
+            sc->beta = d2_of2(cdiv2(rho_new, rho) * cdiv2(al, om));
+        if (rho_new.re == 0.0 && rho_new.im == 0.0 && sc->rr > 0.0) sc->flags |= FLAG_BREAKDOWN;
+        sc->rho0 = sc->rho;
+        sc->rho = d2_of2(rho_new);
+    }
+}
+
+// r was replaced by the true residual: rho = <rhat, r>,
+// beta = (rho / rho0)(alpha / omega); rr keeps the FP64 true residual that
+// the refresh wrote
+__global__ void __launch_bounds__(kRedBlock) k_lo_rho(long long n, const float4 *rhat, const float4 *r,
+                                                      ReduceScratch rs, SolverScalars *sc)
+{
+    float acc[2] = {0.f, 0.f};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 h = rhat[i], a = r[i];
+        acc[0] = fmaf(h.x, a.x, fmaf(h.y, a.y, fmaf(h.z, a.z, fmaf(h.w, a.w, acc[0]))));
+        acc[1] = fmaf(h.x, a.y, fmaf(-h.y, a.x, fmaf(h.z, a.w, fmaf(-h.w, a.z, acc[1]))));
+    }
+    if (grid_reduce_f<2>(acc, rs, rs.result)) {
+        const cx<double> rho_new = mkc(rs.result[0], rs.result[1]);
+        const cx<double> rho0 = c_of2(sc->rho0), om = c_of2(sc->omega), al = c_of2(sc->alpha);
+        if ((om.re != 0.0 || om.im != 0.0) && (rho0.re != 0.0 || rho0.im != 0.0))
+            sc->beta = d2_of2(cdiv2(rho_new, rho0) * cdiv2(al, om));
+        sc->rho = d2_of2(rho_new);
+    }
+}
+
+// x (FP64) += xlo (FP32); xlo = 0.  FP32 plane j holds components 2j and
+// 2j+1 of each site; FP64 plane k holds component k.
+__global__ void k_hp_add_lo(long long n, int V, double2 *x, float4 *xlo)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long j = i / V, site = i - j * V;
+        const float4 a = xlo[i];
+        double2 *x0 = x + (2 * j) * V + site;
+        double2 *x1 = x0 + V;
+        const double2 u = *x0, w = *x1;
+        *x0 = make_double2(u.x + (double)a.x, u.y + (double)a.y);
+        *x1 = make_double2(w.x + (double)a.z, w.y + (double)a.w);
+        xlo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+}  // namespace
+
 #define WC_GRID(n) reduce_grid(S.red, (n)), kRedBlock, 0, S.stream
 
 cudaError_t bicg_init(wc_lattice lat, SolverState &S, const double2 *b, double2 *r, double2 *rhat, double2 *p,
@@ -447,6 +709,57 @@ cudaError_t residual(wc_lattice lat, SolverState &S, const double2 *b, double2 *
     k_residual<<<WC_GRID(n)>>>(n, b, r, S.red, S.scal);
     return cudaGetLastError();
 }
+cudaError_t lo_init(wc_lattice lat, SolverState &S, const float4 *r, float4 *rhat, float4 *p, float4 *v,
+                    float4 *xlo)
+{
+    const long long n = 6LL * lat->g.V;
+    k_lo_init<<<WC_GRID(n)>>>(n, r, rhat, p, v, xlo, S.red, S.scal);
+    return cudaGetLastError();
+}
+cudaError_t lo_p(wc_lattice lat, SolverState &S, const float4 *r, const float4 *v, float4 *p)
+{
+    const long long n = 6LL * lat->g.V;
+    k_lo_p<<<WC_GRID(n)>>>(n, r, v, p, S.scal);
+    return cudaGetLastError();
+}
+cudaError_t lo_alpha(wc_lattice lat, SolverState &S, const float4 *rhat, const float4 *v)
+{
+    const long long n = 6LL * lat->g.V;
+    k_lo_alpha<<<WC_GRID(n)>>>(n, rhat, v, S.red, S.scal);
+    return cudaGetLastError();
+}
+cudaError_t lo_s(wc_lattice lat, SolverState &S, const float4 *r, const float4 *v, float4 *s)
+{
+    const long long n = 6LL * lat->g.V;
+    k_lo_s<<<WC_GRID(n)>>>(n, r, v, s, S.scal);
+    return cudaGetLastError();
+}
+cudaError_t lo_omega(wc_lattice lat, SolverState &S, const float4 *t, const float4 *s)
+{
+    const long long n = 6LL * lat->g.V;
+    k_lo_omega<<<WC_GRID(n)>>>(n, t, s, S.red, S.scal);
+    return cudaGetLastError();
+}
+cudaError_t lo_xr(wc_lattice lat, SolverState &S, float4 *xlo, const float4 *phat, const float4 *shat,
+                  const float4 *s, const float4 *t, float4 *r, const float4 *rhat)
+{
+    const long long n = 6LL * lat->g.V;
+    k_lo_xr<<<WC_GRID(n)>>>(n, xlo, phat, shat, s, t, r, rhat, S.red, S.scal);
+    return cudaGetLastError();
+}
+cudaError_t lo_rho(wc_lattice lat, SolverState &S, const float4 *rhat, const float4 *r)
+{
+    const long long n = 6LL * lat->g.V;
+    k_lo_rho<<<WC_GRID(n)>>>(n, rhat, r, S.red, S.scal);
+    return cudaGetLastError();
+}
+cudaError_t hp_add_lo(wc_lattice lat, SolverState &S, double2 *x, float4 *xlo)
+{
+    const long long n = 6LL * lat->g.V;
+    k_hp_add_lo<<<WC_GRID(n)>>>(n, lat->g.V, x, xlo);
+    return cudaGetLastError();
+}
+
 cudaError_t norm2_to_result(wc_lattice lat, SolverState &S, const double2 *a)
 {
     const long long n = 12LL * lat->g.V;

@@ -1,8 +1,12 @@
 // Wilson-Clover operator kernels: out = M in, M^+ in, H in; field casts.
 //
-// One thread per site, lexicographic site order (so the neighbour loads of a
-// warp are contiguous in every direction and the 8-fold reuse of each input
-// spinor is served by L1/L2).  Per direction the neighbour spinor is spin
+// One thread per site.  Sites map to threads either in lexicographic order
+// or by 4-D tiles (a CTA covers a tx*ty*tz*tt brick, x fastest, so a warp's
+// loads stay 128-byte contiguous and the x/y/z neighbours of most sites lie
+// in the same CTA); the 8-fold reuse of each input spinor is served by
+// L1/L2.  The mapping, CTA size and register cap are picked per lattice
+// extent, precision and operator by a small autotuner (first use, timed with
+// CUDA events; not while the stream is being captured).  Per direction the neighbour spinor is spin
 // projected to a two-spinor before the SU(3) multiply, halving the matvec
 // work (paper Sec. 2/3, the hopping multiplication "MULT"); links are read as
 // two rows and the third rebuilt in registers (SU(3) reconstruction).  The
@@ -10,6 +14,11 @@
 // spinor first and the hops are accumulated into that result with the
 // coefficient -kappa, so out = (1 + T) in - kappa H in is written once.
 //
+#include <array>
+#include <map>
+#include <mutex>
+#include <type_traits>
+
 #include "wc_internal.cuh"
 #include "wc_stencil.cuh"
 
@@ -17,7 +26,36 @@ namespace wc {
 
 namespace {
 
-constexpr int kApplyBlock = 128;
+constexpr int kApplyMaxThreads = 256;
+
+// Site of (block, thread) under a launch shape: tile[] = {0,0,0,0} means
+// lexicographic order, else tile extents (x fastest) tiling the lattice.
+struct TileMap {
+    int tile[4];
+    int ntile[3];   // tiles along x, y, z
+};
+
+__device__ __forceinline__ int site_of_thread(const Geom &g, const TileMap &m, bool &valid)
+{
+    if (m.tile[0] == 0) {
+        const int x = blockIdx.x * blockDim.x + threadIdx.x;
+        valid = x < g.V;
+        return x;
+    }
+    int t = threadIdx.x, b = blockIdx.x;
+    const int cx = (b % m.ntile[0]) * m.tile[0] + t % m.tile[0];
+    t /= m.tile[0];
+    b /= m.ntile[0];
+    const int cy = (b % m.ntile[1]) * m.tile[1] + t % m.tile[1];
+    t /= m.tile[1];
+    b /= m.ntile[1];
+    const int cz = (b % m.ntile[2]) * m.tile[2] + t % m.tile[2];
+    t /= m.tile[2];
+    b /= m.ntile[2];
+    const int ct = b * m.tile[3] + t;
+    valid = true;
+    return cx + g.stride[1] * cy + g.stride[2] * cz + g.stride[3] * ct;
+}
 
 template <class P, int MU, int SF, int SB>
 __device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, const void *in, const float *in_nrm,
@@ -32,8 +70,7 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, cons
         cx<R> p[12], h[6], u[6], r2[3], w[6];
         P::load_spinor(in, in_nrm, g.V, xf, p);
         project<MU, SF>(p, h);
-        P::load_link(U, g.V, MU, x, u);
-        reconstruct_row2(u, r2);
+        P::load_link(U, g.V, MU, x, u, r2);
         su3_mul(u, r2, h, coef, w);
         reconstruct_add<MU, SF>(acc, w);
     }
@@ -44,22 +81,23 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, cons
         cx<R> p[12], h[6], u[6], r2[3], w[6];
         P::load_spinor(in, in_nrm, g.V, xb, p);
         project<MU, SB>(p, h);
-        P::load_link(U, g.V, MU, xb, u);
-        reconstruct_row2(u, r2);
+        P::load_link(U, g.V, MU, xb, u, r2);
         su3_adj_mul(u, r2, h, coef, w);
         reconstruct_add<MU, SB>(acc, w);
     }
 }
 
-// KIND 0: out = M in, 1: out = M^+ in, 2: out = H in
-template <class P, int KIND>
-__global__ void __launch_bounds__(kApplyBlock) k_apply(Geom g, GaugeStore U, CloverStore C, const void *in,
-                                                       const float *in_nrm, void *out, float *out_nrm,
-                                                       double kappa)
+// KIND 0: out = M in, 1: out = M^+ in, 2: out = H in.  MINB: minimum
+// resident CTAs of kApplyMaxThreads threads per SM (caps registers).
+template <class P, int KIND, int MINB>
+__global__ void __launch_bounds__(kApplyMaxThreads, MINB)
+    k_apply(Geom g, TileMap tm, GaugeStore U, CloverStore C, const void *in, const float *in_nrm, void *out,
+            float *out_nrm, double kappa)
 {
     using R = typename P::real;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= g.V) return;
+    bool valid;
+    const int x = site_of_thread(g, tm, valid);
+    if (!valid) return;
     int c[4];
     site_coords(g, x, c);
     cx<R> acc[12];
@@ -86,21 +124,126 @@ __global__ void __launch_bounds__(kApplyBlock) k_apply(Geom g, GaugeStore U, Clo
     P::store_spinor(out, out_nrm, g.V, x, acc);
 }
 
+// ---- launch shapes and their autotuner ---------------------------------
+
+struct ApplyShape {
+    int threads;
+    int tile[4];   // {0,0,0,0}: lexicographic
+    int capped;    // register cap: 0 none, 1: 64 per thread (4 CTAs of 256), 2: 85 (3 CTAs of 256)
+};
+
+constexpr ApplyShape kShapes[] = {
+    {128, {0, 0, 0, 0}, 0}, {128, {0, 0, 0, 0}, 1}, {256, {0, 0, 0, 0}, 0}, {256, {0, 0, 0, 0}, 1},
+    {128, {8, 4, 4, 1}, 0}, {128, {8, 4, 4, 1}, 1}, {128, {8, 4, 2, 2}, 0}, {128, {4, 4, 4, 2}, 0},
+    {256, {8, 4, 4, 2}, 0}, {256, {8, 4, 4, 2}, 1}, {256, {8, 8, 4, 1}, 0}, {128, {0, 0, 0, 0}, 2},
+    {256, {0, 0, 0, 0}, 2}, {128, {8, 4, 4, 1}, 2}, {256, {8, 4, 4, 2}, 2}, {128, {8, 4, 2, 2}, 2},
+};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+bool shape_fits(const Geom &g, const ApplyShape &s, bool fp64)
+{
+    if (fp64 && s.capped) return false;   // the FP64 operator is ALU-bound: no register cap
+    if (s.tile[0] == 0) return true;
+    for (int m = 0; m < 4; ++m)
+        if (g.L[m] % s.tile[m] != 0) return false;
+    return s.tile[0] * s.tile[1] * s.tile[2] * s.tile[3] == s.threads;
+}
+
+template <class P>
+cudaError_t launch_shape(wc_lattice lat, wc_field out, wc_field in, int kind, const ApplyShape &sh,
+                         cudaStream_t stream)
+{
+    const Geom &g = lat->g;
+    TileMap tm{};
+    unsigned blocks;
+    if (sh.tile[0] == 0) {
+        blocks = (unsigned)((g.V + sh.threads - 1) / sh.threads);
+    } else {
+        for (int m = 0; m < 4; ++m) tm.tile[m] = sh.tile[m];
+        for (int m = 0; m < 3; ++m) tm.ntile[m] = g.L[m] / sh.tile[m];
+        blocks = (unsigned)(g.V / sh.threads);
+    }
+#define WC_LAUNCH(K, MB)                                                                                   \
+    k_apply<P, K, MB><<<blocks, sh.threads, 0, stream>>>(g, tm, lat->gauge, lat->clover, in->data, in->nrm, \
+                                                         out->data, out->nrm, lat->kappa)
+    constexpr bool cap_ok = !std::is_same<P, P64>::value;
+    constexpr int MB64 = cap_ok ? 4 : 1, MB85 = cap_ok ? 3 : 1;
+    if (kind == 0) {
+        if (cap_ok && sh.capped == 1) WC_LAUNCH(0, MB64);
+        else if (cap_ok && sh.capped == 2) WC_LAUNCH(0, MB85);
+        else WC_LAUNCH(0, 1);
+    } else if (kind == 1) {
+        if (cap_ok && sh.capped == 1) WC_LAUNCH(1, MB64);
+        else if (cap_ok && sh.capped == 2) WC_LAUNCH(1, MB85);
+        else WC_LAUNCH(1, 1);
+    } else {
+        if (cap_ok && sh.capped == 1) WC_LAUNCH(2, MB64);
+        else if (cap_ok && sh.capped == 2) WC_LAUNCH(2, MB85);
+        else WC_LAUNCH(2, 1);
+    }
+#undef WC_LAUNCH
+    return cudaGetLastError();
+}
+
+std::mutex g_shape_mutex;
+std::map<std::array<int, 6>, int> g_shape_choice;   // (L, prec, kind) -> shape index
+
+// Time every fitting shape (3 launches each after one warm-up) and keep the
+// fastest.  Needs an uncaptured stream; out is overwritten by the real
+// launch that follows.
+template <class P>
+int tune_shape(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t stream)
+{
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 0;
+    }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int i = 0; i < kNumShapes; ++i) {
+        if (!shape_fits(lat->g, kShapes[i], std::is_same<P, P64>::value)) continue;
+        if (launch_shape<P>(lat, out, in, kind, kShapes[i], stream) != cudaSuccess) continue;
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < 3; ++r) launch_shape<P>(lat, out, in, kind, kShapes[i], stream);
+        cudaEventRecord(e1, stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    return best;
+}
+
 template <class P>
 cudaError_t launch_apply_p(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t stream)
 {
-    const int V = lat->g.V;
-    dim3 grid((V + kApplyBlock - 1) / kApplyBlock), block(kApplyBlock);
-    if (kind == 0)
-        k_apply<P, 0><<<grid, block, 0, stream>>>(lat->g, lat->gauge, lat->clover, in->data, in->nrm,
-                                                       out->data, out->nrm, lat->kappa);
-    else if (kind == 1)
-        k_apply<P, 1><<<grid, block, 0, stream>>>(lat->g, lat->gauge, lat->clover, in->data, in->nrm,
-                                                       out->data, out->nrm, lat->kappa);
-    else
-        k_apply<P, 2><<<grid, block, 0, stream>>>(lat->g, lat->gauge, lat->clover, in->data, in->nrm,
-                                                       out->data, out->nrm, lat->kappa);
-    return cudaGetLastError();
+    const std::array<int, 6> key = {lat->g.L[0], lat->g.L[1], lat->g.L[2], lat->g.L[3], (int)in->prec, kind};
+    int choice = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mutex);
+        auto it = g_shape_choice.find(key);
+        if (it != g_shape_choice.end()) choice = it->second;
+    }
+    if (choice < 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(stream, &cs);
+        if (cs != cudaStreamCaptureStatusNone) {
+            choice = 0;   // no timing inside a capture: default shape, not cached
+        } else {
+            choice = tune_shape<P>(lat, out, in, kind, stream);
+            std::lock_guard<std::mutex> lk(g_shape_mutex);
+            g_shape_choice[key] = choice;
+        }
+    }
+    return launch_shape<P>(lat, out, in, kind, kShapes[choice], stream);
 }
 
 // ------------------------------------------------------------------------
@@ -151,6 +294,29 @@ cudaError_t launch_copy_s(wc_lattice lat, wc_field dst, wc_field src, double sca
 }
 
 }  // namespace
+
+// Query or pin the launch shape of (lat extent, prec, kind): force >= 0 pins
+// shape #force (false if it does not fit); out = {threads, tile[4], capped},
+// all -1 when no shape was chosen yet.
+bool apply_shape(wc_lattice lat, wc_prec prec, int kind, int force, int out[6])
+{
+    const std::array<int, 6> key = {lat->g.L[0], lat->g.L[1], lat->g.L[2], lat->g.L[3], (int)prec, kind};
+    for (int i = 0; i < 6; ++i) out[i] = -1;
+    std::lock_guard<std::mutex> lk(g_shape_mutex);
+    if (force >= 0) {
+        if (force >= kNumShapes || !shape_fits(lat->g, kShapes[force], prec == WC_F64)) return false;
+        g_shape_choice[key] = force;
+    }
+    auto it = g_shape_choice.find(key);
+    if (it == g_shape_choice.end()) return true;
+    const ApplyShape &s = kShapes[it->second];
+    out[0] = s.threads;
+    for (int m = 0; m < 4; ++m) out[1 + m] = s.tile[m];
+    out[5] = s.capped;
+    return true;
+}
+
+int apply_shape_count() { return kNumShapes; }
 
 cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t stream)
 {

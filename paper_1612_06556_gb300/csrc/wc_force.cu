@@ -84,8 +84,7 @@ __device__ __forceinline__ void add_scaled(M3 &acc, cx<double> s, const M3 &a)
 __device__ M3 link(const GaugeStore &g, int V, int mu, int x)
 {
     cx<double> u[6], r2[3];
-    P64::load_link(g, V, mu, x, u);
-    reconstruct_row2(u, r2);
+    P64::load_link(g, V, mu, x, u, r2);
     M3 r;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {

@@ -6,9 +6,13 @@
 //           F32: float4  [6][V]        chunk j = components 2j, 2j+1
 //           F16: uint4   [3][V]        chunk j = components 4j..4j+3 (half2
 //                each), times float scale[V] (max |real| of the site)
-//   links   rows 0 and 1 of U_mu(x) (6 complex, row-major); row 2 is
-//           rebuilt as conj(row0 x row1) (paper Sec. 2, SU(3) reconstruction)
-//           F64: double2 [4][6][V]     F32: float4 [4][3][V]
+//   links   FP32/FP16: rows 0 and 1 of U_mu(x) (6 complex, row-major); row 2
+//           is rebuilt in registers as conj(row0 x row1) (paper Sec. 2,
+//           SU(3) reconstruction) -- these kernels are bandwidth-bound.
+//           FP64: all three rows, the third computed once at load time by
+//           the same formula: on GB300 the FP64 operator is bound by the
+//           FP64 pipe, not by bandwidth, so the rebuild is not repeated.
+//           F64: double2 [4][9][V]     F32: float4 [4][3][V]
 //           F16: uint4 [4][V] (complex 0..3) + uint2 [4][V] (complex 4, 5)
 //   clover  A = 1 + T as two Hermitian 6x6 blocks (spins {0,1} and {2,3},
 //           index 3*s_local + colour): per block 6 real diagonal entries then
@@ -109,7 +113,7 @@ __device__ __forceinline__ void site_coords(const Geom &g, int s, int c[4])
 // ------------------------------------------------------------------------
 
 struct GaugeStore {
-    double2 *u64 = nullptr;   // [4][6][V]
+    double2 *u64 = nullptr;   // [4][9][V]
     float4 *u32 = nullptr;    // [4][3][V]
     uint4 *u16a = nullptr;    // [4][V]
     uint2 *u16b = nullptr;    // [4][V]
@@ -159,6 +163,15 @@ __device__ __forceinline__ unsigned c2h(float re, float im)
     return *reinterpret_cast<unsigned *>(&h);
 }
 
+// third row of an SU(3) matrix from its first two: c = conj(a x b)
+template <class R>
+__device__ __forceinline__ void reconstruct_row2(const cx<R> u[6], cx<R> c[3])
+{
+    c[0] = conj(u[1] * u[5] - u[2] * u[4]);
+    c[1] = conj(u[2] * u[3] - u[0] * u[5]);
+    c[2] = conj(u[0] * u[4] - u[1] * u[3]);
+}
+
 struct P64 {
     using real = double;
     static __device__ __forceinline__ void load_spinor(const void *d, const float *, int V, int x,
@@ -178,15 +191,20 @@ struct P64 {
 #pragma unroll
         for (int k = 0; k < 12; ++k) p[(size_t)k * V + x] = make_double2(s[k].re, s[k].im);
     }
-    // rows 0 and 1 of U_mu(x): a[0..2] = row 0, a[3..5] = row 1
+    // U_mu(x): a[0..2] = row 0, a[3..5] = row 1, c[0..2] = row 2
     static __device__ __forceinline__ void load_link(const GaugeStore &g, int V, int mu, int x,
-                                                     cx<double> a[6])
+                                                     cx<double> a[6], cx<double> c[3])
     {
-        const double2 *p = g.u64 + (size_t)mu * 6 * V + x;
+        const double2 *p = g.u64 + (size_t)mu * 9 * V + x;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             double2 v = __ldg(p + (size_t)k * V);
             a[k] = {v.x, v.y};
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double2 v = __ldg(p + (size_t)(6 + k) * V);
+            c[k] = {v.x, v.y};
         }
     }
     // the 36 reals of clover block b
@@ -225,7 +243,7 @@ struct P32 {
             p[(size_t)j * V + x] = make_float4(s[2 * j].re, s[2 * j].im, s[2 * j + 1].re, s[2 * j + 1].im);
     }
     static __device__ __forceinline__ void load_link(const GaugeStore &g, int V, int mu, int x,
-                                                     cx<float> a[6])
+                                                     cx<float> a[6], cx<float> c[3])
     {
         const float4 *p = g.u32 + (size_t)mu * 3 * V + x;
 #pragma unroll
@@ -234,6 +252,7 @@ struct P32 {
             a[2 * j] = {v.x, v.y};
             a[2 * j + 1] = {v.z, v.w};
         }
+        reconstruct_row2(a, c);
     }
     static __device__ __forceinline__ void load_clover(const CloverStore &c, int V, int x, int b,
                                                        float r[36])
@@ -286,7 +305,7 @@ struct P16 {
         nrm[x] = m;
     }
     static __device__ __forceinline__ void load_link(const GaugeStore &g, int V, int mu, int x,
-                                                     cx<float> a[6])
+                                                     cx<float> a[6], cx<float> c[3])
     {
         uint4 v = __ldg(g.u16a + (size_t)mu * V + x);
         uint2 w = __ldg(g.u16b + (size_t)mu * V + x);
@@ -296,6 +315,7 @@ struct P16 {
         a[3] = h2c(v.w);
         a[4] = h2c(w.x);
         a[5] = h2c(w.y);
+        reconstruct_row2(a, c);
     }
     static __device__ __forceinline__ void load_clover(const CloverStore &c, int V, int x, int b,
                                                        float r[36])
@@ -314,15 +334,6 @@ struct P16 {
         }
     }
 };
-
-// third row of an SU(3) matrix from its first two: c = conj(a x b)
-template <class R>
-__device__ __forceinline__ void reconstruct_row2(const cx<R> u[6], cx<R> c[3])
-{
-    c[0] = conj(u[1] * u[5] - u[2] * u[4]);
-    c[1] = conj(u[2] * u[3] - u[0] * u[5]);
-    c[2] = conj(u[0] * u[4] - u[1] * u[3]);
-}
 
 // Hermitian 6x6 block (packed) times a 6-vector: y = B v
 template <class R>
@@ -365,14 +376,14 @@ int sm_count();
 namespace wc {
 
 // Per-solve state: device scalars and their pinned host mirror, reduction
-// scratch, solver work fields (created on first use: slots 0-9 FP64, 10-11
-// FP32, 12-13 FP16) and the stream the solve is queued on.  A lattice owns
+// scratch, solver work fields (created on first use: slots 0-9 FP64, 10-21
+// FP32, 22-23 FP16) and the stream the solve is queued on.  A lattice owns
 // one for its single-RHS calls; a batched solve creates one per RHS.
 struct SolverState {
     SolverScalars *scal = nullptr;
     SolverScalars *scal_host = nullptr;
     ReduceScratch red;
-    wc_field_s *work[16] = {};
+    wc_field_s *work[24] = {};
     cudaStream_t stream = nullptr;
 };
 
@@ -415,6 +426,9 @@ cudaError_t launch_copy(wc_lattice lat, wc_field dst, wc_field src, double scale
                         int invert_scale, cudaStream_t stream);
 cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params &p, int dagger,
                        cudaStream_t stream);
+
+bool apply_shape(wc_lattice lat, wc_prec prec, int kind, int force, int out[6]);
+int apply_shape_count();
 
 // solver states
 wc_status state_init(wc_lattice lat, SolverState &s);

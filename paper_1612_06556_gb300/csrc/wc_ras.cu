@@ -19,9 +19,9 @@
 // is parked in shared memory and the q of its second stays in registers
 // across the block-wide reduction of <q, r> and <q, q> (4^4 blocks with
 // overlap 1: 1296 sites, 672 threads, 211 KB of shared memory, one CTA per
-// SM).  <q, r> and <q, q> are summed in FP32 within warps and in FP64 over
-// the warps by a single thread, which keeps the FP64 pipe -- 1/64 of the
-// FP32 rate on GB300 -- out of the inner loop.  Links and clover are read from
+// SM).  <q, r> and <q, q> are summed in FP32 (GB300's FP64 pipe runs at
+// 1/64 of the FP32 rate) with one barrier per MR step for the reduction and
+// one before the next sweep reads the updated r.  Links and clover are read from
 // global memory (L2-resident across the k sweeps of a block).  Arithmetic is
 // FP32 for FP32 and FP16 storage.
 #include "wc_internal.cuh"
@@ -46,31 +46,30 @@ struct RasGeom {
 };
 
 // alpha = <q, r> / <q, q> from per-thread FP32 partials: lanes are summed
-// in FP32, the warp sums in FP64 by one thread, which also divides and
-// broadcasts alpha (FP32) through shared memory.  On GB300 the FP64 pipe
-// runs at 1/64 of the FP32 rate, so no other thread touches FP64.
-__device__ __forceinline__ cx<float> block_alpha(const float v[3], double *sm /*[32*3]*/, float2 *bcast)
+// by warp shuffles, the warp sums are published in shared memory and every
+// warp then adds them in the same fixed order, so all threads get the same
+// alpha after a single barrier.  FP32 throughout: the FP64 pipe of GB300
+// runs at 1/64 of the FP32 rate, and alpha only steers a preconditioner.
+__device__ __forceinline__ cx<float> block_alpha(const float v[3], float *sm /*[32*3]*/)
 {
     float w[3] = {v[0], v[1], v[2]};
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w[i] += __shfl_down_sync(0xffffffffu, w[i], o);
+        for (int o = 16; o > 0; o >>= 1) w[i] += __shfl_xor_sync(0xffffffffu, w[i], o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) sm[wid * 3 + i] = (double)w[i];
+        for (int i = 0; i < 3; ++i) sm[wid * 3 + i] = w[i];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t[3] = {0.0, 0.0, 0.0};
-        for (int k = 0; k < nw; ++k)
+    float t[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) t[i] += sm[k * 3 + i];
-        *bcast = t[2] > 0.0 ? make_float2((float)(t[0] / t[2]), (float)(t[1] / t[2])) : make_float2(0.f, 0.f);
+    for (int i = 0; i < 3; ++i) {
+        t[i] = lane < nw ? sm[lane * 3 + i] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t[i] += __shfl_xor_sync(0xffffffffu, t[i], o);
     }
-    __syncthreads();
-    const float2 a = *bcast;
-    return mkc(a.x, a.y);
+    return t[2] > 0.f ? mkc(t[0] / t[2], t[1] / t[2]) : mkc(0.f, 0.f);
 }
 
 // q += -kappa * (forward and backward hop in direction MU), both dropped
@@ -90,8 +89,7 @@ __device__ __forceinline__ void ras_hops(const Geom &g, const RasGeom &rg, const
             const float2 v = r[k * rg.ne + lf];
             return mkc(v.x, v.y);
         }, h);
-        P::load_link(U, g.V, MU, site, u);
-        reconstruct_row2(u, r2);
+        P::load_link(U, g.V, MU, site, u, r2);
         su3_mul(u, r2, h, coef, w);
         reconstruct_add<MU, SF>(q, w);
     }
@@ -104,8 +102,7 @@ __device__ __forceinline__ void ras_hops(const Geom &g, const RasGeom &rg, const
             const float2 v = r[k * rg.ne + lb];
             return mkc(v.x, v.y);
         }, h);
-        P::load_link(U, g.V, MU, sb, u);
-        reconstruct_row2(u, r2);
+        P::load_link(U, g.V, MU, sb, u, r2);
         su3_adj_mul(u, r2, h, coef, w);
         reconstruct_add<MU, -SF>(q, w);
     }
@@ -120,8 +117,7 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
     float2 *r = reinterpret_cast<float2 *>(smem_raw);               // [12][ne]
     float2 *qs = r + 12 * rg.ne;                                     // [12][blockDim.x]
     float2 *xc = qs + 12 * blockDim.x;                               // [12][ncore]
-    __shared__ double red[32 * 3];
-    __shared__ float2 alpha_bcast;
+    __shared__ float red[32 * 3];
 
     // block origin
     int bc[4];
@@ -220,7 +216,7 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
             }
         }
         // contains __syncthreads: every read of r is done after it
-        const cx<float> alpha = block_alpha(acc, red, &alpha_bcast);
+        const cx<float> alpha = block_alpha(acc, red);
         // x += alpha r, r -= alpha q on this thread's sites
 #pragma unroll
         for (int j = 0; j < kRasSPT; ++j) {

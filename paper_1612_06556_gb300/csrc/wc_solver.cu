@@ -80,7 +80,7 @@ wc_status solver_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &
     if (st == WC_OK && p.precond == WC_PRECOND_RAS) {
         w->phat = state_work(lat, S, 6, WC_F64, &st);
         if (st == WC_OK) w->shat = state_work(lat, S, 7, WC_F64, &st);
-        const int lo = p.inner_prec == WC_F16 ? 12 : 10;
+        const int lo = p.inner_prec == WC_F16 ? 22 : 10;
         if (st == WC_OK) w->lo_in = state_work(lat, S, lo, p.inner_prec, &st);
         if (st == WC_OK) w->lo_out = state_work(lat, S, lo + 1, p.inner_prec, &st);
     }
@@ -134,6 +134,8 @@ wc_status enqueue_true_residual(wc_lattice lat, SolverState &S, int kind, wc_fie
 
 static wc_status bicgstab_impl(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
                                const wc_solve_params &p, double bb, wc_solve_info *info, int iters_done);
+wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
+                            const wc_solve_params &p, wc_solve_info *info, int iters_done, double bb);
 
 // Solve op x = b (op = M for kind 0, M^+ for kind 1); x, b FP64 fields.
 // S: solver state (scratch); S.stream: the stream everything is queued on.
@@ -144,7 +146,9 @@ wc_status bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_fiel
     wc_solve_info *out = info ? info : &local;
     *out = wc_solve_info{};
     out->status = WC_ERR_CUDA;
-    const wc_status st = bicgstab_impl(lat, S, kind, x, b, p, bb, out, iters_done);
+    const wc_status st = (p.precond == WC_PRECOND_RAS && p.solver == WC_SOLVER_RELIABLE)
+                             ? reliable_bicgstab(lat, S, kind, x, b, p, out, iters_done, bb)
+                             : bicgstab_impl(lat, S, kind, x, b, p, bb, out, iters_done);
     if (st != WC_OK && (out->status == WC_OK || out->status == WC_ERR_CUDA)) out->status = st;
     return st;
 }
@@ -246,6 +250,219 @@ static wc_status bicgstab_impl(wc_lattice lat, SolverState &S, int kind, wc_fiel
     return result;
 }
 
+// ------------------------------------------------------------------------
+// Reliable-update solve: BiCGStab in FP32 with FP64 refreshes
+// ------------------------------------------------------------------------
+
+namespace {
+
+float4 *f4(wc_field f) { return static_cast<float4 *>(f->data); }
+
+}  // namespace
+
+wc_status lo_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &p, LoVecs *w)
+{
+    wc_status st = WC_OK;
+    wc_field *slots[9] = {&w->r, &w->rhat, &w->p, &w->v, &w->s, &w->t, &w->phat, &w->shat, &w->xlo};
+    for (int i = 0; i < 9 && st == WC_OK; ++i) *slots[i] = state_work(lat, S, 12 + i, WC_F32, &st);
+    w->lo_in = w->lo_out = nullptr;
+    if (st == WC_OK && p.inner_prec == WC_F16) {
+        w->lo_in = state_work(lat, S, 22, WC_F16, &st);
+        if (st == WC_OK) w->lo_out = state_work(lat, S, 23, WC_F16, &st);
+    }
+    return st;
+}
+
+namespace {
+
+// uhat = RAS(u) for FP32 u (through FP16 storage when inner_prec is FP16)
+wc_status lo_precond(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind, const LoVecs &w,
+                     wc_field u, wc_field uhat)
+{
+    if (p.inner_prec != WC_F16) return check_cuda(lat, launch_ras(lat, uhat, u, p.ras, kind, S.stream), "ras");
+    wc_status st = check_cuda(lat, launch_copy(lat, w.lo_in, u, 1.0, nullptr, 0, S.stream), "cast to FP16");
+    if (st == WC_OK) st = check_cuda(lat, launch_ras(lat, w.lo_out, w.lo_in, p.ras, kind, S.stream), "ras");
+    if (st == WC_OK) st = check_cuda(lat, launch_copy(lat, uhat, w.lo_out, 1.0, nullptr, 0, S.stream), "cast");
+    return st;
+}
+
+}  // namespace
+
+wc_status enqueue_lo_iteration(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind,
+                               const LoVecs &w)
+{
+    wc_status st = check_cuda(lat, lo_p(lat, S, f4(w.r), f4(w.v), f4(w.p)), "lo_p");
+    if (st == WC_OK) st = lo_precond(lat, S, p, kind, w, w.p, w.phat);
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.v, w.phat, kind, S.stream), "apply");
+    if (st == WC_OK) st = check_cuda(lat, lo_alpha(lat, S, f4(w.rhat), f4(w.v)), "lo_alpha");
+    if (st == WC_OK) st = check_cuda(lat, lo_s(lat, S, f4(w.r), f4(w.v), f4(w.s)), "lo_s");
+    if (st == WC_OK) st = lo_precond(lat, S, p, kind, w, w.s, w.shat);
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.t, w.shat, kind, S.stream), "apply");
+    if (st == WC_OK) st = check_cuda(lat, lo_omega(lat, S, f4(w.t), f4(w.s)), "lo_omega");
+    if (st == WC_OK)
+        st = check_cuda(lat, lo_xr(lat, S, f4(w.xlo), f4(w.phat), f4(w.shat), f4(w.s), f4(w.t), f4(w.r), f4(w.rhat)),
+                        "lo_xr");
+    return st;
+}
+
+wc_status enqueue_refresh_full(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
+                               const LoVecs &w);
+
+wc_status enqueue_lo_start(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
+                           const LoVecs &w)
+{
+    wc_status st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S.stream), "apply");
+    if (st == WC_OK)
+        st = check_cuda(lat, residual(lat, S, static_cast<const double2 *>(b->data),
+                                      static_cast<double2 *>(r_hp->data)), "residual");
+    if (st == WC_OK) st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
+    if (st == WC_OK)
+        st = check_cuda(lat, lo_init(lat, S, f4(w.r), f4(w.rhat), f4(w.p), f4(w.v), f4(w.xlo)), "lo_init");
+    return st;
+}
+
+// x += xlo; r_hp = b - op x (FP64); S.scal->rr = |r_hp|^2
+static wc_status enqueue_refresh(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
+                                 const LoVecs &w)
+{
+    wc_status st = check_cuda(lat, hp_add_lo(lat, S, static_cast<double2 *>(x->data), f4(w.xlo)), "hp_add_lo");
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S.stream), "apply");
+    if (st == WC_OK)
+        st = check_cuda(lat, residual(lat, S, static_cast<const double2 *>(b->data), static_cast<double2 *>(r_hp->data)),
+                        "residual");
+    return st;
+}
+
+wc_status enqueue_refresh_full(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
+                               const LoVecs &w)
+{
+    wc_status st = enqueue_refresh(lat, S, kind, x, b, r_hp, w);
+    if (st == WC_OK) st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
+    if (st == WC_OK) st = check_cuda(lat, lo_rho(lat, S, f4(w.rhat), f4(w.r)), "lo_rho");
+    return st;
+}
+
+wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
+                            const wc_solve_params &p, wc_solve_info *info, int iters_done, double bb)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    wc_solve_info &inf = *info;
+    inf = wc_solve_info{};
+    inf.iters = iters_done;
+    inf.status = WC_ERR_NOT_CONVERGED;
+    wc_status st = WC_OK;
+    wc_field r_hp = state_work(lat, S, 0, WC_F64, &st);
+    LoVecs w;
+    if (st == WC_OK) st = lo_vectors(lat, S, p, &w);
+    if (st != WC_OK) return st;
+    if (bb < 0.0) {
+        st = check_cuda(lat, norm2_to_result(lat, S, static_cast<const double2 *>(b->data)), "norm2");
+        if (st == WC_OK)
+            st = check_cuda(lat, cudaMemcpyAsync(S.red.host_result, S.red.result, sizeof(double),
+                                                 cudaMemcpyDeviceToHost, S.stream), "copy");
+        if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(S.stream), "sync");
+        if (st != WC_OK) return st;
+        bb = S.red.host_result[0];
+    }
+    if (!isfinite(bb)) {
+        inf.status = WC_ERR_NAN;
+        return set_error(lat, WC_ERR_NAN, "source has non-finite entries");
+    }
+    if (bb == 0.0) {
+        st = check_cuda(lat, cudaMemsetAsync(x->data, 0, spinor_bytes(WC_F64, lat->g.V), S.stream), "memset");
+        if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(S.stream), "sync");
+        inf.status = st;
+        return st;
+    }
+    const double tol2 = p.tol * p.tol * bb;
+    const double delta = (p.delta > 0.0 && p.delta < 1.0) ? p.delta : 0.1;
+    const double d2 = delta * delta;
+    wc_status result = WC_ERR_NOT_CONVERGED;
+    for (int restart = 0; restart <= p.max_restarts; ++restart) {
+        inf.restarts = restart;
+        // true residual, FP32 copy, BiCGStab state reset (xlo = 0)
+        st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S.stream), "apply");
+        if (st == WC_OK)
+            st = check_cuda(lat, residual(lat, S, static_cast<const double2 *>(b->data),
+                                          static_cast<double2 *>(r_hp->data)), "residual");
+        if (st == WC_OK) st = read_scalars(lat, S);
+        if (st != WC_OK) return st;
+        double rr_true = S.scal_host->rr;
+        inf.true_rel_resid = sqrt(rr_true / bb);
+        if (!isfinite(rr_true)) {
+            result = set_error(lat, WC_ERR_NAN, "non-finite residual");
+            break;
+        }
+        if (rr_true <= tol2) {
+            result = WC_OK;
+            break;
+        }
+        st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
+        if (st == WC_OK)
+            st = check_cuda(lat, lo_init(lat, S, f4(w.r), f4(w.rhat), f4(w.p), f4(w.v), f4(w.xlo)), "lo_init");
+        if (st != WC_OK) return st;
+        double rmax2 = rr_true;
+        bool breakdown = false, converged = false;
+        while (inf.iters < p.max_iter) {
+            st = enqueue_lo_iteration(lat, S, p, kind, w);
+            if (st == WC_OK) st = read_scalars(lat, S);
+            if (st != WC_OK) return st;
+            ++inf.iters;
+            const SolverScalars h = *S.scal_host;
+            if (h.flags & FLAG_NAN) {
+                result = set_error(lat, WC_ERR_NAN, "non-finite value in BiCGStab");
+                break;
+            }
+            if (h.flags & FLAG_BREAKDOWN) {
+                breakdown = true;
+                break;
+            }
+            if (h.rr > rmax2) rmax2 = h.rr;
+            if (h.rr <= d2 * rmax2 || h.rr <= tol2) {
+                // reliable update: fold the FP32 correction into the FP64
+                // solution and restart the recurrence from the true residual
+                st = enqueue_refresh(lat, S, kind, x, b, r_hp, w);
+                if (st == WC_OK) st = read_scalars(lat, S);
+                if (st != WC_OK) return st;
+                rr_true = S.scal_host->rr;
+                inf.true_rel_resid = sqrt(rr_true / bb);
+                if (rr_true <= tol2) {
+                    converged = true;
+                    break;
+                }
+                st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
+                if (st == WC_OK) st = check_cuda(lat, lo_rho(lat, S, f4(w.rhat), f4(w.r)), "lo_rho");
+                if (st != WC_OK) return st;
+                rmax2 = rr_true;
+            }
+        }
+        if (result == WC_ERR_NAN) break;
+        if (converged) {
+            result = WC_OK;
+            break;
+        }
+        // fold whatever correction is pending and test the true residual
+        st = enqueue_refresh(lat, S, kind, x, b, r_hp, w);
+        if (st == WC_OK) st = read_scalars(lat, S);
+        if (st != WC_OK) return st;
+        rr_true = S.scal_host->rr;
+        inf.true_rel_resid = sqrt(rr_true / bb);
+        if (rr_true <= tol2) {
+            result = WC_OK;
+            break;
+        }
+        if (inf.iters >= p.max_iter) {
+            result = set_error(lat, WC_ERR_NOT_CONVERGED, "max_iter reached");
+            break;
+        }
+        result = set_error(lat, breakdown ? WC_ERR_BREAKDOWN : WC_ERR_NOT_CONVERGED,
+                           breakdown ? "BiCGStab breakdown" : "true residual above tol after all restarts");
+    }
+    inf.status = result;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return result;
+}
+
 wc_status check_solve_args(wc_lattice lat, wc_field x, wc_field b, const wc_solve_params *p)
 {
     if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
@@ -257,6 +474,12 @@ wc_status check_solve_args(wc_lattice lat, wc_field x, wc_field b, const wc_solv
         return set_error(lat, WC_ERR_ARG, "tol must be > 0, max_iter and max_restarts >= 0");
     if (p->precond != WC_PRECOND_NONE && p->precond != WC_PRECOND_RAS)
         return set_error(lat, WC_ERR_ARG, "unknown preconditioner");
+    if (p->solver != WC_SOLVER_FLEXIBLE && p->solver != WC_SOLVER_RELIABLE)
+        return set_error(lat, WC_ERR_ARG, "unknown solver kind");
+    if (p->solver == WC_SOLVER_RELIABLE && p->precond != WC_PRECOND_RAS)
+        return set_error(lat, WC_ERR_ARG, "the reliable-update solver needs the RAS preconditioner");
+    if (p->solver == WC_SOLVER_RELIABLE && !(p->delta >= 0.0 && p->delta < 1.0))
+        return set_error(lat, WC_ERR_ARG, "delta must be in [0, 1)");
     if (p->precond == WC_PRECOND_RAS) {
         if (p->inner_prec != WC_F32 && p->inner_prec != WC_F16)
             return set_error(lat, WC_ERR_ARG, "RAS inner precision must be WC_F32 or WC_F16");

@@ -35,6 +35,25 @@ wc_status bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_fiel
 // Same with the lattice's own state and stream.
 wc_status bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p, wc_solve_info *info);
 
+// FP32 vectors of the reliable-update solver (r, rhat, p, v, s, t, phat,
+// shat, xlo FP32; lo_in/lo_out FP16 casts of the RAS input/output when the
+// inner precision is FP16)
+struct LoVecs {
+    wc_field r, rhat, p, v, s, t, phat, shat, xlo, lo_in, lo_out;
+};
+wc_status lo_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &p, LoVecs *w);
+// one FP32 BiCGStab step (scalars on the device)
+wc_status enqueue_lo_iteration(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind,
+                               const LoVecs &w);
+// reliable update: x += xlo; r_hp = b - op x (FP64, S.scal->rr = |r_hp|^2);
+// r = fl32(r_hp); rho and beta recomputed
+wc_status enqueue_refresh_full(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
+                               const LoVecs &w);
+// start of a reliable solve: r_hp = b - op x; r = fl32(r_hp); rhat = r,
+// p = v = xlo = 0, scalars reset (rr = |r|^2 of the FP32 copy)
+wc_status enqueue_lo_start(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
+                           const LoVecs &w);
+
 cudaError_t ras_prepare();
 
 }  // namespace wc

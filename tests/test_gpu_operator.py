@@ -141,3 +141,32 @@ def test_apply_argument_errors():
     with pytest.raises(w.WCError) as e:
         lat.apply_M(lat.field(0), a)
     assert e.value.status == 1
+
+
+N_SHAPES = 16
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_every_launch_shape_matches_oracle(prec):
+    """Each candidate launch shape of the autotuner (lexicographic and tiled
+    site maps, register caps) computes the same operator."""
+    w = wc()
+    dims, kappa, csw, tbc = (8, 8, 4, 4), 0.124, 1.2, -1
+    U = synth.exp_links(dims, 0.4, 61)
+    psi = synth.gaussian_source(dims, 62)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    ref = oracle.apply_M(dims, tbc, kappa, csw, U, psi)
+    refd = oracle.Operator(dims, U, csw, kappa, tbc).Mdag(psi)
+    tested = 0
+    for i in range(N_SHAPES):
+        try:
+            lat.apply_shape(prec, 0, force=i)
+            lat.apply_shape(prec, 1, force=i)
+        except w.WCError:
+            continue
+        assert_elementwise(gpu_apply(lat, psi, prec, "M"), ref, TOL[prec])
+        assert_elementwise(gpu_apply(lat, psi, prec, "Mdag"), refd, TOL[prec])
+        tested += 1
+    assert tested == (7 if prec == 0 else 16)   # FP64 takes no register-capped shape
+    with pytest.raises(w.WCError):
+        lat.apply_shape(prec, 0, force=N_SHAPES)

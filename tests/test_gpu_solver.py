@@ -201,3 +201,62 @@ def test_batch_solve_masks_and_errors():
     assert [i.status for i in infos] == [4, 4] and [i.iters for i in infos] == [2, 2]
     with pytest.raises(w.WCError):
         w.solve_batch([lat, lat], [xs[0], xs[0]], [bs[0], bs[2]], tol=1e-10)
+
+
+@pytest.mark.parametrize("inner", [1, 2])
+def test_reliable_update_solver(inner):
+    """FP32 BiCGStab + RAS with FP64 reliable updates reaches the FP64 true
+    residual tolerance; checked with the oracle's M."""
+    w = wc()
+    dims, kappa, csw, tbc = (8, 8, 8, 16), 0.125, 1.0, -1
+    U = synth.exp_links(dims, 0.3, 121)
+    src = synth.gaussian_source(dims, 122)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    x, b = lat.field(0), lat.field(0).load(src)
+    info = lat.solve(x, b, tol=1e-10, precond=w.PRECOND_RAS, inner_prec=inner, solver=w.SOLVER_RELIABLE,
+                     delta=0.1)
+    assert info.status == 0 and info.true_rel_resid <= 1e-10
+    sol = x.store(np.zeros_like(src))
+    r = src - oracle.apply_M(dims, tbc, kappa, csw, U, sol)
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+    x2 = lat.field(0)
+    info2 = lat.solve(x2, b, tol=1e-10, precond=w.PRECOND_RAS, inner_prec=inner)
+    assert info.iters <= 3 * info2.iters + 5
+    # M^+ through the action: reliable and flexible give the same S
+    F = np.zeros((synth.volume(dims), 4, 3, 3), complex)
+    phi = lat.field(0).load(src)
+    S1 = lat.action_force(phi, F, tol=1e-12, precond=w.PRECOND_RAS, inner_prec=inner, solver=w.SOLVER_RELIABLE)
+    S2 = lat.action_force(phi, F, tol=1e-12)
+    assert abs(S1 - S2) <= 1e-9 * S2
+
+
+def test_reliable_update_argument_errors():
+    w = wc()
+    dims = (8, 8, 8, 8)
+    lat = make_lattice(dims, synth.unit_links(dims), 1.0, 0.1, -1)
+    x, b = lat.field(0), lat.field(0).load(synth.gaussian_source(dims, 1))
+    with pytest.raises(w.WCError) as e:
+        lat.solve(x, b, solver=w.SOLVER_RELIABLE)                      # needs RAS
+    assert e.value.status == 1
+    with pytest.raises(w.WCError) as e:
+        lat.solve(x, b, precond=w.PRECOND_RAS, solver=w.SOLVER_RELIABLE, delta=1.5)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("inner", [1, 2])
+def test_batch_solve_reliable_update(inner):
+    """The reliable-update solver inside the batch graph (FP32 steps, FP64
+    refreshes as conditional graph nodes) on uneven lattices."""
+    w = wc()
+    lats, xs, bs, srcs, ops = _batch_problem(w, [(6, 6, 6, 8), (8, 8, 8, 12)], 3)
+    infos = w.solve_batch(lats, xs, bs, tol=1e-10, precond=w.PRECOND_RAS, inner_prec=inner, block=(2, 2, 2, 2),
+                          solver=w.SOLVER_RELIABLE, delta=0.1)
+    for info, x, src, (dims, U) in zip(infos, xs, srcs, ops):
+        assert info.status == 0 and info.true_rel_resid <= 1e-10
+        sol = x.store(np.zeros_like(src))
+        r = src - oracle.apply_M(dims, -1, 0.124, 1.0, U, sol)
+        assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+    xs2 = [lat.field(0) for lat in lats]
+    infos2 = w.solve_batch(lats, xs2, bs, tol=1e-12, max_iter=3, precond=w.PRECOND_RAS, inner_prec=inner,
+                           block=(2, 2, 2, 2), solver=w.SOLVER_RELIABLE, check=False)
+    assert all(i.status == 4 and i.iters == 3 for i in infos2)
