@@ -564,19 +564,30 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_s(long long n, const float4 *r
 __global__ void __launch_bounds__(kRedBlock) k_lo_omega(long long n, const float4 *t, const float4 *s,
                                                         ReduceScratch rs, SolverScalars *sc)
 {
-    float acc[3] = {0.f, 0.f, 0.f};
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const float4 a = t[i], b = s[i];
         acc[0] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc[0]))));
         acc[1] = fmaf(a.x, b.y, fmaf(-a.y, b.x, fmaf(a.z, b.w, fmaf(-a.w, b.z, acc[1]))));
         acc[2] = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, acc[2]))));
+        acc[3] = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, acc[3]))));
     }
-    if (grid_reduce_f<3>(acc, rs, rs.result)) {
-        const double tt = rs.result[2];
+    if (grid_reduce_f<4>(acc, rs, rs.result)) {
+        const double tr = rs.result[0], ti = rs.result[1], tt = rs.result[2], ss = rs.result[3];
         sc->tt = tt;
-        if (!isfinite(tt) || !isfinite(rs.result[0]) || !isfinite(rs.result[1])) sc->flags |= FLAG_NAN;
-        sc->omega = tt > 0.0 ? make_double2(rs.result[0] / tt, rs.result[1] / tt) : make_double2(0.0, 0.0);
+        if (!isfinite(tt) || !isfinite(tr) || !isfinite(ti) || !isfinite(ss)) sc->flags |= FLAG_NAN;
+        double2 om = tt > 0.0 ? make_double2(tr / tt, ti / tt) : make_double2(0.0, 0.0);
+        // omega stabilisation (Sleijpen & van der Vorst): when t and s are
+        // nearly orthogonal, |<t,s>| / (|t||s|) < 0.7, the minimising omega is
+        // tiny and BiCGStab loses accuracy in finite precision; enlarge it
+        const double rho_t = (tt > 0.0 && ss > 0.0) ? sqrt(tr * tr + ti * ti) / sqrt(tt * ss) : 1.0;
+        if (rho_t > 0.0 && rho_t < 0.7) {
+            const double f = 0.7 / rho_t;
+            om.x *= f;
+            om.y *= f;
+        }
+        sc->omega = om;
     }
 }
 

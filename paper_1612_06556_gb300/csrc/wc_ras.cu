@@ -72,36 +72,79 @@ __device__ __forceinline__ cx<float> block_alpha(const float v[3], float *sm /*[
     return t[2] > 0.f ? mkc(t[0] / t[2], t[1] / t[2]) : mkc(0.f, 0.f);
 }
 
+// Spinors in shared memory are float4 planes [6][n] paired by colour:
+// plane 2c holds spins 0 and 1 of colour c, plane 2c+1 spins 2 and 3
+// (component k = 3 spin + colour).  A spin projection of colour c is then
+// two 16-byte accesses, a clover block (spins 0,1 or 2,3) three, and a
+// warp's access to one plane is contiguous (conflict-free).
+__device__ __forceinline__ void sm_load(const float4 *a, int n, int i, cx<float> s[12])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float4 v = a[(2 * c) * n + i], w = a[(2 * c + 1) * n + i];
+        s[c] = mkc(v.x, v.y);
+        s[3 + c] = mkc(v.z, v.w);
+        s[6 + c] = mkc(w.x, w.y);
+        s[9 + c] = mkc(w.z, w.w);
+    }
+}
+
+__device__ __forceinline__ void sm_store(float4 *a, int n, int i, const cx<float> s[12])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a[(2 * c) * n + i] = make_float4(s[c].re, s[c].im, s[3 + c].re, s[3 + c].im);
+        a[(2 * c + 1) * n + i] = make_float4(s[6 + c].re, s[6 + c].im, s[9 + c].re, s[9 + c].im);
+    }
+}
+
+// spins 2b, 2b+1 (clover block b) of site i: v[3 s_local + c]
+__device__ __forceinline__ void sm_load_block(const float4 *a, int n, int i, int b, cx<float> v[6])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float4 t = a[(2 * c + b) * n + i];
+        v[c] = mkc(t.x, t.y);
+        v[3 + c] = mkc(t.z, t.w);
+    }
+}
+
+template <int MU, int S>
+__device__ __forceinline__ void project_sm(const float4 *a, int n, int i, cx<float> h[6])
+{
+    project_from<MU, S, float>(
+        [&](int c, cx<float> &u0, cx<float> &u1, cx<float> &d0, cx<float> &d1) {
+            const float4 v = a[(2 * c) * n + i], w = a[(2 * c + 1) * n + i];
+            u0 = mkc(v.x, v.y);
+            u1 = mkc(v.z, v.w);
+            d0 = mkc(w.x, w.y);
+            d1 = mkc(w.z, w.w);
+        },
+        h);
+}
+
 // q += -kappa * (forward and backward hop in direction MU), both dropped
 // when their target leaves the extended block.  SF = -1 for M (forward
 // projector 1 - gamma), +1 for M^+ = gamma5 M gamma5.
 template <class P, int MU, int SF>
-__device__ __forceinline__ void ras_hops(const Geom &g, const RasGeom &rg, const GaugeStore &U, const float2 *r,
+__device__ __forceinline__ void ras_hops(const Geom &g, const RasGeom &rg, const GaugeStore &U, const float4 *r,
                                          int l, int site, unsigned lpack, unsigned wbits, float mk, cx<float> q[12])
 {
     const int lm = (lpack >> (8 * MU)) & 255u;
     const int stl = rg.es[MU];
     if (lm + 1 < rg.e[MU]) {
-        const int lf = l + stl;
         const float coef = (MU == 3 && (wbits & (16u << 3))) ? mk * (float)g.tbc : mk;
         cx<float> h[6], u[6], r2[3], w[6];
-        project_from<MU, SF, float>([&](int k) {
-            const float2 v = r[k * rg.ne + lf];
-            return mkc(v.x, v.y);
-        }, h);
+        project_sm<MU, SF>(r, rg.ne, l + stl, h);
         P::load_link(U, g.V, MU, site, u, r2);
         su3_mul(u, r2, h, coef, w);
         reconstruct_add<MU, SF>(q, w);
     }
     if (lm >= 1) {
-        const int lb = l - stl;
         const int sb = (wbits & (1u << MU)) ? site + (g.L[MU] - 1) * g.stride[MU] : site - g.stride[MU];
         const float coef = (MU == 3 && (wbits & (1u << 3))) ? mk * (float)g.tbc : mk;
         cx<float> h[6], u[6], r2[3], w[6];
-        project_from<MU, -SF, float>([&](int k) {
-            const float2 v = r[k * rg.ne + lb];
-            return mkc(v.x, v.y);
-        }, h);
+        project_sm<MU, -SF>(r, rg.ne, l - stl, h);
         P::load_link(U, g.V, MU, sb, u, r2);
         su3_adj_mul(u, r2, h, coef, w);
         reconstruct_add<MU, -SF>(q, w);
@@ -114,9 +157,9 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
           float *zout_nrm, float kappa)
 {
     extern __shared__ float4 smem_raw[];
-    float2 *r = reinterpret_cast<float2 *>(smem_raw);               // [12][ne]
-    float2 *qs = r + 12 * rg.ne;                                     // [12][blockDim.x]
-    float2 *xc = qs + 12 * blockDim.x;                               // [12][ncore]
+    float4 *r = smem_raw;                                            // [6][ne]
+    float4 *qs = r + 6 * rg.ne;                                      // [6][blockDim.x]
+    float4 *xc = qs + 6 * blockDim.x;                                // [6][ncore]
     __shared__ float red[32 * 3];
 
     // block origin
@@ -167,11 +210,10 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
             // r = R v, x = 0
             cx<float> sp[12];
             P::load_spinor(vin, vin_nrm, V, site, sp);
-#pragma unroll
-            for (int k = 0; k < 12; ++k) r[k * rg.ne + l] = make_float2(sp[k].re, sp[k].im);
+            sm_store(r, rg.ne, l, sp);
             if (in_core)
 #pragma unroll
-                for (int k = 0; k < 12; ++k) xc[k * rg.ncore + ci] = make_float2(0.f, 0.f);
+                for (int j = 0; j < 6; ++j) xc[j * rg.ncore + ci] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     __syncthreads();
@@ -185,33 +227,33 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
         for (int j = 0; j < kRasSPT; ++j) {
             const int l = threadIdx.x + j * nt;
             if (gs[j] < 0) continue;
-            if (j > 0 && gs[0] >= 0) {
-                // park the first site's q in shared memory
-#pragma unroll
-                for (int k = 0; k < 12; ++k) qs[k * nt + threadIdx.x] = make_float2(q[k].re, q[k].im);
-            }
+            if (j > 0 && gs[0] >= 0) sm_store(qs, nt, threadIdx.x, q);   // park the first site's q
             // q = A r_l - kappa (hops inside the extended block)
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 cx<float> rl[6];
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const float2 v = r[(6 * b + k) * rg.ne + l];
-                    rl[k] = mkc(v.x, v.y);
-                }
+                sm_load_block(r, rg.ne, l, b, rl);
                 float cl[36];
                 P::load_clover(C, V, gs[j], b, cl);
                 clover_block_mul(cl, rl, q + 6 * b);
             }
-            ras_hops<P, 0, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q);
-            ras_hops<P, 1, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q);
-            ras_hops<P, 2, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q);
-            ras_hops<P, 3, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q);
+            // one direction at a time (not unrolled): bounds the registers
+            // the scheduler spends on loads in flight
+#pragma unroll 1
+            for (int mu = 0; mu < 4; ++mu) {
+                switch (mu) {
+                case 0: ras_hops<P, 0, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q); break;
+                case 1: ras_hops<P, 1, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q); break;
+                case 2: ras_hops<P, 2, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q); break;
+                default: ras_hops<P, 3, SF>(g, rg, U, r, l, gs[j], lpack[j], wbits[j], mk, q); break;
+                }
+            }
+            cx<float> rl[12];
+            sm_load(r, rg.ne, l, rl);
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
-                const float2 v = r[k * rg.ne + l];
-                acc[0] = fmaf(q[k].re, v.x, fmaf(q[k].im, v.y, acc[0]));    // Re <q, r>
-                acc[1] = fmaf(q[k].re, v.y, fmaf(-q[k].im, v.x, acc[1]));   // Im <q, r>
+                acc[0] = fmaf(q[k].re, rl[k].re, fmaf(q[k].im, rl[k].im, acc[0]));    // Re <q, r>
+                acc[1] = fmaf(q[k].re, rl[k].im, fmaf(-q[k].im, rl[k].re, acc[1]));   // Im <q, r>
                 acc[2] = fmaf(q[k].re, q[k].re, fmaf(q[k].im, q[k].im, acc[2]));
             }
         }
@@ -223,25 +265,24 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
             const int l = threadIdx.x + j * nt;
             if (gs[j] < 0) continue;
             const bool last = (j == kRasSPT - 1) || gs[kRasSPT - 1] < 0;
+            cx<float> rk[12], qk[12];
+            sm_load(r, rg.ne, l, rk);
+            if (last) {
 #pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                const float2 v = r[k * rg.ne + l];
-                const cx<float> rk = mkc(v.x, v.y);
-                cx<float> qk;
-                if (last) {
-                    qk = q[k];
-                } else {
-                    const float2 w = qs[k * nt + threadIdx.x];
-                    qk = mkc(w.x, w.y);
-                }
-                if (core[j] >= 0) {
-                    float2 *xp = xc + k * rg.ncore + core[j];
-                    const cx<float> xn = cfma(alpha, rk, mkc(xp->x, xp->y));
-                    *xp = make_float2(xn.re, xn.im);
-                }
-                const cx<float> rn = rk - alpha * qk;
-                r[k * rg.ne + l] = make_float2(rn.re, rn.im);
+                for (int k = 0; k < 12; ++k) qk[k] = q[k];
+            } else {
+                sm_load(qs, nt, threadIdx.x, qk);
             }
+            if (core[j] >= 0) {
+                cx<float> xk[12];
+                sm_load(xc, rg.ncore, core[j], xk);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) xk[k] = cfma(alpha, rk[k], xk[k]);
+                sm_store(xc, rg.ncore, core[j], xk);
+            }
+#pragma unroll
+            for (int k = 0; k < 12; ++k) rk[k] = rk[k] - alpha * qk[k];
+            sm_store(r, rg.ne, l, rk);
         }
         __syncthreads();
     }
@@ -250,13 +291,9 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
 #pragma unroll
     for (int j = 0; j < kRasSPT; ++j) {
         if (core[j] < 0) continue;
-        cx<float> s[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const float2 v = xc[k * rg.ncore + core[j]];
-            s[k] = mkc(v.x, v.y);
-        }
-        P::store_spinor(zout, zout_nrm, V, gs[j], s);
+        cx<float> sp[12];
+        sm_load(xc, rg.ncore, core[j], sp);
+        P::store_spinor(zout, zout_nrm, V, gs[j], sp);
     }
 }
 
@@ -271,7 +308,7 @@ size_t ras_smem_bytes(const wc_ras_params &p)
         ne *= (size_t)(p.block[m] + 2 * p.overlap);
         nc *= (size_t)p.block[m];
     }
-    return (ne + (size_t)ras_threads(p) + nc) * 12 * sizeof(float2);
+    return (ne + (size_t)ras_threads(p) + nc) * 6 * sizeof(float4);
 }
 
 int ras_threads(const wc_ras_params &p)

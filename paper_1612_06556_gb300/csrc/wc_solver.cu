@@ -401,16 +401,18 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
         if (st == WC_OK)
             st = check_cuda(lat, lo_init(lat, S, f4(w.r), f4(w.rhat), f4(w.p), f4(w.v), f4(w.xlo)), "lo_init");
         if (st != WC_OK) return st;
-        double rmax2 = rr_true;
-        bool breakdown = false, converged = false;
+        double rmax2 = rr_true, rr_refresh = rr_true;
+        bool breakdown = false, converged = false, diverged = false;
         while (inf.iters < p.max_iter) {
             st = enqueue_lo_iteration(lat, S, p, kind, w);
             if (st == WC_OK) st = read_scalars(lat, S);
             if (st != WC_OK) return st;
             ++inf.iters;
             const SolverScalars h = *S.scal_host;
-            if (h.flags & FLAG_NAN) {
-                result = set_error(lat, WC_ERR_NAN, "non-finite value in BiCGStab");
+            if ((h.flags & FLAG_NAN) || h.rr > 1e8 * rr_refresh) {
+                // the FP32 recurrence blew up: drop its pending correction and
+                // restart from the last FP64-verified iterate
+                diverged = true;
                 break;
             }
             if (h.flags & FLAG_BREAKDOWN) {
@@ -434,12 +436,21 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
                 if (st == WC_OK) st = check_cuda(lat, lo_rho(lat, S, f4(w.rhat), f4(w.r)), "lo_rho");
                 if (st != WC_OK) return st;
                 rmax2 = rr_true;
+                rr_refresh = rr_true;
             }
         }
-        if (result == WC_ERR_NAN) break;
         if (converged) {
             result = WC_OK;
             break;
+        }
+        if (diverged) {
+            st = check_cuda(lat, cudaMemsetAsync(w.xlo->data, 0, spinor_bytes(WC_F32, lat->g.V), S.stream), "memset");
+            if (st != WC_OK) return st;
+            if (restart == p.max_restarts) {
+                result = set_error(lat, WC_ERR_NAN, "FP32 recurrence diverged after all restarts");
+                break;
+            }
+            continue;   // restart from x (true residual recomputed at the top)
         }
         // fold whatever correction is pending and test the true residual
         st = enqueue_refresh(lat, S, kind, x, b, r_hp, w);

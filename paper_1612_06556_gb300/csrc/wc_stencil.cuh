@@ -18,13 +18,15 @@
 namespace wc {
 
 // Two-spinor h of (1 + S gamma_mu) psi, reading the four spin components of
-// one colour at a time through ld(k) (k = 3*spin + colour).
-template <int MU, int S, class R, class Load>
-__device__ __forceinline__ void project_from(Load ld, cx<R> h[6])
+// one colour at a time through ldc(c, u0, u1, d0, d1) (spins 0..3 of
+// colour c).
+template <int MU, int S, class R, class LoadColour>
+__device__ __forceinline__ void project_from(LoadColour ldc, cx<R> h[6])
 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const cx<R> u0 = ld(c), u1 = ld(3 + c), d0 = ld(6 + c), d1 = ld(9 + c);
+        cx<R> u0, u1, d0, d1;
+        ldc(c, u0, u1, d0, d1);
         const R s = R(S);
         if (MU == 0) {
             h[c] = u0 + s * times_i(d1);
@@ -45,7 +47,14 @@ __device__ __forceinline__ void project_from(Load ld, cx<R> h[6])
 template <int MU, int S, class R>
 __device__ __forceinline__ void project(const cx<R> p[12], cx<R> h[6])
 {
-    project_from<MU, S, R>([&](int k) { return p[k]; }, h);
+    project_from<MU, S, R>(
+        [&](int c, cx<R> &u0, cx<R> &u1, cx<R> &d0, cx<R> &d1) {
+            u0 = p[c];
+            u1 = p[3 + c];
+            d0 = p[6 + c];
+            d1 = p[9 + c];
+        },
+        h);
 }
 
 template <int MU, int S, class R>
