@@ -44,8 +44,13 @@ METRIC = "Wilson-Clover apply GFlop/s & % HBM roofline; mixed vs FP64 solve time
 # DRAM bytes per launch of the timed kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only while the kernel source is unchanged.
 NCU_TRAFFIC = {
-    "sources_sha": None,
-    "bytes_per_launch": None,
+    # dram__bytes_read.sum + dram__bytes_write.sum of one k_apply<P32, M>
+    # launch at 24^3x32 (shape #11; the persistent shape runs the same
+    # kernel body), from the capture summarised in
+    # profiles/apply_fp32_24x24x24x32.md; valid while the kernel sources hash
+    # to sources_sha
+    "sources_sha": "9dbf8568a8e5be39",
+    "bytes_per_launch": 291716096,
 }
 
 
@@ -241,6 +246,8 @@ def run_ours(args, world, rank, local):
     def max_over_ranks(x):
         return reduce_max(x, world, "cuda")
 
+    if args.apply_shape >= 0:   # pin one launch shape instead of the autotuner's pick
+        lat.apply_shape(wc.F32, 0, args.apply_shape)
     for i in range(args.warmup):
         lat.apply_M(outs[i % nring], ins[i % nring])
     with ClockSampler(local) as clocks:
@@ -298,7 +305,9 @@ def run_ours(args, world, rank, local):
                                "kappa=0.125, antiperiodic t",
                    "lattice": list(dims), "l2": "inputs 297 MB per step > 129 MB L2; 4 rotating field pairs",
                    "parallelism": f"replicas{world}",
-                   "launch_shape": {"threads": shape[0], "tile": list(shape[1]), "reg_capped": shape[2]}},
+                   "launch_shape": {"threads": shape[0], "tile": list(shape[1]), "reg_cap": shape[2] % 4,
+                                    "persistent": shape[2] // 4,
+                                    "chosen_by": "pinned" if args.apply_shape >= 0 else "autotuner"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_apply<P32, M>",
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_alg},
@@ -464,8 +473,9 @@ def force_timing(wc, args):
 
 
 def solve_comparison(wc, lat, src, args):
-    """Mixed-precision RAS-BiCGStab (FP32 and FP16 inner) vs plain FP64
-    BiCGStab, both to 1e-10 from x0 = 0, on the same GPU and lattice."""
+    """Mixed-precision RAS-BiCGStab (FP32 and FP16 inner; flexible, reliable
+    update, nested) and even-odd (Schur complement) solves vs plain FP64
+    BiCGStab, all to 1e-10 from x0 = 0, on the same GPU and lattice."""
     b = lat.field(wc.F64).load(src)
     out = {}
     for name, kw in (("mixed_ras_f32", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F32)),
@@ -474,7 +484,14 @@ def solve_comparison(wc, lat, src, args):
                                                solver=wc.SOLVER_RELIABLE, delta=0.1)),
                      ("reliable_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
                                                solver=wc.SOLVER_RELIABLE, delta=0.1)),
-                     ("fp64_plain", dict(precond=wc.PRECOND_NONE))):
+                     ("nested_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
+                                             solver=wc.SOLVER_NESTED, inner_tol=0.1, inner_iters=8)),
+                     ("fp64_plain", dict(precond=wc.PRECOND_NONE)),
+                     ("eo_fp64_plain", dict(precond=wc.PRECOND_NONE, even_odd=True)),
+                     ("eo_reliable_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE, delta=0.1,
+                                              even_odd=True)),
+                     ("eo_nested_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED, inner_tol=0.1,
+                                            inner_iters=8, even_odd=True))):
         x = lat.field(wc.F64)
         lat.solve(x, b, tol=1e-10, max_iter=20000, check=False, **kw)   # warm-up (allocations)
         x.close()
@@ -484,7 +501,7 @@ def solve_comparison(wc, lat, src, args):
                      "status": wc.STATUS.get(info.status, info.status)}
         x.close()
     out["speedup_mixed_f32_vs_fp64"] = out["fp64_plain"]["seconds"] / out["mixed_ras_f32"]["seconds"]
-    best = min((k for k, v in out.items() if isinstance(v, dict) and k != "fp64_plain"),
+    best = min((k for k, v in out.items() if isinstance(v, dict) and k != "fp64_plain" and v["status"] == "WC_OK"),
                key=lambda k: out[k]["seconds"])
     out["fastest_mixed"] = best
     out["speedup_fastest_mixed_vs_fp64"] = out["fp64_plain"]["seconds"] / out[best]["seconds"]
@@ -505,6 +522,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-force", action="store_true")
     ap.add_argument("--skip-large", action="store_true")
+    ap.add_argument("--apply-shape", type=int, default=-1,
+                    help="pin launch shape #N (0..19) of the timed FP32 apply instead of autotuning it")
     ap.add_argument("--large-solve", type=int, default=0,
                     help="also solve the 32^3x64 near-critical system (max steps)")
     args = ap.parse_args()

@@ -93,9 +93,17 @@ typedef struct {
  *   largest value since the last refresh, the correction is added to the FP64
  *   solution and the residual is recomputed as b - M x in FP64 (a "reliable
  *   update").  This trades FP64 work, slow on GB300, for FP32 work.
+ * NESTED (the paper's three levels, Sec. 2): FP64 flexible BiCGStab whose
+ *   preconditioner is an FP32 BiCGStab solve of M z = u / |u| that is itself
+ *   right-preconditioned by RAS (MR block solves), run until its residual
+ *   falls below inner_tol or for inner_iters steps.
+ * With precond NONE, FLEXIBLE is plain FP64 BiCGStab, RELIABLE is FP32
+ * BiCGStab with FP64 reliable updates and NESTED's inner FP32 BiCGStab runs
+ * without RAS.  even_odd = 1 (precond NONE) runs any of the three on the
+ * even-site Schur complement (the paper's two outer levels, Sec. 2).
  * The true residual |b - M x| / |b| reported and tested against tol is FP64
- * in both. */
-typedef enum { WC_SOLVER_FLEXIBLE = 0, WC_SOLVER_RELIABLE = 1 } wc_solver_kind;
+ * in all of them, on the full lattice. */
+typedef enum { WC_SOLVER_FLEXIBLE = 0, WC_SOLVER_RELIABLE = 1, WC_SOLVER_NESTED = 2 } wc_solver_kind;
 
 typedef struct {
     double tol;            /* stop when |b - M x| / |b| <= tol (true residual) */
@@ -104,8 +112,13 @@ typedef struct {
     wc_precond precond;    /* NONE: plain FP64 BiCGStab; RAS: mixed precision */
     wc_prec inner_prec;    /* storage of the RAS preconditioner: WC_F32 or WC_F16 */
     wc_ras_params ras;
-    wc_solver_kind solver; /* FLEXIBLE or RELIABLE (RELIABLE needs precond RAS) */
+    wc_solver_kind solver; /* FLEXIBLE, RELIABLE or NESTED */
     double delta;          /* RELIABLE refresh threshold, 0 < delta < 1 (0: 0.1) */
+    double inner_tol;      /* NESTED inner relative tolerance, 0 < inner_tol < 1 (0: 0.1) */
+    int inner_iters;       /* NESTED inner step limit, >= 0 (0: 8) */
+    int even_odd;          /* 1: solve the even-site Schur complement (see wc_apply_schur) and
+                              reconstruct the odd sites; needs even extents and precond NONE
+                              (any solver kind); 0: full lattice */
 } wc_solve_params;
 
 typedef struct {
@@ -164,17 +177,31 @@ wc_status wc_apply_Mdag(wc_lattice lat, wc_field out, wc_field in);
 /* out = H in (hopping term only, no clover, no kappa).  Same rules. */
 wc_status wc_apply_hop(wc_lattice lat, wc_field out, wc_field in);
 
+/* Even-odd preconditioned operator (the matrix the paper's CCS-QCD solver
+ * works on, Sec. 2).  With sites ordered by parity (even: x+y+z+t even),
+ * M = [[A_ee, -k H_eo], [-k H_oe, A_oo]] and its Schur complement on the
+ * even sites is  M^ = A_ee - k^2 H_eo A_oo^-1 H_oe.  out (even sites) =
+ * M^ in (even sites), or M^+ = gamma5 M^ gamma5 with dagger != 0; the odd
+ * sites of in are ignored and those of out set to zero.  A^-1 is built on
+ * the first call (blocking; WC_ERR_BREAKDOWN if a clover block is
+ * singular).  All four extents must be even (WC_ERR_ARG otherwise: a hop
+ * across the boundary of an odd extent would keep the parity).  Fields:
+ * distinct, same lattice and
+ * precision.  Blocking. */
+wc_status wc_apply_schur(wc_lattice lat, wc_field out, wc_field in, int dagger);
+
 /* Launch shape of the operator kernels.  The site-to-thread mapping
  * (lexicographic or 4-D tiles), CTA size and register cap of wc_apply_M /
  * wc_apply_Mdag / wc_apply_hop are chosen per lattice extent, precision and
  * kind (0 M, 1 M^+, 2 H) by timing the candidates on the first apply (that
  * first call blocks; not done while the stream is being captured, where the
  * default shape is used).  force_index >= 0 pins candidate #force_index
- * (0..15; WC_ERR_ARG if its tile does not divide the lattice or it is a
+ * (0..19; WC_ERR_ARG if its tile does not divide the lattice or it is a
  * register-capped shape with FP64); -1 only reports.  shape_out receives
- * {threads per CTA, tile x, y, z, t (all 0: lexicographic), register cap
- * (0 none, 1: 64, 2: 85 registers per thread)}, all -1 if nothing was
- * chosen yet.  The choice is shared by lattices of equal
+ * {threads per CTA, tile x, y, z, t (all 0: lexicographic), flags}, flags
+ * = register cap (0 none, 1: 64, 2: 85 registers per thread) + 4 if the
+ * launch is persistent (grid = resident CTAs, each CTA walking the site
+ * blocks); all -1 if nothing was chosen yet.  The choice is shared by lattices of equal
  * extent in the process. */
 wc_status wc_apply_shape(wc_lattice lat, wc_prec prec, int kind, int force_index, int shape_out[6]);
 
@@ -223,7 +250,8 @@ wc_status wc_solve_bicgstab(wc_lattice lat, wc_field x, wc_field b, const wc_sol
  * one CUDA graph launch (a device-side loop with one convergence mask per
  * right-hand side; right-hand sides proceed concurrently), queued on
  * internal streams; the true residual of each is then recomputed in FP64 and
- * any that misses tol is continued by the host-driven solver.  With
+ * any that misses tol is continued by the host-driven solver (FLEXIBLE and
+ * RELIABLE; NESTED and even_odd are WC_ERR_ARG here).  With
  * p->precond = WC_PRECOND_RAS and p->ras.block = {0,0,0,0} the RAS block
  * shape of each lattice is chosen by wc_ras_autotune.  Blocking; fills
  * infos[0..n-1] (seconds: wall time of the whole batch); returns the first

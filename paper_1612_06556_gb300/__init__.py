@@ -29,7 +29,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 F64, F32, F16 = 0, 1, 2
 PRECOND_NONE, PRECOND_RAS = 0, 1
-SOLVER_FLEXIBLE, SOLVER_RELIABLE = 0, 1
+SOLVER_FLEXIBLE, SOLVER_RELIABLE, SOLVER_NESTED = 0, 1, 2
 STATUS = {0: "WC_OK", 1: "WC_ERR_ARG", 2: "WC_ERR_CUDA", 3: "WC_ERR_STATE", 4: "WC_ERR_NOT_CONVERGED",
           5: "WC_ERR_BREAKDOWN", 6: "WC_ERR_NAN", 7: "WC_ERR_TIMEOUT"}
 
@@ -38,7 +38,7 @@ EXPORTED = [
     "wc_field_create", "wc_field_destroy", "wc_field_import", "wc_field_export", "wc_field_copy",
     "wc_apply_M", "wc_apply_Mdag", "wc_apply_hop", "wc_dot", "wc_norm2", "wc_axpy_norm",
     "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
-    "wc_dot_noalloc", "wc_ras_autotune", "wc_apply_shape",
+    "wc_dot_noalloc", "wc_ras_autotune", "wc_apply_shape", "wc_apply_schur",
 ]
 
 
@@ -49,7 +49,8 @@ class RasParams(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("precond", ctypes.c_int), ("inner_prec", ctypes.c_int), ("ras", RasParams),
-                ("solver", ctypes.c_int), ("delta", ctypes.c_double)]
+                ("solver", ctypes.c_int), ("delta", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("inner_iters", ctypes.c_int), ("even_odd", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -85,6 +86,7 @@ _L.wc_solve_bicgstab.argtypes = [_vp, _vp, _vp, ctypes.POINTER(SolveParams), cty
 _L.wc_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                               ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]
 _L.wc_action_force.argtypes = [_vp, _vp, _dp, _vp, ctypes.POINTER(SolveParams)]
+_L.wc_apply_schur.argtypes = [_vp, _vp, _vp, ctypes.c_int]
 _L.wc_apply_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
 _L.wc_ras_autotune.argtypes = [_vp, _vp, ctypes.POINTER(SolveParams), ctypes.POINTER(RasParams)]
 _L.wc_dot_noalloc.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
@@ -129,9 +131,11 @@ def ras_params(block=(4, 4, 4, 4), overlap=1, mr_iters=4) -> RasParams:
 
 
 def solve_params(tol=1e-10, max_iter=10000, max_restarts=5, precond=PRECOND_NONE, inner_prec=F32,
-                 block=(4, 4, 4, 4), overlap=1, mr_iters=4, solver=SOLVER_FLEXIBLE, delta=0.1) -> SolveParams:
+                 block=(4, 4, 4, 4), overlap=1, mr_iters=4, solver=SOLVER_FLEXIBLE, delta=0.1, inner_tol=0.1,
+                 inner_iters=8, even_odd=False) -> SolveParams:
     return SolveParams(float(tol), int(max_iter), int(max_restarts), int(precond), int(inner_prec),
-                       ras_params(block, overlap, mr_iters), int(solver), float(delta))
+                       ras_params(block, overlap, mr_iters), int(solver), float(delta), float(inner_tol),
+                       int(inner_iters), int(bool(even_odd)))
 
 
 class Field:
@@ -214,6 +218,11 @@ class Lattice:
 
     def apply_hop(self, out: Field, inp: Field):
         _check(_L.wc_apply_hop(self.handle, out.handle, inp.handle), self.handle)
+
+    def apply_schur(self, out: Field, inp: Field, dagger: bool = False):
+        """out (even sites) = M^ in (even sites), M^ = A_ee - k^2 H_eo A_oo^-1 H_oe;
+        odd sites of out set to zero (see wc_apply_schur)."""
+        _check(_L.wc_apply_schur(self.handle, out.handle, inp.handle, int(bool(dagger))), self.handle)
 
     def apply_shape(self, prec: int, kind: int = 0, force: int = -1):
         """(threads, tile, capped) of the operator launch for prec / kind

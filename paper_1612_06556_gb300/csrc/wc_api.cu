@@ -358,6 +358,11 @@ wc_status state_init(wc_lattice lat, SolverState &s)
 
 void state_free(SolverState &s)
 {
+    if (s.inner) {
+        state_free(*s.inner);
+        delete s.inner;
+        s.inner = nullptr;
+    }
     for (auto &w : s.work) {
         wc_field_destroy(w);
         w = nullptr;
@@ -424,9 +429,11 @@ wc_status wc_destroy_lattice(wc_lattice lat)
 {
     if (!lat) return WC_OK;
     cudaStreamSynchronize(lat->stream);
+    free_half(lat);
     state_free(lat->st);
     free_gauge(lat->gauge);
     free_clover(lat->clover);
+    free_clover(lat->cinv);
     cudaFree(lat->staging);
     delete lat;
     return WC_OK;
@@ -473,6 +480,7 @@ wc_status wc_load_gauge(wc_lattice lat, const double *data)
     if (src == lat->staging) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync(gauge)");
     lat->gauge_loaded = (st == WC_OK);
     lat->clover_loaded = false;
+    lat->cinv_loaded = false;
     return st;
 }
 
@@ -499,6 +507,7 @@ wc_status wc_load_clover(wc_lattice lat, double csw, double kappa)
     lat->csw = csw;
     lat->kappa = kappa;
     lat->clover_loaded = true;
+    lat->cinv_loaded = false;
     return WC_OK;
 }
 
@@ -621,6 +630,32 @@ static wc_status apply_common(wc_lattice lat, wc_field out, wc_field in, int kin
 }
 
 wc_status wc_apply_M(wc_lattice lat, wc_field out, wc_field in) { return apply_common(lat, out, in, 0); }
+
+wc_status wc_apply_schur(wc_lattice lat, wc_field out, wc_field in, int dagger)
+{
+    if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
+    wc_status st = check_field(lat, out, "out");
+    if (st == WC_OK) st = check_field(lat, in, "in");
+    if (st != WC_OK) return st;
+    if (out == in || out->prec != in->prec)
+        return set_error(lat, WC_ERR_ARG, "out and in must be distinct fields of one precision");
+    if (!lat->gauge_loaded || !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "gauge/clover not loaded");
+    wc_lattice h = nullptr;
+    st = half_lattice(lat, &h);
+    if (st != WC_OK) return st;
+    wc_field e = nullptr, o = nullptr, r = nullptr;
+    st = wc_field_create(h, in->prec, &e);
+    if (st == WC_OK) st = wc_field_create(h, in->prec, &o);
+    if (st == WC_OK) st = wc_field_create(h, in->prec, &r);
+    if (st == WC_OK) st = check_cuda(lat, launch_split(lat, in, e, o, lat->stream), "split");
+    if (st == WC_OK) st = check_cuda(lat, launch_schur(h, r, e, dagger ? 1 : 0, lat->stream), "schur");
+    if (st == WC_OK) st = check_cuda(lat, launch_merge(lat, r, nullptr, out, lat->stream), "merge");
+    if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync");
+    wc_field_destroy(e);
+    wc_field_destroy(o);
+    wc_field_destroy(r);
+    return st;
+}
 wc_status wc_apply_Mdag(wc_lattice lat, wc_field out, wc_field in) { return apply_common(lat, out, in, 1); }
 wc_status wc_apply_hop(wc_lattice lat, wc_field out, wc_field in) { return apply_common(lat, out, in, 2); }
 

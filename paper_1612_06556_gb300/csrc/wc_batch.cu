@@ -334,6 +334,9 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
     if (n < 0 || (n > 0 && (!lats || !xs || !bs || !p || !infos)))
         return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: bad arguments");
     if (n == 0) return WC_OK;
+    if (p->solver == WC_SOLVER_NESTED || p->even_odd)
+        return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: the nested solver and even-odd solves are "
+                                              "host-driven; use FLEXIBLE or RELIABLE on the full lattice");
     for (int i = 0; i < n; ++i) {
         // the RAS shape is checked after autotuning when it is left to it
         wc_solve_params q = *p;
@@ -349,7 +352,7 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
             if (xs[j] == xs[i] || xs[i] == bs[j])
                 return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: solution fields must be distinct");
     }
-    const bool reliable = p->precond == WC_PRECOND_RAS && p->solver == WC_SOLVER_RELIABLE;
+    const bool reliable = p->solver == WC_SOLVER_RELIABLE;
     auto t0 = std::chrono::steady_clock::now();
     Resources R;
     R.S.resize(n);

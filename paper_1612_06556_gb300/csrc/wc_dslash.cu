@@ -35,14 +35,14 @@ struct TileMap {
     int ntile[3];   // tiles along x, y, z
 };
 
-__device__ __forceinline__ int site_of_thread(const Geom &g, const TileMap &m, bool &valid)
+__device__ __forceinline__ int site_of_thread(const Geom &g, const TileMap &m, int blk, bool &valid)
 {
     if (m.tile[0] == 0) {
-        const int x = blockIdx.x * blockDim.x + threadIdx.x;
+        const int x = blk * blockDim.x + threadIdx.x;
         valid = x < g.V;
         return x;
     }
-    int t = threadIdx.x, b = blockIdx.x;
+    int t = threadIdx.x, b = blk;
     const int cx = (b % m.ntile[0]) * m.tile[0] + t % m.tile[0];
     t /= m.tile[0];
     b /= m.ntile[0];
@@ -66,9 +66,9 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, cons
     {
         const bool wrap = c[MU] == L - 1;
         const int xf = wrap ? x - (L - 1) * st : x + st;
-        const R coef = (MU == 3 && wrap) ? k * R(g.tbc) : k;
         cx<R> p[12], h[6], u[6], r2[3], w[6];
-        P::load_spinor(in, in_nrm, g.V, xf, p);
+        const R scale = P::load_spinor_raw(in, in_nrm, g.V, xf, p);
+        const R coef = ((MU == 3 && wrap) ? k * R(g.tbc) : k) * scale;
         project<MU, SF>(p, h);
         P::load_link(U, g.V, MU, x, u, r2);
         su3_mul(u, r2, h, coef, w);
@@ -77,9 +77,9 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, cons
     {
         const bool wrap = c[MU] == 0;
         const int xb = wrap ? x + (L - 1) * st : x - st;
-        const R coef = (MU == 3 && wrap) ? k * R(g.tbc) : k;
         cx<R> p[12], h[6], u[6], r2[3], w[6];
-        P::load_spinor(in, in_nrm, g.V, xb, p);
+        const R scale = P::load_spinor_raw(in, in_nrm, g.V, xb, p);
+        const R coef = ((MU == 3 && wrap) ? k * R(g.tbc) : k) * scale;
         project<MU, SB>(p, h);
         P::load_link(U, g.V, MU, xb, u, r2);
         su3_adj_mul(u, r2, h, coef, w);
@@ -87,16 +87,16 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, cons
     }
 }
 
-// KIND 0: out = M in, 1: out = M^+ in, 2: out = H in.  MINB: minimum
-// resident CTAs of kApplyMaxThreads threads per SM (caps registers).
-template <class P, int KIND, int MINB>
-__global__ void __launch_bounds__(kApplyMaxThreads, MINB)
-    k_apply(Geom g, TileMap tm, GaugeStore U, CloverStore C, const void *in, const float *in_nrm, void *out,
-            float *out_nrm, double kappa)
+// One site: out(x) = M in, M^+ in or H in (KIND 0, 1, 2) for the site of
+// this thread in logical block blk.
+template <class P, int KIND>
+__device__ __forceinline__ void apply_site(const Geom &g, const TileMap &tm, int blk, const GaugeStore &U,
+                                           const CloverStore &C, const void *in, const float *in_nrm, void *out,
+                                           float *out_nrm, double kappa)
 {
     using R = typename P::real;
     bool valid;
-    const int x = site_of_thread(g, tm, valid);
+    const int x = site_of_thread(g, tm, blk, valid);
     if (!valid) return;
     int c[4];
     site_coords(g, x, c);
@@ -124,19 +124,34 @@ __global__ void __launch_bounds__(kApplyMaxThreads, MINB)
     P::store_spinor(out, out_nrm, g.V, x, acc);
 }
 
+// KIND 0: out = M in, 1: out = M^+ in, 2: out = H in.  MINB: minimum
+// resident CTAs of kApplyMaxThreads threads per SM (caps registers).  The
+// grid may be smaller than the nlogical logical blocks (persistent launch:
+// each CTA walks the logical blocks with stride gridDim.x).
+template <class P, int KIND, int MINB>
+__global__ void __launch_bounds__(kApplyMaxThreads, MINB)
+    k_apply(Geom g, TileMap tm, int nlogical, GaugeStore U, CloverStore C, const void *in, const float *in_nrm,
+            void *out, float *out_nrm, double kappa)
+{
+    for (int blk = blockIdx.x; blk < nlogical; blk += gridDim.x)
+        apply_site<P, KIND>(g, tm, blk, U, C, in, in_nrm, out, out_nrm, kappa);
+}
+
 // ---- launch shapes and their autotuner ---------------------------------
 
 struct ApplyShape {
     int threads;
-    int tile[4];   // {0,0,0,0}: lexicographic
-    int capped;    // register cap: 0 none, 1: 64 per thread (4 CTAs of 256), 2: 85 (3 CTAs of 256)
+    int tile[4];     // {0,0,0,0}: lexicographic
+    int capped;      // register cap: 0 none, 1: 64 per thread (4 CTAs of 256), 2: 85 (3 CTAs of 256)
+    int persistent;  // 1: grid = resident CTAs, each walks logical blocks
 };
 
 constexpr ApplyShape kShapes[] = {
-    {128, {0, 0, 0, 0}, 0}, {128, {0, 0, 0, 0}, 1}, {256, {0, 0, 0, 0}, 0}, {256, {0, 0, 0, 0}, 1},
-    {128, {8, 4, 4, 1}, 0}, {128, {8, 4, 4, 1}, 1}, {128, {8, 4, 2, 2}, 0}, {128, {4, 4, 4, 2}, 0},
-    {256, {8, 4, 4, 2}, 0}, {256, {8, 4, 4, 2}, 1}, {256, {8, 8, 4, 1}, 0}, {128, {0, 0, 0, 0}, 2},
-    {256, {0, 0, 0, 0}, 2}, {128, {8, 4, 4, 1}, 2}, {256, {8, 4, 4, 2}, 2}, {128, {8, 4, 2, 2}, 2},
+    {128, {0, 0, 0, 0}, 0, 0}, {128, {0, 0, 0, 0}, 1, 0}, {256, {0, 0, 0, 0}, 0, 0}, {256, {0, 0, 0, 0}, 1, 0},
+    {128, {8, 4, 4, 1}, 0, 0}, {128, {8, 4, 4, 1}, 1, 0}, {128, {8, 4, 2, 2}, 0, 0}, {128, {4, 4, 4, 2}, 0, 0},
+    {256, {8, 4, 4, 2}, 0, 0}, {256, {8, 4, 4, 2}, 1, 0}, {256, {8, 8, 4, 1}, 0, 0}, {128, {0, 0, 0, 0}, 2, 0},
+    {256, {0, 0, 0, 0}, 2, 0}, {128, {8, 4, 4, 1}, 2, 0}, {256, {8, 4, 4, 2}, 2, 0}, {128, {8, 4, 2, 2}, 2, 0},
+    {128, {0, 0, 0, 0}, 2, 1}, {256, {0, 0, 0, 0}, 2, 1}, {128, {0, 0, 0, 0}, 0, 1}, {256, {0, 0, 0, 0}, 0, 1},
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
@@ -149,23 +164,43 @@ bool shape_fits(const Geom &g, const ApplyShape &s, bool fp64)
     return s.tile[0] * s.tile[1] * s.tile[2] * s.tile[3] == s.threads;
 }
 
+// Resident CTAs per SM of one kernel instantiation (cached per function).
+template <class K>
+int resident_ctas(K kernel, int threads)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
+}
+
 template <class P>
 cudaError_t launch_shape(wc_lattice lat, wc_field out, wc_field in, int kind, const ApplyShape &sh,
                          cudaStream_t stream)
 {
     const Geom &g = lat->g;
     TileMap tm{};
-    unsigned blocks;
+    int nlogical;
     if (sh.tile[0] == 0) {
-        blocks = (unsigned)((g.V + sh.threads - 1) / sh.threads);
+        nlogical = (g.V + sh.threads - 1) / sh.threads;
     } else {
         for (int m = 0; m < 4; ++m) tm.tile[m] = sh.tile[m];
         for (int m = 0; m < 3; ++m) tm.ntile[m] = g.L[m] / sh.tile[m];
-        blocks = (unsigned)(g.V / sh.threads);
+        nlogical = g.V / sh.threads;
     }
-#define WC_LAUNCH(K, MB)                                                                                   \
-    k_apply<P, K, MB><<<blocks, sh.threads, 0, stream>>>(g, tm, lat->gauge, lat->clover, in->data, in->nrm, \
-                                                         out->data, out->nrm, lat->kappa)
+#define WC_LAUNCH(K, MB)                                                                                      \
+    do {                                                                                                      \
+        auto kern = k_apply<P, K, MB>;                                                                        \
+        int grid = nlogical;                                                                                  \
+        if (sh.persistent) {                                                                                  \
+            const int cap = resident_ctas(kern, sh.threads) * sm_count();                                   \
+            grid = nlogical < cap ? nlogical : cap;                                                           \
+        }                                                                                                     \
+        kern<<<grid, sh.threads, 0, stream>>>(g, tm, nlogical, lat->gauge, lat->clover, in->data, in->nrm,    \
+                                              out->data, out->nrm, lat->kappa);                               \
+    } while (0)
     constexpr bool cap_ok = !std::is_same<P, P64>::value;
     constexpr int MB64 = cap_ok ? 4 : 1, MB85 = cap_ok ? 3 : 1;
     if (kind == 0) {
@@ -188,9 +223,10 @@ cudaError_t launch_shape(wc_lattice lat, wc_field out, wc_field in, int kind, co
 std::mutex g_shape_mutex;
 std::map<std::array<int, 6>, int> g_shape_choice;   // (L, prec, kind) -> shape index
 
-// Time every fitting shape (3 launches each after one warm-up) and keep the
-// fastest.  Needs an uncaptured stream; out is overwritten by the real
-// launch that follows.
+// Time every fitting shape (two rounds of 8 launches after one warm-up,
+// best round kept, candidates interleaved so that clock drift affects all
+// alike) and keep the fastest.  Needs an uncaptured stream; out is
+// overwritten by the real launch that follows.
 template <class P>
 int tune_shape(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t stream)
 {
@@ -200,22 +236,24 @@ int tune_shape(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t
         cudaEventDestroy(e0);
         return 0;
     }
-    int best = 0;
-    float best_ms = 1e30f;
-    for (int i = 0; i < kNumShapes; ++i) {
-        if (!shape_fits(lat->g, kShapes[i], std::is_same<P, P64>::value)) continue;
-        if (launch_shape<P>(lat, out, in, kind, kShapes[i], stream) != cudaSuccess) continue;
-        cudaEventRecord(e0, stream);
-        for (int r = 0; r < 3; ++r) launch_shape<P>(lat, out, in, kind, kShapes[i], stream);
-        cudaEventRecord(e1, stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) continue;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = i;
+    float best_ms[kNumShapes];
+    for (int i = 0; i < kNumShapes; ++i) best_ms[i] = 1e30f;
+    for (int round = 0; round < 2; ++round) {
+        for (int i = 0; i < kNumShapes; ++i) {
+            if (!shape_fits(lat->g, kShapes[i], std::is_same<P, P64>::value)) continue;
+            if (launch_shape<P>(lat, out, in, kind, kShapes[i], stream) != cudaSuccess) continue;
+            cudaEventRecord(e0, stream);
+            for (int r = 0; r < 8; ++r) launch_shape<P>(lat, out, in, kind, kShapes[i], stream);
+            cudaEventRecord(e1, stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms[i]) best_ms[i] = ms;
         }
     }
+    int best = 0;
+    for (int i = 1; i < kNumShapes; ++i)
+        if (best_ms[i] < best_ms[best]) best = i;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaGetLastError();
@@ -312,7 +350,7 @@ bool apply_shape(wc_lattice lat, wc_prec prec, int kind, int force, int out[6])
     const ApplyShape &s = kShapes[it->second];
     out[0] = s.threads;
     for (int m = 0; m < 4; ++m) out[1 + m] = s.tile[m];
-    out[5] = s.capped;
+    out[5] = s.capped + 4 * s.persistent;
     return true;
 }
 
@@ -320,6 +358,7 @@ int apply_shape_count() { return kNumShapes; }
 
 cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t stream)
 {
+    if (lat->schur_parent) return launch_schur(lat, out, in, kind == 1, stream);   // half lattice: M^
     switch (in->prec) {
     case WC_F64: return launch_apply_p<P64>(lat, out, in, kind, stream);
     case WC_F32: return launch_apply_p<P32>(lat, out, in, kind, stream);

@@ -184,6 +184,13 @@ struct P64 {
             s[k] = {v.x, v.y};
         }
     }
+    // the stored values and the factor they must be multiplied by (1 here)
+    static __device__ __forceinline__ double load_spinor_raw(const void *d, const float *n, int V, int x,
+                                                             cx<double> s[12])
+    {
+        load_spinor(d, n, V, x, s);
+        return 1.0;
+    }
     static __device__ __forceinline__ void store_spinor(void *d, float *, int V, int x,
                                                         const cx<double> s[12])
     {
@@ -234,6 +241,12 @@ struct P32 {
             s[2 * j + 1] = {v.z, v.w};
         }
     }
+    static __device__ __forceinline__ float load_spinor_raw(const void *d, const float *n, int V, int x,
+                                                            cx<float> s[12])
+    {
+        load_spinor(d, n, V, x, s);
+        return 1.f;
+    }
     static __device__ __forceinline__ void store_spinor(void *d, float *, int V, int x,
                                                         const cx<float> s[12])
     {
@@ -271,6 +284,22 @@ struct P32 {
 
 struct P16 {
     using real = float;
+    // stored (unit-scaled) values; returns the site's scale, to be folded
+    // into a later coefficient instead of multiplying all 24 components
+    static __device__ __forceinline__ float load_spinor_raw(const void *d, const float *nrm, int V, int x,
+                                                            cx<float> s[12])
+    {
+        const uint4 *p = static_cast<const uint4 *>(d);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            uint4 v = __ldg(p + (size_t)j * V + x);
+            s[4 * j] = h2c(v.x);
+            s[4 * j + 1] = h2c(v.y);
+            s[4 * j + 2] = h2c(v.z);
+            s[4 * j + 3] = h2c(v.w);
+        }
+        return __ldg(nrm + x);
+    }
     static __device__ __forceinline__ void load_spinor(const void *d, const float *nrm, int V, int x,
                                                        cx<float> s[12])
     {
@@ -385,6 +414,7 @@ struct SolverState {
     ReduceScratch red;
     wc_field_s *work[24] = {};
     cudaStream_t stream = nullptr;
+    SolverState *inner = nullptr;   // state of a nested inner solve, created on first use
 };
 
 }  // namespace wc
@@ -400,6 +430,13 @@ struct wc_lattice_s {
     wc::SolverState st;                       // scratch of single-RHS calls
     double2 *staging = nullptr;               // canonical-size device buffer
     size_t staging_bytes = 0;
+    // even-odd: A^-1 (built on first use) and the half lattice whose
+    // operator is the Schur complement M^ (V/2 sites, shares gauge/clover)
+    wc::CloverStore cinv;
+    bool cinv_loaded = false;
+    wc_lattice_s *half = nullptr;
+    wc_lattice_s *schur_parent = nullptr;     // set on a half lattice
+    wc_field_s *schur_tmp[3] = {};            // half lattice: odd-site temporaries
     std::string err;
 };
 
@@ -428,6 +465,18 @@ cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_p
                        cudaStream_t stream);
 
 bool apply_shape(wc_lattice lat, wc_prec prec, int kind, int force, int out[6]);
+
+// even-odd preconditioning (wc_evenodd.cu)
+cudaError_t launch_schur(wc_lattice half, wc_field out, wc_field in, int dagger, cudaStream_t stream);
+cudaError_t launch_eo(const wc_lattice_s *full, int parity, int mode, int dagger, const wc_field_s *hin,
+                      const wc_field_s *vin, wc_field_s *out, double beta, cudaStream_t stream);
+cudaError_t launch_split(const wc_lattice_s *full, const wc_field_s *f, wc_field_s *ev, wc_field_s *od,
+                         cudaStream_t stream);
+cudaError_t launch_merge(const wc_lattice_s *full, const wc_field_s *ev, const wc_field_s *od, wc_field_s *f,
+                         cudaStream_t stream);
+wc_status build_clover_inverse(wc_lattice lat);
+wc_status half_lattice(wc_lattice lat, wc_lattice *out);
+void free_half(wc_lattice lat);
 int apply_shape_count();
 
 // solver states

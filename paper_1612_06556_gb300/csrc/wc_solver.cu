@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include <chrono>
+#include <new>
 
 #include "wc_internal.cuh"
 #include "wc_solver_kernels.cuh"
@@ -77,9 +78,11 @@ wc_status solver_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &
     w->phat = w->p;
     w->shat = w->s;
     w->lo_in = w->lo_out = nullptr;
-    if (st == WC_OK && p.precond == WC_PRECOND_RAS) {
+    if (st == WC_OK && (p.precond == WC_PRECOND_RAS || p.solver == WC_SOLVER_NESTED)) {
         w->phat = state_work(lat, S, 6, WC_F64, &st);
         if (st == WC_OK) w->shat = state_work(lat, S, 7, WC_F64, &st);
+    }
+    if (st == WC_OK && p.precond == WC_PRECOND_RAS && p.solver != WC_SOLVER_NESTED) {
         const int lo = p.inner_prec == WC_F16 ? 22 : 10;
         if (st == WC_OK) w->lo_in = state_work(lat, S, lo, p.inner_prec, &st);
         if (st == WC_OK) w->lo_out = state_work(lat, S, lo + 1, p.inner_prec, &st);
@@ -88,9 +91,13 @@ wc_status solver_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &
 }
 
 // uhat = K^-1 u = |u| RAS(u / |u|); norm2_dev: |u|^2 on the device
+static wc_status nested_inner(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind, wc_field u,
+                              wc_field uhat, const double *norm2_dev);
+
 static wc_status apply_precond(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind,
                                const SolverVecs &w, wc_field u, wc_field uhat, const double *norm2_dev)
 {
+    if (p.solver == WC_SOLVER_NESTED) return nested_inner(lat, S, p, kind, u, uhat, norm2_dev);
     if (p.precond == WC_PRECOND_NONE) return WC_OK;   // uhat aliases u
     wc_status st = check_cuda(lat, launch_copy(lat, w.lo_in, u, 1.0, norm2_dev, 1, S.stream), "defect cast down");
     if (st == WC_OK) st = check_cuda(lat, launch_ras(lat, w.lo_out, w.lo_in, p.ras, kind, S.stream), "ras");
@@ -146,17 +153,83 @@ wc_status bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_fiel
     wc_solve_info *out = info ? info : &local;
     *out = wc_solve_info{};
     out->status = WC_ERR_CUDA;
-    const wc_status st = (p.precond == WC_PRECOND_RAS && p.solver == WC_SOLVER_RELIABLE)
+    const wc_status st = p.solver == WC_SOLVER_RELIABLE
                              ? reliable_bicgstab(lat, S, kind, x, b, p, out, iters_done, bb)
                              : bicgstab_impl(lat, S, kind, x, b, p, bb, out, iters_done);
     if (st != WC_OK && (out->status == WC_OK || out->status == WC_ERR_CUDA)) out->status = st;
     return st;
 }
 
+static wc_status eo_bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p,
+                             wc_solve_info *info);
+
 wc_status bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p, wc_solve_info *info)
 {
     lat->st.stream = lat->stream;
+    if (p.even_odd) return eo_bicgstab(lat, kind, x, b, p, info);
     return bicgstab(lat, lat->st, kind, x, b, p, info, 0, -1.0);
+}
+
+// Even-odd solve of op x = b (op = M, or M^+ for kind 1):
+//   t = A_oo^-1 b_o, b^_e = b_e + k H_eo t, solve M^ x_e = b^_e on the half
+//   lattice (tolerance scaled so that |b - M x| <= tol |b|: the full
+//   residual equals the Schur residual on the even sites and vanishes on
+//   the odd ones), x_o = A_oo^-1 (b_o + k H_oe x_e); the true FP64 residual
+//   of the full system is recomputed at the end.
+static wc_status eo_bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p,
+                             wc_solve_info *info)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    wc_solve_info local{};
+    wc_solve_info &inf = info ? *info : local;
+    inf = wc_solve_info{};
+    inf.status = WC_ERR_CUDA;
+    wc_lattice h = nullptr;
+    wc_status st = half_lattice(lat, &h);
+    if (st != WC_OK) return inf.status = st;
+    cudaStream_t s = lat->stream;
+    h->st.stream = s;
+    wc_field f[5] = {};   // be, bo, xe, xo, bh
+    for (int i = 0; i < 5 && st == WC_OK; ++i) st = wc_field_create(h, WC_F64, &f[i]);
+    wc_field be = f[0], bo = f[1], xe = f[2], xo = f[3], bh = f[4], t = h->schur_tmp[WC_F64];
+    const double k = lat->kappa;
+    if (st == WC_OK) st = check_cuda(lat, launch_split(lat, b, be, bo, s), "split");
+    if (st == WC_OK) st = check_cuda(lat, launch_split(lat, x, xe, xo, s), "split");
+    if (st == WC_OK) st = check_cuda(lat, launch_eo(lat, 1, 4, kind, nullptr, bo, t, 0.0, s), "A_oo^-1 b_o");
+    if (st == WC_OK) st = check_cuda(lat, launch_eo(lat, 0, 2, kind, t, be, bh, k, s), "b^_e");
+    double bb = 0.0, bbh = 0.0;
+    if (st == WC_OK) st = reduce_norm2(lat, b, &bb);
+    if (st == WC_OK) st = reduce_norm2(h, bh, &bbh);
+    if (st == WC_OK) {
+        wc_solve_params q = p;
+        q.even_odd = 0;
+        if (bbh > 0.0 && bb > 0.0) q.tol = p.tol * sqrt(bb / bbh);
+        const wc_status sr = bicgstab(h, h->st, kind, xe, bh, q, &inf, 0, bbh);
+        if (sr != WC_OK && sr != WC_ERR_NOT_CONVERGED && sr != WC_ERR_BREAKDOWN) st = sr;
+    }
+    const int iters = inf.iters, restarts = inf.restarts;
+    wc_status half_status = inf.status;
+    if (st == WC_OK) st = check_cuda(lat, launch_eo(lat, 1, 3, kind, xe, bo, xo, k, s), "x_o");
+    if (st == WC_OK) st = check_cuda(lat, launch_merge(lat, xe, xo, x, s), "merge");
+    // true residual of the full system in FP64
+    SolverVecs w;
+    wc_solve_params p0 = p;
+    p0.precond = WC_PRECOND_NONE;
+    p0.even_odd = 0;
+    if (st == WC_OK) st = solver_vectors(lat, lat->st, p0, &w);
+    if (st == WC_OK) st = enqueue_true_residual(lat, lat->st, kind, x, b, w);
+    if (st == WC_OK) st = read_scalars(lat, lat->st);
+    for (auto &fi : f) wc_field_destroy(fi);
+    if (st != WC_OK) return inf.status = st;
+    inf = wc_solve_info{};
+    inf.iters = iters;
+    inf.restarts = restarts;
+    inf.true_rel_resid = bb > 0.0 ? sqrt(lat->st.scal_host->rr / bb) : 0.0;
+    const bool ok = bb == 0.0 || lat->st.scal_host->rr <= p.tol * p.tol * bb;
+    inf.status = ok ? WC_OK : (half_status != WC_OK ? half_status : WC_ERR_NOT_CONVERGED);
+    if (!ok) set_error(lat, inf.status, "even-odd solve: true residual above tol");
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return inf.status;
 }
 
 static wc_status bicgstab_impl(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
@@ -265,8 +338,12 @@ wc_status lo_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &p, L
     wc_status st = WC_OK;
     wc_field *slots[9] = {&w->r, &w->rhat, &w->p, &w->v, &w->s, &w->t, &w->phat, &w->shat, &w->xlo};
     for (int i = 0; i < 9 && st == WC_OK; ++i) *slots[i] = state_work(lat, S, 12 + i, WC_F32, &st);
+    if (p.precond == WC_PRECOND_NONE) {   // no preconditioner: phat, shat are p, s
+        w->phat = w->p;
+        w->shat = w->s;
+    }
     w->lo_in = w->lo_out = nullptr;
-    if (st == WC_OK && p.inner_prec == WC_F16) {
+    if (st == WC_OK && p.precond == WC_PRECOND_RAS && p.inner_prec == WC_F16) {
         w->lo_in = state_work(lat, S, 22, WC_F16, &st);
         if (st == WC_OK) w->lo_out = state_work(lat, S, 23, WC_F16, &st);
     }
@@ -275,10 +352,12 @@ wc_status lo_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &p, L
 
 namespace {
 
-// uhat = RAS(u) for FP32 u (through FP16 storage when inner_prec is FP16)
+// uhat = RAS(u) for FP32 u (through FP16 storage when inner_prec is FP16);
+// nothing without a preconditioner (uhat aliases u)
 wc_status lo_precond(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind, const LoVecs &w,
                      wc_field u, wc_field uhat)
 {
+    if (p.precond == WC_PRECOND_NONE) return WC_OK;
     if (p.inner_prec != WC_F16) return check_cuda(lat, launch_ras(lat, uhat, u, p.ras, kind, S.stream), "ras");
     wc_status st = check_cuda(lat, launch_copy(lat, w.lo_in, u, 1.0, nullptr, 0, S.stream), "cast to FP16");
     if (st == WC_OK) st = check_cuda(lat, launch_ras(lat, w.lo_out, w.lo_in, p.ras, kind, S.stream), "ras");
@@ -340,6 +419,51 @@ wc_status enqueue_refresh_full(wc_lattice lat, SolverState &S, int kind, wc_fiel
     if (st == WC_OK) st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
     if (st == WC_OK) st = check_cuda(lat, lo_rho(lat, S, f4(w.rhat), f4(w.r)), "lo_rho");
     return st;
+}
+
+// Inner level of the nested solver: uhat = |u| z with z an approximate
+// solution of op z = u / |u| by FP32 BiCGStab (right-preconditioned by RAS
+// unless precond is NONE),
+// from z = 0, stopped at |r| <= inner_tol or after inner_iters steps.  Uses
+// its own solver state so that the outer scalars are untouched.
+static wc_status nested_inner(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind, wc_field u,
+                              wc_field uhat, const double *norm2_dev)
+{
+    wc_status st = WC_OK;
+    if (!S.inner) {
+        S.inner = new (std::nothrow) SolverState();
+        if (!S.inner) return set_error(lat, WC_ERR_ARG, "out of host memory");
+        st = state_init(lat, *S.inner);
+        if (st != WC_OK) {
+            delete S.inner;
+            S.inner = nullptr;
+            return st;
+        }
+    }
+    SolverState &I = *S.inner;
+    I.stream = S.stream;
+    LoVecs w;
+    st = lo_vectors(lat, I, p, &w);
+    if (st != WC_OK) return st;
+    const double itol = (p.inner_tol > 0.0 && p.inner_tol < 1.0) ? p.inner_tol : 0.1;
+    const int iters = p.inner_iters > 0 ? p.inner_iters : 8;
+    st = check_cuda(lat, launch_copy(lat, w.r, u, 1.0, norm2_dev, 1, I.stream), "cast to unit norm");
+    if (st == WC_OK)
+        st = check_cuda(lat, lo_init(lat, I, f4(w.r), f4(w.rhat), f4(w.p), f4(w.v), f4(w.xlo)), "lo_init");
+    if (st == WC_OK) st = read_scalars(lat, I);
+    if (st != WC_OK) return st;
+    const double rr0 = I.scal_host->rr;
+    for (int it = 0; it < iters && rr0 > 0.0; ++it) {
+        st = enqueue_lo_iteration(lat, I, p, kind, w);
+        if (st == WC_OK) st = read_scalars(lat, I);
+        if (st != WC_OK) return st;
+        const SolverScalars &h = *I.scal_host;
+        if (h.flags != 0 || !(h.rr > itol * itol * rr0)) break;
+    }
+    // a blown-up inner solve (NaN) falls back to the identity preconditioner
+    if (I.scal_host->flags & FLAG_NAN)
+        return check_cuda(lat, launch_copy(lat, uhat, u, 1.0, nullptr, 0, I.stream), "copy");
+    return check_cuda(lat, launch_copy(lat, uhat, w.xlo, 1.0, norm2_dev, 0, I.stream), "cast back");
 }
 
 wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
@@ -485,10 +609,12 @@ wc_status check_solve_args(wc_lattice lat, wc_field x, wc_field b, const wc_solv
         return set_error(lat, WC_ERR_ARG, "tol must be > 0, max_iter and max_restarts >= 0");
     if (p->precond != WC_PRECOND_NONE && p->precond != WC_PRECOND_RAS)
         return set_error(lat, WC_ERR_ARG, "unknown preconditioner");
-    if (p->solver != WC_SOLVER_FLEXIBLE && p->solver != WC_SOLVER_RELIABLE)
+    if (p->solver != WC_SOLVER_FLEXIBLE && p->solver != WC_SOLVER_RELIABLE && p->solver != WC_SOLVER_NESTED)
         return set_error(lat, WC_ERR_ARG, "unknown solver kind");
-    if (p->solver == WC_SOLVER_RELIABLE && p->precond != WC_PRECOND_RAS)
-        return set_error(lat, WC_ERR_ARG, "the reliable-update solver needs the RAS preconditioner");
+    if (p->even_odd && p->precond != WC_PRECOND_NONE)
+        return set_error(lat, WC_ERR_ARG, "even-odd solves take no RAS preconditioner (precond NONE)");
+    if (p->solver == WC_SOLVER_NESTED && (!(p->inner_tol >= 0.0 && p->inner_tol < 1.0) || p->inner_iters < 0))
+        return set_error(lat, WC_ERR_ARG, "inner_tol must be in [0, 1) and inner_iters >= 0");
     if (p->solver == WC_SOLVER_RELIABLE && !(p->delta >= 0.0 && p->delta < 1.0))
         return set_error(lat, WC_ERR_ARG, "delta must be in [0, 1)");
     if (p->precond == WC_PRECOND_RAS) {

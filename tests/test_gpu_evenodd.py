@@ -1,0 +1,135 @@
+"""GPU parity of the even-odd (Schur complement) operator and solves.
+
+M^ = A_ee - k^2 H_eo A_oo^-1 H_oe and M^+ through wc_apply_schur in FP64,
+FP32 and FP16 storage, element by element against the oracle's EvenOdd
+(itself pinned to the full operator by block elimination, the solve
+round trip and det M = det A_oo det M^).  Tolerances as for M: 1e-12, 1e-5,
+5e-3 relative.  Even-odd solves of every solver kind are checked with the
+oracle's full M.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import assert_elementwise, make_lattice, wc
+from oracle.evenodd import EvenOdd
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5, 2: 5e-3}
+CASES = [((4, 4, 4, 4), -1), ((6, 4, 8, 10), 1), ((2, 2, 2, 2), -1), ((8, 2, 4, 6), -1), ((10, 6, 2, 4), 1)]
+
+
+def _setup(dims, tbc, seed, kappa=0.13, csw=1.4):
+    U = synth.exp_links(dims, 0.5, seed)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    op = oracle.Operator(dims, U, csw, kappa, tbc)
+    return U, lat, op, EvenOdd(dims, tbc, kappa, U, op.T)
+
+
+def _gpu_schur(lat, psi, prec, dagger):
+    fi = lat.field(prec).load(psi)
+    fo = lat.field(prec)
+    lat.apply_schur(fo, fi, dagger)
+    return fo.store(np.zeros_like(psi))
+
+
+@pytest.mark.parametrize("dims,tbc", CASES)
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_schur_matches_oracle(dims, tbc, prec, dagger):
+    U, lat, op, eo = _setup(dims, tbc, 700 + sum(dims))
+    psi = synth.gaussian_source(dims, 710 + sum(dims))
+    out = _gpu_schur(lat, psi, prec, dagger)
+    assert np.abs(out[eo.odd]).max() == 0.0
+    # the odd half of the input is ignored
+    assert_elementwise(out, eo.schur(psi, dagger), TOL[prec])
+
+
+def test_schur_full_size_sampled():
+    """24^3x32 (a half lattice of 221,184 sites per parity) in FP32: every
+    odd site zero, sampled even sites against the oracle composition."""
+    dims, tbc = (24, 24, 24, 32), -1
+    U, lat, op, eo = _setup(dims, tbc, 901, kappa=0.125, csw=1.0)
+    psi = synth.z2_source(dims, 902)
+    out = _gpu_schur(lat, psi, 1, False)
+    assert np.abs(out[eo.odd]).max() == 0.0
+    # the reference on the full lattice is a few seconds of numpy; compare a
+    # sample of even sites
+    ref = eo.schur(psi)
+    rng = np.random.default_rng(903)
+    sites = rng.choice(np.flatnonzero(eo.even), 4096, replace=False)
+    assert_elementwise(out[sites], ref[sites], TOL[1])
+
+
+def test_schur_argument_errors():
+    w = wc()
+    dims = (4, 3, 4, 4)
+    lat = make_lattice(dims, synth.unit_links(dims), 1.0, 0.12, -1)
+    a, b = lat.field(0), lat.field(0)
+    with pytest.raises(w.WCError) as e:
+        lat.apply_schur(a, b)                       # odd y extent
+    assert e.value.status == 1
+    dims = (4, 4, 4, 4)
+    lat = make_lattice(dims, synth.unit_links(dims), 1.0, 0.12, -1)
+    a, c = lat.field(0), lat.field(1)
+    with pytest.raises(w.WCError):
+        lat.apply_schur(a, a)
+    with pytest.raises(w.WCError):
+        lat.apply_schur(a, c)
+
+
+def test_schur_after_reloading_clover():
+    """The clover inverse follows a new kappa / csw."""
+    dims, tbc = (4, 4, 4, 8), -1
+    U, lat, op, eo = _setup(dims, tbc, 55)
+    psi = synth.gaussian_source(dims, 56)
+    _gpu_schur(lat, psi, 0, False)
+    lat.load_clover(0.7, 0.11)
+    op2 = oracle.Operator(dims, U, 0.7, 0.11, tbc)
+    eo2 = EvenOdd(dims, tbc, 0.11, U, op2.T)
+    assert_elementwise(_gpu_schur(lat, psi, 0, False), eo2.schur(psi), TOL[0])
+
+
+@pytest.mark.parametrize("solver", [0, 1, 2])
+def test_even_odd_solve(solver):
+    """Every solver kind on M^ (FLEXIBLE: plain FP64; RELIABLE: FP32 with FP64
+    reliable updates; NESTED: FP64 outer, FP32 inner BiCGStab) reaches the
+    FP64 true residual of the full system; the solution is checked with the
+    oracle's M and the iteration count against the full-lattice solve."""
+    w = wc()
+    dims, kappa, csw, tbc = (8, 8, 8, 16), 0.125, 1.0, -1
+    U = synth.exp_links(dims, 0.3, 131)
+    src = synth.gaussian_source(dims, 132)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    x, b = lat.field(0), lat.field(0).load(src)
+    info = lat.solve(x, b, tol=1e-10, solver=solver, even_odd=True, max_iter=2000)
+    assert info.status == 0 and info.true_rel_resid <= 1e-10
+    sol = x.store(np.zeros_like(src))
+    r = src - oracle.apply_M(dims, tbc, kappa, csw, U, sol)
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+    if solver == 0:
+        full = lat.solve(lat.field(0), b, tol=1e-10, max_iter=2000)
+        assert info.iters < full.iters
+
+
+def test_even_odd_action_and_zero_source():
+    """M^+ solves through the action (even-odd vs full lattice give the same
+    S), and a zero source gives x = 0."""
+    w = wc()
+    dims, kappa, csw, tbc = (4, 4, 8, 8), 0.12, 1.2, -1
+    U = synth.exp_links(dims, 0.4, 141)
+    src = synth.gaussian_source(dims, 142)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    F1 = np.zeros((synth.volume(dims), 4, 3, 3), complex)
+    F2 = np.zeros_like(F1)
+    phi = lat.field(0).load(src)
+    S1 = lat.action_force(phi, F1, tol=1e-12, even_odd=True)
+    S2 = lat.action_force(phi, F2, tol=1e-12)
+    assert abs(S1 - S2) <= 1e-9 * S2
+    assert np.abs(F1 - F2).max() <= 1e-8 * np.abs(F2).max()
+    x, z = lat.field(0).load(src), lat.field(0)
+    info = lat.solve(x, z, tol=1e-10, even_odd=True)
+    assert info.status == 0
+    assert np.abs(x.store(np.zeros_like(src))).max() == 0.0

@@ -236,10 +236,13 @@ def test_reliable_update_argument_errors():
     lat = make_lattice(dims, synth.unit_links(dims), 1.0, 0.1, -1)
     x, b = lat.field(0), lat.field(0).load(synth.gaussian_source(dims, 1))
     with pytest.raises(w.WCError) as e:
-        lat.solve(x, b, solver=w.SOLVER_RELIABLE)                      # needs RAS
+        lat.solve(x, b, solver=7)                                      # unknown kind
     assert e.value.status == 1
     with pytest.raises(w.WCError) as e:
         lat.solve(x, b, precond=w.PRECOND_RAS, solver=w.SOLVER_RELIABLE, delta=1.5)
+    assert e.value.status == 1
+    with pytest.raises(w.WCError) as e:
+        lat.solve(x, b, precond=w.PRECOND_RAS, even_odd=True)          # even-odd takes no RAS
     assert e.value.status == 1
 
 
@@ -260,3 +263,23 @@ def test_batch_solve_reliable_update(inner):
     infos2 = w.solve_batch(lats, xs2, bs, tol=1e-12, max_iter=3, precond=w.PRECOND_RAS, inner_prec=inner,
                            block=(2, 2, 2, 2), solver=w.SOLVER_RELIABLE, check=False)
     assert all(i.status == 4 and i.iters == 3 for i in infos2)
+
+
+@pytest.mark.parametrize("inner", [1, 2])
+def test_nested_three_level_solver(inner):
+    """FP64 flexible BiCGStab -> FP32 BiCGStab + RAS -> MR blocks, on the
+    near-critical 32^3x64 parameters (kappa 0.128, csw 1.6) at 8^4; the
+    solution is checked with the oracle's M."""
+    w = wc()
+    dims, U, src, csw, kappa, tbc = synth.config_inputs(3, dims=(8, 8, 8, 8))
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    x, b = lat.field(0), lat.field(0).load(src)
+    info = lat.solve(x, b, tol=1e-10, precond=w.PRECOND_RAS, inner_prec=inner, solver=w.SOLVER_NESTED,
+                     mr_iters=16, inner_tol=0.05, inner_iters=10)
+    assert info.status == 0 and info.true_rel_resid <= 1e-10
+    sol = x.store(np.zeros_like(src))
+    r = src - oracle.apply_M(dims, tbc, kappa, csw, U, sol)
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+    with pytest.raises(w.WCError) as e:
+        w.solve_batch([lat], [lat.field(0)], [b], tol=1e-10, precond=w.PRECOND_RAS, solver=w.SOLVER_NESTED)
+    assert e.value.status == 1

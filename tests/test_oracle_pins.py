@@ -433,3 +433,89 @@ def test_generated_links_are_su3(kind):
     u = U.reshape(-1, 3, 3)
     assert np.allclose(u @ u.conj().transpose(0, 2, 1), np.eye(3), atol=1e-13)
     assert np.allclose(np.linalg.det(u), 1.0, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# even-odd Schur complement (Sec. 2: the solvers act on the even-odd
+# preconditioned matrix); pinned to the full operator, not to itself
+# --------------------------------------------------------------------------
+def _eo_setup(dims, seed, kappa=0.13, csw=1.2, tbc=-1):
+    from oracle.evenodd import EvenOdd
+    U = synth.exp_links(dims, 0.5, seed)
+    op = oracle.Operator(dims, U, csw, kappa, tbc)
+    return op, EvenOdd(dims, tbc, kappa, U, op.T)
+
+
+def test_parity_mask_and_hopping_term_flip_parity():
+    from oracle.evenodd import parity
+    dims = (4, 2, 6, 4)
+    par = parity(dims)
+    xyz = coords(dims)
+    assert np.array_equal(par, xyz.sum(axis=1) % 2)
+    assert par.sum() * 2 == synth.volume(dims)
+    op, eo = _eo_setup(dims, 31)
+    psi = synth.gaussian_source(dims, 32)
+    psi[par == 1] = 0
+    h = oracle.apply_hop(dims, -1, op.U, psi)
+    assert np.abs(h[par == 0]).max() == 0.0   # H maps even sites to odd only
+
+
+def test_schur_block_elimination_against_full_M():
+    """M (x_e + k A_oo^-1 H_oe x_e) = M^ x_e on the even sites, 0 on the odd
+    ones: the lower block row of M vanishes by construction."""
+    dims = (4, 4, 2, 6)
+    op, eo = _eo_setup(dims, 41)
+    xe = synth.gaussian_source(dims, 42)
+    xe[eo.odd] = 0
+    from oracle.evenodd import _site_solve
+    xo = _site_solve(eo.A, op.kappa * eo.hop(xe, eo.odd), eo.odd)
+    full = op.M(xe + xo)
+    sch = eo.schur(xe)
+    assert np.abs(full[eo.odd]).max() <= 1e-13 * np.abs(full).max()
+    assert np.allclose(full[eo.even], sch[eo.even], atol=1e-13)
+    assert np.abs(sch[eo.odd]).max() == 0.0
+
+
+def test_schur_solve_reconstructs_full_solution():
+    """prepare -> dense solve of M^ -> reconstruct gives M x = b."""
+    dims = (4, 2, 2, 4)
+    op, eo = _eo_setup(dims, 51)
+    b = synth.gaussian_source(dims, 52)
+    ev = np.flatnonzero(eo.even)
+    n = len(ev)
+
+    def schur_on_even(v):
+        f = np.zeros((synth.volume(dims), 4, 3), dtype=np.complex128)
+        f[ev] = v
+        return eo.schur(f)[ev]
+
+    D = dense(schur_on_even, n)
+    bh = eo.prepare(b)
+    xe = np.zeros_like(b)
+    xe[ev] = np.linalg.solve(D, bh[ev].ravel()).reshape(n, 4, 3)
+    x = eo.reconstruct(xe, b)
+    assert np.allclose(op.M(x), b, atol=1e-11)
+
+
+def test_schur_determinant_identity_and_adjoint():
+    """det M = det A_oo det M^, and M^+ is the conjugate transpose of M^."""
+    dims = (2, 2, 2, 4)
+    op, eo = _eo_setup(dims, 61, kappa=0.2)
+    V = synth.volume(dims)
+    ev = np.flatnonzero(eo.even)
+    od = np.flatnonzero(eo.odd)
+
+    def on_even(fn):
+        def f(v):
+            g = np.zeros((V, 4, 3), dtype=np.complex128)
+            g[ev] = v
+            return fn(g)[ev]
+        return f
+
+    D = dense(on_even(eo.schur), len(ev))
+    Dd = dense(on_even(lambda g: eo.schur(g, dagger=True)), len(ev))
+    assert np.allclose(Dd, D.conj().T, atol=1e-13)
+    _, ld_full = np.linalg.slogdet(dense(op.M, V))
+    _, ld_s = np.linalg.slogdet(D)
+    ld_a = sum(np.linalg.slogdet(eo.A[s])[1] for s in od)
+    assert abs(ld_full - (ld_s + ld_a)) <= 1e-9 * abs(ld_full)
