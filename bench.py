@@ -414,8 +414,8 @@ def large_lattice(wc, args):
     """The 32^3x64 workload (exp(0.25 iH) links, csw 1.6, kappa 0.128,
     Gaussian source): FP32 and FP16-storage applies with their roofline
     fractions and sampled errors against the FP64 oracle; with
-    --large-solve N also the reliable-update solve (FP16 storage, MR_64
-    blocks) to 1e-10 within N steps."""
+    --large-solve N also the reliable-update solves (FP16-storage RAS with
+    MR_64 blocks; even-odd FP32) to 1e-10 within N steps."""
     import torch
     import oracle
     import synth
@@ -451,6 +451,13 @@ def large_lattice(wc, args):
         out["solve_reliable_f16_mr64"] = {"seconds": info.seconds, "steps": info.iters,
                                           "true_rel_resid": info.true_rel_resid,
                                           "status": wc.STATUS.get(info.status, info.status)}
+        x.close()
+        x = lat.field(wc.F64)
+        info = lat.solve(x, b, tol=1e-10, max_iter=args.large_solve, precond=wc.PRECOND_NONE,
+                         solver=wc.SOLVER_RELIABLE, delta=0.1, even_odd=True, check=False)
+        out["solve_eo_reliable_f32"] = {"seconds": info.seconds, "steps": info.iters,
+                                        "true_rel_resid": info.true_rel_resid,
+                                        "status": wc.STATUS.get(info.status, info.status)}
     return out
 
 
