@@ -37,7 +37,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOPS_PER_SITE = 1320 + 504
-BYTES_PER_SITE = {"f32": 96 + 96 + 192 + 288, "f16": 52 + 52 + 96 + 144, "f64": 1344}
+# compulsory bytes per site of one M apply: in + out spinor, 4 forward links,
+# clover (FP16: per-site FP32 scale with each spinor, 18-real FP16 links;
+# FP64: 18-real links)
+BYTES_PER_SITE = {"f32": 96 + 96 + 192 + 288, "f16": 52 + 52 + 144 + 144, "f64": 192 + 192 + 576 + 576}
 CFG = 2  # the 24^3x32 FP32 workload
 METRIC = "Wilson-Clover apply GFlop/s & % HBM roofline; mixed vs FP64 solve time to 1e-10"
 
@@ -306,7 +309,7 @@ def run_ours(args, world, rank, local):
                    "lattice": list(dims), "l2": "inputs 297 MB per step > 129 MB L2; 4 rotating field pairs",
                    "parallelism": f"replicas{world}",
                    "launch_shape": {"threads": shape[0], "tile": list(shape[1]), "reg_cap": shape[2] % 4,
-                                    "persistent": shape[2] // 4,
+                                    "persistent": (shape[2] // 4) % 4, "pdl": shape[2] // 16,
                                     "chosen_by": "pinned" if args.apply_shape >= 0 else "autotuner"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_apply<P32, M>",
@@ -340,7 +343,8 @@ def batch_comparison(wc, args):
     24^3x48, 16^3x32 and 32^3x32, each lattice with its own exp(0.3 iH)
     gauge field) to 1e-10 with FP32 RAS (block shapes from the autotuner):
     one graph-launched batch (reliable-update solver; also the flexible FP64
-    outer solver) vs 36 sequential solves on the same GPU."""
+    outer solver, and the even-odd reliable-update solver without RAS) vs 36
+    sequential solves on the same GPU."""
     import synth
     cfg = synth.CONFIGS[4]
     lats, bs, srcs = [], [], []
@@ -353,7 +357,7 @@ def batch_comparison(wc, args):
                 lats.append(lat)
                 bs.append(lat.field(wc.F64).load(synth.point_source(dims, spin, colour)))
     params = wc.solve_params(tol=1e-10, max_iter=2000, precond=wc.PRECOND_RAS, inner_prec=wc.F32,
-                             block=(0, 0, 0, 0), solver=wc.SOLVER_RELIABLE, delta=0.1)
+                             block=(0, 0, 0, 0), solver=wc.SOLVER_RELIABLE, delta=0.01)
     shapes = {}
     for lat, b in zip(lats[::12], bs[::12]):
         shapes["x".join(map(str, lat.dims))] = list(lat.ras_autotune(b, params)[0])
@@ -372,17 +376,21 @@ def batch_comparison(wc, args):
     flex = wc.solve_params(tol=1e-10, max_iter=2000, precond=wc.PRECOND_RAS, inner_prec=wc.F32,
                            block=(0, 0, 0, 0), solver=wc.SOLVER_FLEXIBLE)
     infos_flex, t_flex = run_batch(flex)
+    eo = wc.solve_params(tol=1e-10, max_iter=5000, precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE,
+                         delta=0.01, even_odd=True)
+    run_batch(eo)                           # warm-up: clover inverses, half-lattice fields
+    infos_eo, t_eo = run_batch(eo)
     t0 = time.perf_counter()
     seq = []
     for lat, b in zip(lats, bs):
         x = lat.field(wc.F64)
         blk = shapes["x".join(map(str, lat.dims))]
         seq.append(lat.solve(x, b, tol=1e-10, max_iter=2000, precond=wc.PRECOND_RAS, inner_prec=wc.F32,
-                             block=blk, solver=wc.SOLVER_RELIABLE, delta=0.1, check=False))
+                             block=blk, solver=wc.SOLVER_RELIABLE, delta=0.01, check=False))
         x.close()
     t_seq = time.perf_counter() - t0
     return {"rhs": len(lats), "lattices": [list(d) for d in cfg["dims"]],
-            "solver": "reliable update (FP32 BiCGStab + FP32 RAS, FP64 refreshes, delta 0.1), tol 1e-10",
+            "solver": "reliable update (FP32 BiCGStab + FP32 RAS, FP64 refreshes, delta 0.01), tol 1e-10",
             "batch_seconds": t_batch, "sequential_seconds": t_seq, "speedup_vs_sequential": t_seq / t_batch,
             "max_true_rel_resid": max(i.true_rel_resid for i in infos),
             "all_ok": all(i.status == 0 for i in infos),
@@ -390,6 +398,9 @@ def batch_comparison(wc, args):
             "sequential_all_ok": all(i.status == 0 for i in seq),
             "flexible_batch_seconds": t_flex, "flexible_all_ok": all(i.status == 0 for i in infos_flex),
             "flexible_steps": [min(i.iters for i in infos_flex), max(i.iters for i in infos_flex)],
+            "even_odd_batch_seconds": t_eo, "even_odd_all_ok": all(i.status == 0 for i in infos_eo),
+            "even_odd_steps": [min(i.iters for i in infos_eo), max(i.iters for i in infos_eo)],
+            "even_odd_max_true_rel_resid": max(i.true_rel_resid for i in infos_eo),
             "ras_blocks_autotuned": shapes}
 
 
@@ -414,8 +425,8 @@ def large_lattice(wc, args):
     """The 32^3x64 workload (exp(0.25 iH) links, csw 1.6, kappa 0.128,
     Gaussian source): FP32 and FP16-storage applies with their roofline
     fractions and sampled errors against the FP64 oracle; with
-    --large-solve N also the reliable-update solves (FP16-storage RAS with
-    MR_64 blocks; even-odd FP32) to 1e-10 within N steps."""
+    --large-solve N also the even-odd reliable-update solve (FP32 with
+    FP64 refreshes) to 1e-10 within N steps."""
     import torch
     import oracle
     import synth
@@ -442,41 +453,41 @@ def large_lattice(wc, args):
         for f in ins + outs:
             f.close()
     if args.large_solve:
-        # near-critical (kappa 0.128, csw 1.6): needs strong block solves and
-        # many iterations; a minutes-long experiment, not part of the default run
+        # near-critical (kappa 0.128, csw 1.6): many iterations; a
+        # minutes-long experiment, not part of the default run
         b = lat.field(wc.F64).load(src)
-        x = lat.field(wc.F64)
-        info = lat.solve(x, b, tol=1e-10, max_iter=args.large_solve, precond=wc.PRECOND_RAS, inner_prec=wc.F16,
-                         solver=wc.SOLVER_RELIABLE, delta=0.1, mr_iters=64, check=False)
-        out["solve_reliable_f16_mr64"] = {"seconds": info.seconds, "steps": info.iters,
-                                          "true_rel_resid": info.true_rel_resid,
-                                          "status": wc.STATUS.get(info.status, info.status)}
-        x.close()
-        x = lat.field(wc.F64)
-        info = lat.solve(x, b, tol=1e-10, max_iter=args.large_solve, precond=wc.PRECOND_NONE,
-                         solver=wc.SOLVER_RELIABLE, delta=0.1, even_odd=True, check=False)
-        out["solve_eo_reliable_f32"] = {"seconds": info.seconds, "steps": info.iters,
-                                        "true_rel_resid": info.true_rel_resid,
-                                        "status": wc.STATUS.get(info.status, info.status)}
+        for name, kw in (("solve_eo_reliable_f32", dict(precond=wc.PRECOND_NONE, even_odd=True)),):
+            x = lat.field(wc.F64)
+            info = lat.solve(x, b, tol=1e-10, max_iter=args.large_solve, solver=wc.SOLVER_RELIABLE, delta=0.01,
+                             check=False, **kw)
+            out[name] = {"seconds": info.seconds, "steps": info.iters, "true_rel_resid": info.true_rel_resid,
+                         "status": wc.STATUS.get(info.status, info.status)}
+            x.close()
     return out
 
 
 def force_timing(wc, args):
     """S = phi^+ (M^+ M)^-1 phi and its force on 16^3x32 (kappa 0.12,
-    csw 1.0, exp(0.3 iH) links, Gaussian phi): two FP64 flexible BiCGStab
-    solves with FP32 RAS to 1e-12, then the force kernels."""
+    csw 1.0, exp(0.3 iH) links, Gaussian phi): two solves to 1e-12 (FP64
+    flexible BiCGStab + FP32 RAS, or even-odd reliable update), then the
+    force kernels."""
     import synth
     dims, U, phi, csw, kappa, tbc = synth.config_inputs(5)
     lat = wc.Lattice(dims, tbc).load_gauge(U).load_clover(csw, kappa)
     f_phi = lat.field(wc.F64).load(phi)
     F = np.zeros((int(np.prod(dims)), 4, 3, 3), dtype=np.complex128)
-    kw = dict(tol=1e-12, precond=wc.PRECOND_RAS, inner_prec=wc.F32)
-    lat.action_force(f_phi, F, **kw)
-    t0 = time.perf_counter()
-    S = lat.action_force(f_phi, F, **kw)
-    dt = time.perf_counter() - t0
-    return {"lattice": list(dims), "seconds": dt, "S": S,
-            "solves": "M^+ Y = phi then M X = Y, FP64 flexible BiCGStab + FP32 RAS, tol 1e-12"}
+    out = {"lattice": list(dims)}
+    for name, kw, what in (
+            ("flexible_ras", dict(tol=1e-12, precond=wc.PRECOND_RAS, inner_prec=wc.F32),
+             "FP64 flexible BiCGStab + FP32 RAS"),
+            ("eo_reliable", dict(tol=1e-12, precond=wc.PRECOND_NONE, even_odd=True, solver=wc.SOLVER_RELIABLE),
+             "even-odd FP32 BiCGStab with FP64 reliable updates")):
+        lat.action_force(f_phi, F, **kw)
+        t0 = time.perf_counter()
+        S = lat.action_force(f_phi, F, **kw)
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": dt, "S": S, "solves": f"M^+ Y = phi then M X = Y, {what}, tol 1e-12"}
+    return out
 
 
 def solve_comparison(wc, lat, src, args):
@@ -488,14 +499,14 @@ def solve_comparison(wc, lat, src, args):
     for name, kw in (("mixed_ras_f32", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F32)),
                      ("mixed_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16)),
                      ("reliable_ras_f32", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F32,
-                                               solver=wc.SOLVER_RELIABLE, delta=0.1)),
+                                               solver=wc.SOLVER_RELIABLE, delta=0.01)),
                      ("reliable_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
-                                               solver=wc.SOLVER_RELIABLE, delta=0.1)),
+                                               solver=wc.SOLVER_RELIABLE, delta=0.01)),
                      ("nested_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
                                              solver=wc.SOLVER_NESTED, inner_tol=0.1, inner_iters=8)),
                      ("fp64_plain", dict(precond=wc.PRECOND_NONE)),
                      ("eo_fp64_plain", dict(precond=wc.PRECOND_NONE, even_odd=True)),
-                     ("eo_reliable_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE, delta=0.1,
+                     ("eo_reliable_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE, delta=0.01,
                                               even_odd=True)),
                      ("eo_nested_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED, inner_tol=0.1,
                                             inner_iters=8, even_odd=True))):
@@ -530,7 +541,7 @@ def main():
     ap.add_argument("--skip-force", action="store_true")
     ap.add_argument("--skip-large", action="store_true")
     ap.add_argument("--apply-shape", type=int, default=-1,
-                    help="pin launch shape #N (0..19) of the timed FP32 apply instead of autotuning it")
+                    help="pin launch shape #N (0..21) of the timed FP32 apply instead of autotuning it")
     ap.add_argument("--large-solve", type=int, default=0,
                     help="also solve the 32^3x64 near-critical system (max steps)")
     args = ap.parse_args()

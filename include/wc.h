@@ -113,7 +113,7 @@ typedef struct {
     wc_prec inner_prec;    /* storage of the RAS preconditioner: WC_F32 or WC_F16 */
     wc_ras_params ras;
     wc_solver_kind solver; /* FLEXIBLE, RELIABLE or NESTED */
-    double delta;          /* RELIABLE refresh threshold, 0 < delta < 1 (0: 0.1) */
+    double delta;          /* RELIABLE refresh threshold, 0 < delta < 1 (0: 0.01) */
     double inner_tol;      /* NESTED inner relative tolerance, 0 < inner_tol < 1 (0: 0.1) */
     int inner_iters;       /* NESTED inner step limit, >= 0 (0: 8) */
     int even_odd;          /* 1: solve the even-site Schur complement (see wc_apply_schur) and
@@ -196,12 +196,15 @@ wc_status wc_apply_schur(wc_lattice lat, wc_field out, wc_field in, int dagger);
  * kind (0 M, 1 M^+, 2 H) by timing the candidates on the first apply (that
  * first call blocks; not done while the stream is being captured, where the
  * default shape is used).  force_index >= 0 pins candidate #force_index
- * (0..19; WC_ERR_ARG if its tile does not divide the lattice or it is a
+ * (0..21; WC_ERR_ARG if its tile does not divide the lattice or it is a
  * register-capped shape with FP64); -1 only reports.  shape_out receives
  * {threads per CTA, tile x, y, z, t (all 0: lexicographic), flags}, flags
  * = register cap (0 none, 1: 64, 2: 85 registers per thread) + 4 if the
  * launch is persistent (grid = resident CTAs, each CTA walking the site
- * blocks); all -1 if nothing was chosen yet.  The choice is shared by lattices of equal
+ * blocks) + 16 if it is a programmatic dependent launch (the kernel may
+ * start while the previous kernel of the stream drains, prefetches its
+ * links and clover into L2, then waits for that kernel; plain launch while
+ * the stream is being captured); all -1 if nothing was chosen yet.  The choice is shared by lattices of equal
  * extent in the process. */
 wc_status wc_apply_shape(wc_lattice lat, wc_prec prec, int kind, int force_index, int shape_out[6]);
 
@@ -251,7 +254,10 @@ wc_status wc_solve_bicgstab(wc_lattice lat, wc_field x, wc_field b, const wc_sol
  * right-hand side; right-hand sides proceed concurrently), queued on
  * internal streams; the true residual of each is then recomputed in FP64 and
  * any that misses tol is continued by the host-driven solver (FLEXIBLE and
- * RELIABLE; NESTED and even_odd are WC_ERR_ARG here).  With
+ * RELIABLE; NESTED is WC_ERR_ARG here).  With even_odd every right-hand side
+ * is first reduced to its even-site Schur system (all extents even), the
+ * Schur systems are solved in the graph, and each solution is completed on
+ * the odd sites and checked on the full system.  With
  * p->precond = WC_PRECOND_RAS and p->ras.block = {0,0,0,0} the RAS block
  * shape of each lattice is chosen by wc_ras_autotune.  Blocking; fills
  * infos[0..n-1] (seconds: wall time of the whole batch); returns the first

@@ -328,15 +328,20 @@ wc_status resolve_ras(wc_lattice lat, wc_field b, const wc_solve_params &p, wc_r
 
 using namespace wc;
 
+static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_field *bs, const wc_solve_params *p,
+                            const double *tol_scale, wc_solve_info *infos);
+static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_field *bs,
+                                const wc_solve_params *p, wc_solve_info *infos);
+
 extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs, wc_field *bs,
                                     const wc_solve_params *p, wc_solve_info *infos)
 {
     if (n < 0 || (n > 0 && (!lats || !xs || !bs || !p || !infos)))
         return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: bad arguments");
     if (n == 0) return WC_OK;
-    if (p->solver == WC_SOLVER_NESTED || p->even_odd)
-        return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: the nested solver and even-odd solves are "
-                                              "host-driven; use FLEXIBLE or RELIABLE on the full lattice");
+    if (p->solver == WC_SOLVER_NESTED)
+        return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: the nested solver is host-driven; use FLEXIBLE "
+                                              "or RELIABLE");
     for (int i = 0; i < n; ++i) {
         // the RAS shape is checked after autotuning when it is left to it
         wc_solve_params q = *p;
@@ -352,6 +357,14 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
             if (xs[j] == xs[i] || xs[i] == bs[j])
                 return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: solution fields must be distinct");
     }
+    return p->even_odd ? batch_even_odd(n, lats, xs, bs, p, infos) : batch_core(n, lats, xs, bs, p, nullptr, infos);
+}
+
+// The batched solve proper, on checked arguments.  tol_scale (may be null):
+// per-RHS factors on p->tol.
+static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_field *bs, const wc_solve_params *p,
+                            const double *tol_scale, wc_solve_info *infos)
+{
     const bool reliable = p->solver == WC_SOLVER_RELIABLE;
     auto t0 = std::chrono::steady_clock::now();
     Resources R;
@@ -360,6 +373,8 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
     R.LW.resize(n);
     R.streams.assign(n, nullptr);
     std::vector<wc_solve_params> P(n, *p);
+    if (tol_scale)
+        for (int i = 0; i < n; ++i) P[i].tol *= tol_scale[i];
     wc_status st = check_cuda(nullptr, ras_prepare(), "ras_prepare");
     for (int i = 0; i < n && st == WC_OK; ++i) {
         st = resolve_ras(lats[i], bs[i], *p, &P[i].ras);
@@ -417,7 +432,7 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
     if (any) {
         std::vector<BatchItem> items(n);
         for (int i = 0; i < n; ++i) {
-            const double dl = (P[i].delta > 0.0 && P[i].delta < 1.0) ? P[i].delta : 0.1;
+            const double dl = (P[i].delta > 0.0 && P[i].delta < 1.0) ? P[i].delta : 0.01;
             items[i] = BatchItem{R.S[i].scal, tol2[i], dl * dl, P[i].max_iter, 0};
         }
         st = check_cuda(nullptr, to_device(&R.d_items, items), "copy");
@@ -527,6 +542,79 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
         if (inf.status == WC_OK) inf.seconds = batch_seconds;
         if (inf.status != WC_OK && worst == WC_OK) worst = inf.status;
     }
+    return worst;
+}
+
+// Even-odd batch: every RHS is reduced to its Schur system on the half
+// lattice (b^_e = b_e + k H_eo A_oo^-1 b_o, tolerance scaled by |b|/|b^_e|),
+// all Schur systems are solved in one batched graph (each solve keeps its
+// odd-site intermediate in its own state), then x_o = A_oo^-1 (b_o + k H_oe
+// x_e) and the FP64 true residual of the full system are formed per RHS.
+static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_field *bs,
+                                const wc_solve_params *p, wc_solve_info *infos)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<wc_lattice> H(n, nullptr);
+    std::vector<wc_field> fe(5 * (size_t)n, nullptr);   // per RHS: b_e, b_o, x_e, x_o, b^_e
+    std::vector<double> bb(n, 0.0), scale(n, 1.0);
+    wc_status st = WC_OK;
+    auto F = [&](int i, int k) -> wc_field & { return fe[5 * (size_t)i + k]; };
+    for (int i = 0; i < n && st == WC_OK; ++i) {
+        wc_lattice lat = lats[i];
+        st = half_lattice(lat, &H[i]);
+        if (st != WC_OK) {
+            st = set_error(nullptr, st, "wc_solve_batch: RHS " + std::to_string(i) + ": " + lat->err);
+            break;
+        }
+        for (int k = 0; k < 5 && st == WC_OK; ++k) st = wc_field_create(H[i], WC_F64, &F(i, k));
+        cudaStream_t s = lat->stream;
+        wc_field t = H[i]->schur_tmp[WC_F64];
+        if (st == WC_OK) st = check_cuda(lat, launch_split(lat, bs[i], F(i, 0), F(i, 1), s), "split");
+        if (st == WC_OK) st = check_cuda(lat, launch_split(lat, xs[i], F(i, 2), F(i, 3), s), "split");
+        if (st == WC_OK) st = check_cuda(lat, launch_eo(lat, 1, 4, 0, nullptr, F(i, 1), t, 0.0, s), "A_oo^-1 b_o");
+        if (st == WC_OK) st = check_cuda(lat, launch_eo(lat, 0, 2, 0, t, F(i, 0), F(i, 4), lat->kappa, s), "b^_e");
+        double bbh = 0.0;
+        if (st == WC_OK) st = reduce_norm2(lat, bs[i], &bb[i]);
+        if (st == WC_OK) st = reduce_norm2(H[i], F(i, 4), &bbh);
+        if (st == WC_OK && bb[i] > 0.0 && bbh > 0.0) scale[i] = sqrt(bb[i] / bbh);
+    }
+    std::vector<wc_field> xe(n), bh(n);
+    for (int i = 0; i < n; ++i) {
+        xe[i] = F(i, 2);
+        bh[i] = F(i, 4);
+    }
+    wc_solve_params q = *p;
+    q.even_odd = 0;
+    if (st == WC_OK) {
+        const wc_status sc = batch_core(n, H.data(), xe.data(), bh.data(), &q, scale.data(), infos);
+        if (sc == WC_ERR_CUDA || sc == WC_ERR_ARG || sc == WC_ERR_STATE) st = sc;
+    }
+    wc_status worst = WC_OK;
+    for (int i = 0; i < n && st == WC_OK; ++i) {
+        wc_lattice lat = lats[i];
+        cudaStream_t s = lat->stream;
+        st = check_cuda(lat, launch_eo(lat, 1, 3, 0, F(i, 2), F(i, 1), F(i, 3), lat->kappa, s), "x_o");
+        if (st == WC_OK) st = check_cuda(lat, launch_merge(lat, F(i, 2), F(i, 3), xs[i], s), "merge");
+        SolverVecs w;
+        wc_solve_params p0 = *p;
+        p0.precond = WC_PRECOND_NONE;
+        p0.even_odd = 0;
+        lat->st.stream = s;
+        if (st == WC_OK) st = solver_vectors(lat, lat->st, p0, &w);
+        if (st == WC_OK) st = enqueue_true_residual(lat, lat->st, 0, xs[i], bs[i], w);
+        if (st == WC_OK) st = read_scalars(lat, lat->st);
+        if (st != WC_OK) break;
+        wc_solve_info &inf = infos[i];
+        const double rr = lat->st.scal_host->rr;
+        inf.true_rel_resid = bb[i] > 0.0 ? sqrt(rr / bb[i]) : 0.0;
+        if (!isfinite(rr)) inf.status = WC_ERR_NAN;
+        else if (bb[i] == 0.0 || rr <= p->tol * p->tol * bb[i]) inf.status = WC_OK;
+        else if (inf.status == WC_OK) inf.status = WC_ERR_NOT_CONVERGED;
+        inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (inf.status != WC_OK && worst == WC_OK) worst = inf.status;
+    }
+    for (auto &f : fe) wc_field_destroy(f);
+    if (st != WC_OK) return st;
     return worst;
 }
 

@@ -90,14 +90,11 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, cons
 // One site: out(x) = M in, M^+ in or H in (KIND 0, 1, 2) for the site of
 // this thread in logical block blk.
 template <class P, int KIND>
-__device__ __forceinline__ void apply_site(const Geom &g, const TileMap &tm, int blk, const GaugeStore &U,
-                                           const CloverStore &C, const void *in, const float *in_nrm, void *out,
-                                           float *out_nrm, double kappa)
+__device__ __forceinline__ void apply_site_at(const Geom &g, int x, const GaugeStore &U, const CloverStore &C,
+                                              const void *in, const float *in_nrm, void *out, float *out_nrm,
+                                              double kappa)
 {
     using R = typename P::real;
-    bool valid;
-    const int x = site_of_thread(g, tm, blk, valid);
-    if (!valid) return;
     int c[4];
     site_coords(g, x, c);
     cx<R> acc[12];
@@ -124,15 +121,73 @@ __device__ __forceinline__ void apply_site(const Geom &g, const TileMap &tm, int
     P::store_spinor(out, out_nrm, g.V, x, acc);
 }
 
+template <class P, int KIND>
+__device__ __forceinline__ void apply_site(const Geom &g, const TileMap &tm, int blk, const GaugeStore &U,
+                                           const CloverStore &C, const void *in, const float *in_nrm, void *out,
+                                           float *out_nrm, double kappa)
+{
+    bool valid;
+    const int x = site_of_thread(g, tm, blk, valid);
+    if (valid) apply_site_at<P, KIND>(g, x, U, C, in, in_nrm, out, out_nrm, kappa);
+}
+
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream serialization attribute may start while the previous kernel of the
+// stream drains; griddepcontrol.wait then blocks until that kernel has
+// completed and its writes are visible.  launch_dependents lets the next
+// such kernel start once every CTA of this grid is running.  Both are no-ops
+// for kernels launched without the attribute.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+// Bulk L2 prefetch of n bytes at p (both 16-byte multiples); only a cache
+// hint: L2 is the point of coherence, so data still being written by the
+// previous kernel is read correctly by the loads after griddep_wait().
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned n)
+{
+    if (n >= 16 && (reinterpret_cast<uintptr_t>(p) & 15) == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(n & ~15u) : "memory");
+}
+
+// The links and clover term of sites [x0, x0 + n) (lexicographic block),
+// one contiguous range per component plane; plane i is issued by thread i.
+template <class P>
+__device__ __forceinline__ void prefetch_block(const Geom &g, const GaugeStore &U, const CloverStore &C, int x0,
+                                               int n, int i)
+{
+    const size_t V = g.V;
+    if (std::is_same<P, P32>::value) {
+        if (i < 12) prefetch_l2(U.u32 + i * V + x0, 16u * n);                   // [4][3][V] float4
+        else if (i < 30) prefetch_l2(C.c32 + (i - 12) * V + x0, 16u * n);      // [18][V] float4
+    } else if (std::is_same<P, P16>::value) {
+        if (i < 4) prefetch_l2(U.u16a + i * V + x0, 16u * n);                   // [4][V] uint4
+        else if (i < 8) prefetch_l2(U.u16b + (i - 4) * V + x0, 16u * n);       // [4][V] uint4
+        else if (i < 12) prefetch_l2(U.u16c + (i - 8) * V + x0, 4u * n);       // [4][V] unsigned
+        else if (i < 21) prefetch_l2(C.c16 + (i - 12) * V + x0, 16u * n);      // [9][V] uint4
+    }
+}
+
 // KIND 0: out = M in, 1: out = M^+ in, 2: out = H in.  MINB: minimum
 // resident CTAs of kApplyMaxThreads threads per SM (caps registers).  The
 // grid may be smaller than the nlogical logical blocks (persistent launch:
-// each CTA walks the logical blocks with stride gridDim.x).
+// each CTA walks the logical blocks with stride gridDim.x).  kFlagPdl: the launch is a programmatic
+// dependent of the previous kernel (lexicographic site maps only): the CTA
+// warms L2 with the links and clover of its first sites, which no kernel of
+// a solve writes, before it waits for the previous kernel's output.
+constexpr int kFlagPdl = 1;
+
 template <class P, int KIND, int MINB>
 __global__ void __launch_bounds__(kApplyMaxThreads, MINB)
     k_apply(Geom g, TileMap tm, int nlogical, GaugeStore U, CloverStore C, const void *in, const float *in_nrm,
-            void *out, float *out_nrm, double kappa)
+            void *out, float *out_nrm, double kappa, int flags)
 {
+    if (flags & kFlagPdl) {
+        const int x0 = blockIdx.x * blockDim.x;
+        const int n = g.V - x0 < (int)blockDim.x ? g.V - x0 : (int)blockDim.x;
+        if (n > 0) prefetch_block<P>(g, U, C, x0, n, threadIdx.x);
+        griddep_wait();
+    }
+    griddep_launch_dependents();
     for (int blk = blockIdx.x; blk < nlogical; blk += gridDim.x)
         apply_site<P, KIND>(g, tm, blk, U, C, in, in_nrm, out, out_nrm, kappa);
 }
@@ -144,6 +199,7 @@ struct ApplyShape {
     int tile[4];     // {0,0,0,0}: lexicographic
     int capped;      // register cap: 0 none, 1: 64 per thread (4 CTAs of 256), 2: 85 (3 CTAs of 256)
     int persistent;  // 1: grid = resident CTAs, each walks logical blocks
+    int pdl;         // 1: programmatic dependent launch (lexicographic only; not inside a capture)
 };
 
 constexpr ApplyShape kShapes[] = {
@@ -152,6 +208,7 @@ constexpr ApplyShape kShapes[] = {
     {256, {8, 4, 4, 2}, 0, 0}, {256, {8, 4, 4, 2}, 1, 0}, {256, {8, 8, 4, 1}, 0, 0}, {128, {0, 0, 0, 0}, 2, 0},
     {256, {0, 0, 0, 0}, 2, 0}, {128, {8, 4, 4, 1}, 2, 0}, {256, {8, 4, 4, 2}, 2, 0}, {128, {8, 4, 2, 2}, 2, 0},
     {128, {0, 0, 0, 0}, 2, 1}, {256, {0, 0, 0, 0}, 2, 1}, {128, {0, 0, 0, 0}, 0, 1}, {256, {0, 0, 0, 0}, 0, 1},
+    {128, {0, 0, 0, 0}, 2, 1, 1}, {256, {0, 0, 0, 0}, 2, 1, 1},
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
@@ -190,6 +247,12 @@ cudaError_t launch_shape(wc_lattice lat, wc_field out, wc_field in, int kind, co
         for (int m = 0; m < 3; ++m) tm.ntile[m] = g.L[m] / sh.tile[m];
         nlogical = g.V / sh.threads;
     }
+    int pdl = 0;
+    if (sh.pdl && sh.tile[0] == 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(stream, &cs);
+        pdl = cs == cudaStreamCaptureStatusNone;
+    }
 #define WC_LAUNCH(K, MB)                                                                                      \
     do {                                                                                                      \
         auto kern = k_apply<P, K, MB>;                                                                        \
@@ -198,8 +261,21 @@ cudaError_t launch_shape(wc_lattice lat, wc_field out, wc_field in, int kind, co
             const int cap = resident_ctas(kern, sh.threads) * sm_count();                                   \
             grid = nlogical < cap ? nlogical : cap;                                                           \
         }                                                                                                     \
+        if (pdl) {                                                                                            \
+            cudaLaunchConfig_t cfg = {};                                                                      \
+            cudaLaunchAttribute attr[1];                                                                      \
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                                  \
+            attr[0].val.programmaticStreamSerializationAllowed = 1;                                           \
+            cfg.gridDim = dim3(grid);                                                                         \
+            cfg.blockDim = dim3(sh.threads);                                                                  \
+            cfg.stream = stream;                                                                              \
+            cfg.attrs = attr;                                                                                 \
+            cfg.numAttrs = 1;                                                                                 \
+            return cudaLaunchKernelEx(&cfg, kern, g, tm, nlogical, lat->gauge, lat->clover, in->data,         \
+                                      (const float *)in->nrm, out->data, out->nrm, lat->kappa, kFlagPdl);    \
+        }                                                                                                     \
         kern<<<grid, sh.threads, 0, stream>>>(g, tm, nlogical, lat->gauge, lat->clover, in->data, in->nrm,    \
-                                              out->data, out->nrm, lat->kappa);                               \
+                                              out->data, out->nrm, lat->kappa, 0);                            \
     } while (0)
     constexpr bool cap_ok = !std::is_same<P, P64>::value;
     constexpr int MB64 = cap_ok ? 4 : 1, MB85 = cap_ok ? 3 : 1;
@@ -350,7 +426,7 @@ bool apply_shape(wc_lattice lat, wc_prec prec, int kind, int force, int out[6])
     const ApplyShape &s = kShapes[it->second];
     out[0] = s.threads;
     for (int m = 0; m < 4; ++m) out[1 + m] = s.tile[m];
-    out[5] = s.capped + 4 * s.persistent;
+    out[5] = s.capped + 4 * s.persistent + 16 * s.pdl;
     return true;
 }
 

@@ -360,13 +360,19 @@ cudaError_t launch_merge(const wc_lattice_s *full, const wc_field_s *ev, const w
 
 // out = M^ in (or M^+ in) on half fields of the half lattice `half`: t = A_oo^-1 H_oe in,
 // out = A_ee in - k^2 H_eo t.  t: the half lattice's scratch of out's precision.
-cudaError_t launch_schur(wc_lattice half, wc_field out, wc_field in, int dagger, cudaStream_t stream)
+cudaError_t launch_schur(wc_lattice half, wc_field out, wc_field in, int dagger, cudaStream_t stream, wc_field tmp)
 {
     const wc_lattice_s *full = half->schur_parent;
-    wc_field_s *t = half->schur_tmp[out->prec];
+    wc_field_s *t = tmp ? tmp : half->schur_tmp[out->prec];
     cudaError_t e = launch_eo(full, 1, 0, dagger, in, nullptr, t, 0.0, stream);
     if (e == cudaSuccess) e = launch_eo(full, 0, 1, dagger, t, in, out, -full->kappa * full->kappa, stream);
     return e;
+}
+
+cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind, SolverState &S)
+{
+    if (!lat->schur_parent) return launch_apply(lat, out, in, kind, S.stream);
+    return launch_schur(lat, out, in, kind == 1, S.stream, S.work[kSchurSlot + out->prec]);
 }
 
 wc_status build_clover_inverse(wc_lattice lat)

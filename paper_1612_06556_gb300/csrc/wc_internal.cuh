@@ -115,8 +115,9 @@ __device__ __forceinline__ void site_coords(const Geom &g, int s, int c[4])
 struct GaugeStore {
     double2 *u64 = nullptr;   // [4][9][V]
     float4 *u32 = nullptr;    // [4][3][V]
-    uint4 *u16a = nullptr;    // [4][V]
-    uint2 *u16b = nullptr;    // [4][V]
+    uint4 *u16a = nullptr;    // [4][V]  row 0, row 1 entry 0
+    uint4 *u16b = nullptr;    // [4][V]  row 1 entries 1, 2, row 2 entries 0, 1
+    unsigned *u16c = nullptr; // [4][V]  row 2 entry 2
 };
 
 struct CloverStore {
@@ -336,15 +337,20 @@ struct P16 {
     static __device__ __forceinline__ void load_link(const GaugeStore &g, int V, int mu, int x,
                                                      cx<float> a[6], cx<float> c[3])
     {
+        // all three rows stored: FP16 bytes are cheap here, the
+        // reconstruction instructions are not (this kernel is issue-bound)
         uint4 v = __ldg(g.u16a + (size_t)mu * V + x);
-        uint2 w = __ldg(g.u16b + (size_t)mu * V + x);
+        uint4 w = __ldg(g.u16b + (size_t)mu * V + x);
+        unsigned z = __ldg(g.u16c + (size_t)mu * V + x);
         a[0] = h2c(v.x);
         a[1] = h2c(v.y);
         a[2] = h2c(v.z);
         a[3] = h2c(v.w);
         a[4] = h2c(w.x);
         a[5] = h2c(w.y);
-        reconstruct_row2(a, c);
+        c[0] = h2c(w.z);
+        c[1] = h2c(w.w);
+        c[2] = h2c(z);
     }
     static __device__ __forceinline__ void load_clover(const CloverStore &c, int V, int x, int b,
                                                        float r[36])
@@ -406,13 +412,16 @@ namespace wc {
 
 // Per-solve state: device scalars and their pinned host mirror, reduction
 // scratch, solver work fields (created on first use: slots 0-9 FP64, 10-21
-// FP32, 22-23 FP16) and the stream the solve is queued on.  A lattice owns
-// one for its single-RHS calls; a batched solve creates one per RHS.
+// FP32, 22-23 FP16, 24 + precision: the odd-site intermediate of the
+// even-odd operator on a half lattice) and the stream the solve is queued
+// on.  A lattice owns one for its single-RHS calls; a batched solve creates
+// one per RHS.
+constexpr int kSchurSlot = 24;
 struct SolverState {
     SolverScalars *scal = nullptr;
     SolverScalars *scal_host = nullptr;
     ReduceScratch red;
-    wc_field_s *work[24] = {};
+    wc_field_s *work[27] = {};
     cudaStream_t stream = nullptr;
     SolverState *inner = nullptr;   // state of a nested inner solve, created on first use
 };
@@ -459,6 +468,10 @@ inline size_t spinor_bytes(wc_prec p, int V)
 // launchers implemented in the .cu files (all asynchronous on `stream`)
 cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind /*0 M, 1 Mdag, 2 H*/,
                          cudaStream_t stream);
+// The operator of a solve on S.stream; on a half lattice (M^) the odd-site
+// intermediate is the state's own (slot kSchurSlot + precision, when it
+// exists), so that solves on one lattice may run concurrently.
+cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind, SolverState &S);
 cudaError_t launch_copy(wc_lattice lat, wc_field dst, wc_field src, double scale, const double *dev_scale,
                         int invert_scale, cudaStream_t stream);
 cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params &p, int dagger,
@@ -467,7 +480,10 @@ cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_p
 bool apply_shape(wc_lattice lat, wc_prec prec, int kind, int force, int out[6]);
 
 // even-odd preconditioning (wc_evenodd.cu)
-cudaError_t launch_schur(wc_lattice half, wc_field out, wc_field in, int dagger, cudaStream_t stream);
+// tmp: a half-lattice field of out's precision for the odd-site
+// intermediate (nullptr: the half lattice's own, shared by its callers)
+cudaError_t launch_schur(wc_lattice half, wc_field out, wc_field in, int dagger, cudaStream_t stream,
+                         wc_field tmp = nullptr);
 cudaError_t launch_eo(const wc_lattice_s *full, int parity, int mode, int dagger, const wc_field_s *hin,
                       const wc_field_s *vin, wc_field_s *out, double beta, cudaStream_t stream);
 cudaError_t launch_split(const wc_lattice_s *full, const wc_field_s *f, wc_field_s *ev, wc_field_s *od,

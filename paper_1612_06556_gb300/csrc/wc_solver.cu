@@ -78,6 +78,7 @@ wc_status solver_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &
     w->phat = w->p;
     w->shat = w->s;
     w->lo_in = w->lo_out = nullptr;
+    if (st == WC_OK && lat->schur_parent) state_work(lat, S, kSchurSlot + WC_F64, WC_F64, &st);
     if (st == WC_OK && (p.precond == WC_PRECOND_RAS || p.solver == WC_SOLVER_NESTED)) {
         w->phat = state_work(lat, S, 6, WC_F64, &st);
         if (st == WC_OK) w->shat = state_work(lat, S, 7, WC_F64, &st);
@@ -106,9 +107,12 @@ static wc_status apply_precond(wc_lattice lat, SolverState &S, const wc_solve_pa
     return st;
 }
 
-wc_status enqueue_init(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, const SolverVecs &w)
+wc_status enqueue_init(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, const SolverVecs &w,
+                       bool x_zero)
 {
-    wc_status st = check_cuda(lat, launch_apply(lat, w.r, x, kind, S.stream), "apply");
+    wc_status st = x_zero ? check_cuda(lat, cudaMemsetAsync(w.r->data, 0, spinor_bytes(WC_F64, lat->g.V), S.stream),
+                                       "memset")
+                          : check_cuda(lat, launch_apply(lat, w.r, x, kind, S), "apply");
     if (st == WC_OK)
         st = check_cuda(lat, bicg_init(lat, S, d2(b), d2(w.r), d2(w.rhat), d2(w.p), d2(w.v)), "bicg_init");
     return st;
@@ -119,11 +123,11 @@ wc_status enqueue_iteration(wc_lattice lat, SolverState &S, const wc_solve_param
 {
     wc_status st = check_cuda(lat, bicg_p(lat, S, d2(w.r), d2(w.v), d2(w.p)), "bicg_p");
     if (st == WC_OK) st = apply_precond(lat, S, p, kind, w, w.p, w.phat, &S.scal->pp);
-    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.v, w.phat, kind, S.stream), "apply");
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.v, w.phat, kind, S), "apply");
     if (st == WC_OK) st = check_cuda(lat, bicg_alpha(lat, S, d2(w.rhat), d2(w.v)), "bicg_alpha");
     if (st == WC_OK) st = check_cuda(lat, bicg_s(lat, S, d2(w.r), d2(w.v), d2(w.s)), "bicg_s");
     if (st == WC_OK) st = apply_precond(lat, S, p, kind, w, w.s, w.shat, &S.scal->ss);
-    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.t, w.shat, kind, S.stream), "apply");
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.t, w.shat, kind, S), "apply");
     if (st == WC_OK) st = check_cuda(lat, bicg_omega(lat, S, d2(w.t), d2(w.s)), "bicg_omega");
     if (st == WC_OK)
         st = check_cuda(lat, bicg_xr(lat, S, d2(x), d2(w.phat), d2(w.shat), d2(w.s), d2(w.t), d2(w.r), d2(w.rhat)),
@@ -134,13 +138,26 @@ wc_status enqueue_iteration(wc_lattice lat, SolverState &S, const wc_solve_param
 wc_status enqueue_true_residual(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
                                 const SolverVecs &w)
 {
-    wc_status st = check_cuda(lat, launch_apply(lat, w.r, x, kind, S.stream), "apply");
+    wc_status st = check_cuda(lat, launch_apply(lat, w.r, x, kind, S), "apply");
     if (st == WC_OK) st = check_cuda(lat, residual(lat, S, d2(b), d2(w.r)), "residual");
     return st;
 }
 
 static wc_status bicgstab_impl(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
                                const wc_solve_params &p, double bb, wc_solve_info *info, int iters_done);
+
+// x == 0 (one reduction and a synchronisation): the residual of a zero
+// start vector is b and needs no FP64 operator application
+static wc_status x_is_zero(wc_lattice lat, SolverState &S, wc_field x, bool *zero)
+{
+    wc_status st = check_cuda(lat, norm2_to_result(lat, S, static_cast<const double2 *>(x->data)), "norm2");
+    if (st == WC_OK)
+        st = check_cuda(lat, cudaMemcpyAsync(S.red.host_result, S.red.result, sizeof(double), cudaMemcpyDeviceToHost,
+                                             S.stream), "copy");
+    if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(S.stream), "sync");
+    if (st == WC_OK) *zero = S.red.host_result[0] == 0.0;
+    return st;
+}
 wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
                             const wc_solve_params &p, wc_solve_info *info, int iters_done, double bb);
 
@@ -266,10 +283,13 @@ static wc_status bicgstab_impl(wc_lattice lat, SolverState &S, int kind, wc_fiel
     }
     const double tol2 = p.tol * p.tol * bb;
     wc_status result = WC_ERR_NOT_CONVERGED;
+    bool x_zero = false;
+    if (iters_done == 0) st = x_is_zero(lat, S, x, &x_zero);
+    if (st != WC_OK) return st;
 
     for (int restart = 0; restart <= p.max_restarts; ++restart) {
         inf.restarts = restart;
-        st = enqueue_init(lat, S, kind, x, b, w);
+        st = enqueue_init(lat, S, kind, x, b, w, restart == 0 && x_zero);
         if (st == WC_OK) st = read_scalars(lat, S);
         if (st != WC_OK) return st;
         if (S.scal_host->flags & FLAG_NAN) {
@@ -343,6 +363,8 @@ wc_status lo_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &p, L
         w->shat = w->s;
     }
     w->lo_in = w->lo_out = nullptr;
+    if (st == WC_OK && lat->schur_parent) state_work(lat, S, kSchurSlot + WC_F32, WC_F32, &st);
+    if (st == WC_OK && lat->schur_parent) state_work(lat, S, kSchurSlot + WC_F64, WC_F64, &st);
     if (st == WC_OK && p.precond == WC_PRECOND_RAS && p.inner_prec == WC_F16) {
         w->lo_in = state_work(lat, S, 22, WC_F16, &st);
         if (st == WC_OK) w->lo_out = state_work(lat, S, 23, WC_F16, &st);
@@ -372,11 +394,11 @@ wc_status enqueue_lo_iteration(wc_lattice lat, SolverState &S, const wc_solve_pa
 {
     wc_status st = check_cuda(lat, lo_p(lat, S, f4(w.r), f4(w.v), f4(w.p)), "lo_p");
     if (st == WC_OK) st = lo_precond(lat, S, p, kind, w, w.p, w.phat);
-    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.v, w.phat, kind, S.stream), "apply");
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.v, w.phat, kind, S), "apply");
     if (st == WC_OK) st = check_cuda(lat, lo_alpha(lat, S, f4(w.rhat), f4(w.v)), "lo_alpha");
     if (st == WC_OK) st = check_cuda(lat, lo_s(lat, S, f4(w.r), f4(w.v), f4(w.s)), "lo_s");
     if (st == WC_OK) st = lo_precond(lat, S, p, kind, w, w.s, w.shat);
-    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.t, w.shat, kind, S.stream), "apply");
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.t, w.shat, kind, S), "apply");
     if (st == WC_OK) st = check_cuda(lat, lo_omega(lat, S, f4(w.t), f4(w.s)), "lo_omega");
     if (st == WC_OK)
         st = check_cuda(lat, lo_xr(lat, S, f4(w.xlo), f4(w.phat), f4(w.shat), f4(w.s), f4(w.t), f4(w.r), f4(w.rhat)),
@@ -390,7 +412,7 @@ wc_status enqueue_refresh_full(wc_lattice lat, SolverState &S, int kind, wc_fiel
 wc_status enqueue_lo_start(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
                            const LoVecs &w)
 {
-    wc_status st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S.stream), "apply");
+    wc_status st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S), "apply");
     if (st == WC_OK)
         st = check_cuda(lat, residual(lat, S, static_cast<const double2 *>(b->data),
                                       static_cast<double2 *>(r_hp->data)), "residual");
@@ -405,7 +427,7 @@ static wc_status enqueue_refresh(wc_lattice lat, SolverState &S, int kind, wc_fi
                                  const LoVecs &w)
 {
     wc_status st = check_cuda(lat, hp_add_lo(lat, S, static_cast<double2 *>(x->data), f4(w.xlo)), "hp_add_lo");
-    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S.stream), "apply");
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S), "apply");
     if (st == WC_OK)
         st = check_cuda(lat, residual(lat, S, static_cast<const double2 *>(b->data), static_cast<double2 *>(r_hp->data)),
                         "residual");
@@ -499,19 +521,27 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
         return st;
     }
     const double tol2 = p.tol * p.tol * bb;
-    const double delta = (p.delta > 0.0 && p.delta < 1.0) ? p.delta : 0.1;
+    const double delta = (p.delta > 0.0 && p.delta < 1.0) ? p.delta : 0.01;
     const double d2 = delta * delta;
     wc_status result = WC_ERR_NOT_CONVERGED;
+    bool x_zero = false;
+    if (iters_done == 0) st = x_is_zero(lat, S, x, &x_zero);
+    if (st != WC_OK) return st;
     for (int restart = 0; restart <= p.max_restarts; ++restart) {
         inf.restarts = restart;
         // true residual, FP32 copy, BiCGStab state reset (xlo = 0)
-        st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S.stream), "apply");
-        if (st == WC_OK)
-            st = check_cuda(lat, residual(lat, S, static_cast<const double2 *>(b->data),
-                                          static_cast<double2 *>(r_hp->data)), "residual");
-        if (st == WC_OK) st = read_scalars(lat, S);
+        double rr_true = bb;
+        if (restart == 0 && x_zero) {
+            st = check_cuda(lat, launch_copy(lat, r_hp, b, 1.0, nullptr, 0, S.stream), "copy");
+        } else {
+            st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S), "apply");
+            if (st == WC_OK)
+                st = check_cuda(lat, residual(lat, S, static_cast<const double2 *>(b->data),
+                                              static_cast<double2 *>(r_hp->data)), "residual");
+            if (st == WC_OK) st = read_scalars(lat, S);
+            if (st == WC_OK) rr_true = S.scal_host->rr;
+        }
         if (st != WC_OK) return st;
-        double rr_true = S.scal_host->rr;
         inf.true_rel_resid = sqrt(rr_true / bb);
         if (!isfinite(rr_true)) {
             result = set_error(lat, WC_ERR_NAN, "non-finite residual");

@@ -22,7 +22,8 @@ wc_status read_scalars(wc_lattice lat, SolverState &S);
 //   init: r = b - op x, rhat = r, p = v = 0, scalars reset
 //   iteration: one flexible BiCGStab step, scalars updated on the device
 //   true residual: r = b - op x, S.scal->rr = |r|^2
-wc_status enqueue_init(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, const SolverVecs &w);
+wc_status enqueue_init(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, const SolverVecs &w,
+                       bool x_zero = false);
 wc_status enqueue_iteration(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind, wc_field x,
                             const SolverVecs &w);
 wc_status enqueue_true_residual(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,

@@ -133,3 +133,35 @@ def test_even_odd_action_and_zero_source():
     info = lat.solve(x, z, tol=1e-10, even_odd=True)
     assert info.status == 0
     assert np.abs(x.store(np.zeros_like(src))).max() == 0.0
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_even_odd_batch(solver):
+    """Even-odd inside the batched graph: 2 uneven lattices x 3 point sources
+    (several Schur solves on one lattice run concurrently, each with its own
+    odd-site intermediate); every solution checked with the oracle's full M;
+    an odd extent is an argument error."""
+    w = wc()
+    lats, xs, bs, srcs, ops = [], [], [], [], []
+    for i, dims in enumerate([(6, 6, 6, 8), (8, 4, 8, 12)]):
+        U = synth.exp_links(dims, 0.3, 1300 + 10 * i)
+        lat = make_lattice(dims, U, 1.0, 0.124, -1)
+        for k in range(3):
+            src = synth.point_source(dims, spin=k, colour=k)
+            lats.append(lat)
+            xs.append(lat.field(0))
+            bs.append(lat.field(0).load(src))
+            srcs.append(src)
+            ops.append((dims, U))
+    infos = w.solve_batch(lats, xs, bs, tol=1e-10, solver=solver, even_odd=True, max_iter=2000)
+    for info, x, src, (dims, U) in zip(infos, xs, srcs, ops):
+        assert info.status == 0 and info.true_rel_resid <= 1e-10
+        sol = x.store(np.zeros_like(src))
+        r = src - oracle.apply_M(dims, -1, 0.124, 1.0, U, sol)
+        assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+    dims = (6, 5, 6, 8)
+    lat = make_lattice(dims, synth.unit_links(dims), 1.0, 0.12, -1)
+    with pytest.raises(w.WCError) as e:
+        w.solve_batch([lat], [lat.field(0)], [lat.field(0).load(synth.z2_source(dims, 3))], tol=1e-10,
+                      even_odd=True)
+    assert e.value.status == 1

@@ -143,7 +143,7 @@ def test_apply_argument_errors():
     assert e.value.status == 1
 
 
-N_SHAPES = 20
+N_SHAPES = 22
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
@@ -167,25 +167,26 @@ def test_every_launch_shape_matches_oracle(prec):
         assert_elementwise(gpu_apply(lat, psi, prec, "M"), ref, TOL[prec])
         assert_elementwise(gpu_apply(lat, psi, prec, "Mdag"), refd, TOL[prec])
         tested += 1
-    assert tested == (9 if prec == 0 else 20)   # FP64 takes no register-capped shape
+    assert tested == (9 if prec == 0 else 22)   # FP64 takes no register-capped shape
     with pytest.raises(w.WCError):
         lat.apply_shape(prec, 0, force=N_SHAPES)
 
 
-@pytest.mark.parametrize("shape", [16, 17, 18, 19])
+@pytest.mark.parametrize("shape", [16, 17, 18, 19, 20, 21])
 def test_persistent_launch_walks_all_blocks(shape):
     """Persistent shapes launch fewer CTAs than there are site blocks (16^3x32:
     1024 blocks of 128 sites, 512 of 256, against at most 152 x resident
-    CTAs); every site must still be computed."""
-    w = wc()
-    dims, kappa, csw, tbc = (16, 16, 16, 32), 0.12, 1.0, -1
-    U = synth.exp_links(dims, 0.3, 71)
-    psi = synth.gaussian_source(dims, 72)
-    lat = make_lattice(dims, U, csw, kappa, tbc)
-    lat.apply_shape(1, 0, force=shape)
-    out = gpu_apply(lat, psi, 1, "M")
-    V = synth.volume(dims)
-    sites = np.concatenate([np.arange(0, V, 97), [V - 1]])
-    ref = oracle.apply_M(dims, tbc, kappa, csw, U, psi, sites=sites)
-    assert rel_err(out[sites], ref) <= 1e-5
-    assert np.count_nonzero(np.all(out.reshape(V, -1) == 0, axis=1)) == 0
+    CTAs), also as programmatic dependent launches; every site must still be
+    computed (also with a volume that is not a multiple of the CTA size)."""
+    kappa, csw, tbc = 0.12, 1.0, -1
+    for dims in ((16, 16, 16, 32), (6, 5, 7, 9)):
+        U = synth.exp_links(dims, 0.3, 71)
+        psi = synth.gaussian_source(dims, 72)
+        lat = make_lattice(dims, U, csw, kappa, tbc)
+        lat.apply_shape(1, 0, force=shape)
+        out = gpu_apply(lat, psi, 1, "M")
+        V = synth.volume(dims)
+        sites = np.concatenate([np.arange(0, V, 97), [V - 1]])
+        ref = oracle.apply_M(dims, tbc, kappa, csw, U, psi, sites=sites)
+        assert rel_err(out[sites], ref) <= 1e-5
+        assert np.count_nonzero(np.all(out.reshape(V, -1) == 0, axis=1)) == 0
