@@ -440,6 +440,8 @@ def large_lattice(wc, args):
     sites = rng.choice(V, 2000, replace=False)
     ref = oracle.apply_M(dims, tbc, kappa, csw, U, src, sites=sites)
     for name, prec, bps in (("f32", wc.F32, BYTES_PER_SITE["f32"]), ("f16", wc.F16, BYTES_PER_SITE["f16"])):
+        if args.apply_shape >= 0:
+            lat.apply_shape(prec, 0, args.apply_shape)
         ins = [lat.field(prec).load(src) for _ in range(2)]
         outs = [lat.field(prec) for _ in range(2)]
         ms = time_applies(lat, outs, ins, "M", 200, stream)
@@ -541,7 +543,7 @@ def main():
     ap.add_argument("--skip-force", action="store_true")
     ap.add_argument("--skip-large", action="store_true")
     ap.add_argument("--apply-shape", type=int, default=-1,
-                    help="pin launch shape #N (0..21) of the timed FP32 apply instead of autotuning it")
+                    help="pin launch shape #N (0..21) of the timed applies instead of autotuning it")
     ap.add_argument("--large-solve", type=int, default=0,
                     help="also solve the 32^3x64 near-critical system (max steps)")
     args = ap.parse_args()
