@@ -38,9 +38,9 @@ sys.path.insert(0, ROOT)
 
 FLOPS_PER_SITE = 1320 + 504
 # compulsory bytes per site of one M apply: in + out spinor, 4 forward links,
-# clover (FP16: per-site FP32 scale with each spinor, 18-real FP16 links;
-# FP64: 18-real links)
-BYTES_PER_SITE = {"f32": 96 + 96 + 192 + 288, "f16": 52 + 52 + 144 + 144, "f64": 192 + 192 + 576 + 576}
+# clover (FP32 and FP16: 12-real links; FP16: per-site FP32 scale with each
+# spinor; FP64: 18-real links)
+BYTES_PER_SITE = {"f32": 96 + 96 + 192 + 288, "f16": 52 + 52 + 96 + 144, "f64": 192 + 192 + 576 + 576}
 CFG = 2  # the 24^3x32 FP32 workload
 METRIC = "Wilson-Clover apply GFlop/s & % HBM roofline; mixed vs FP64 solve time to 1e-10"
 

@@ -113,14 +113,11 @@ __global__ void k_pack_gauge(int V, const double2 *U, GaugeStore g)
     h.y = c2h((float)a[1].x, (float)a[1].y);
     h.z = c2h((float)a[2].x, (float)a[2].y);
     h.w = c2h((float)a[3].x, (float)a[3].y);
-    uint4 h2;
+    uint2 h2;
     h2.x = c2h((float)a[4].x, (float)a[4].y);
     h2.y = c2h((float)a[5].x, (float)a[5].y);
-    h2.z = c2h((float)r2[0].re, (float)r2[0].im);
-    h2.w = c2h((float)r2[1].re, (float)r2[1].im);
     g.u16a[(size_t)mu * V + x] = h;
     g.u16b[(size_t)mu * V + x] = h2;
-    g.u16c[(size_t)mu * V + x] = c2h((float)r2[2].re, (float)r2[2].im);
 }
 
 // ------------------------------------------------------------------------
@@ -306,7 +303,6 @@ void free_gauge(GaugeStore &g)
     cudaFree(g.u32);
     cudaFree(g.u16a);
     cudaFree(g.u16b);
-    cudaFree(g.u16c);
     g = GaugeStore{};
 }
 
@@ -459,8 +455,7 @@ wc_status wc_load_gauge(wc_lattice lat, const double *data)
         st = check_cuda(lat, dalloc(&g.u64, sizeof(double2) * 36 * (size_t)V), "cudaMalloc(gauge)");
         if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u32, sizeof(float4) * 12 * (size_t)V), "cudaMalloc(gauge)");
         if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u16a, sizeof(uint4) * 4 * (size_t)V), "cudaMalloc(gauge)");
-        if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u16b, sizeof(uint4) * 4 * (size_t)V), "cudaMalloc(gauge)");
-        if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u16c, sizeof(unsigned) * 4 * (size_t)V), "cudaMalloc(gauge)");
+        if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u16b, sizeof(uint2) * 4 * (size_t)V), "cudaMalloc(gauge)");
         if (st != WC_OK) {
             free_gauge(g);
             return st;

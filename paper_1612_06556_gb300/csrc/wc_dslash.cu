@@ -161,9 +161,8 @@ __device__ __forceinline__ void prefetch_block(const Geom &g, const GaugeStore &
         else if (i < 30) prefetch_l2(C.c32 + (i - 12) * V + x0, 16u * n);      // [18][V] float4
     } else if (std::is_same<P, P16>::value) {
         if (i < 4) prefetch_l2(U.u16a + i * V + x0, 16u * n);                   // [4][V] uint4
-        else if (i < 8) prefetch_l2(U.u16b + (i - 4) * V + x0, 16u * n);       // [4][V] uint4
-        else if (i < 12) prefetch_l2(U.u16c + (i - 8) * V + x0, 4u * n);       // [4][V] unsigned
-        else if (i < 21) prefetch_l2(C.c16 + (i - 12) * V + x0, 16u * n);      // [9][V] uint4
+        else if (i < 8) prefetch_l2(U.u16b + (i - 4) * V + x0, 8u * n);        // [4][V] uint2
+        else if (i < 17) prefetch_l2(C.c16 + (i - 8) * V + x0, 16u * n);       // [9][V] uint4
     }
 }
 

@@ -116,8 +116,7 @@ struct GaugeStore {
     double2 *u64 = nullptr;   // [4][9][V]
     float4 *u32 = nullptr;    // [4][3][V]
     uint4 *u16a = nullptr;    // [4][V]  row 0, row 1 entry 0
-    uint4 *u16b = nullptr;    // [4][V]  row 1 entries 1, 2, row 2 entries 0, 1
-    unsigned *u16c = nullptr; // [4][V]  row 2 entry 2
+    uint2 *u16b = nullptr;    // [4][V]  row 1 entries 1, 2
 };
 
 struct CloverStore {
@@ -337,20 +336,15 @@ struct P16 {
     static __device__ __forceinline__ void load_link(const GaugeStore &g, int V, int mu, int x,
                                                      cx<float> a[6], cx<float> c[3])
     {
-        // all three rows stored: FP16 bytes are cheap here, the
-        // reconstruction instructions are not (this kernel is issue-bound)
         uint4 v = __ldg(g.u16a + (size_t)mu * V + x);
-        uint4 w = __ldg(g.u16b + (size_t)mu * V + x);
-        unsigned z = __ldg(g.u16c + (size_t)mu * V + x);
+        uint2 w = __ldg(g.u16b + (size_t)mu * V + x);
         a[0] = h2c(v.x);
         a[1] = h2c(v.y);
         a[2] = h2c(v.z);
         a[3] = h2c(v.w);
         a[4] = h2c(w.x);
         a[5] = h2c(w.y);
-        c[0] = h2c(w.z);
-        c[1] = h2c(w.w);
-        c[2] = h2c(z);
+        reconstruct_row2(a, c);
     }
     static __device__ __forceinline__ void load_clover(const CloverStore &c, int V, int x, int b,
                                                        float r[36])
