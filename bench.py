@@ -424,11 +424,12 @@ def time_applies(lat, outs, ins, kind, steps, stream):
 def large_lattice(wc, args):
     """The 32^3x64 workload (exp(0.25 iH) links, csw 1.6, kappa 0.128,
     Gaussian source): FP32 and FP16-storage applies with their roofline
-    fractions and sampled errors against the FP64 oracle; with
-    --large-solve N also the even-odd reliable-update solve (FP32 with
-    FP64 refreshes) to 1e-10 within N steps."""
+    fractions and errors against this library's FP64 apply (the oracle
+    parity of all three precisions is the tests' job); nested solves to
+    1e-10 (FP16-storage RAS inner, and even-odd FP32 inner) with their FP64
+    true residuals; with --large-solve N also the even-odd reliable-update
+    solve within N steps (it stagnates here)."""
     import torch
-    import oracle
     import synth
     dims, U, src, csw, kappa, tbc = synth.config_inputs(3)
     V = int(np.prod(dims))
@@ -436,9 +437,11 @@ def large_lattice(wc, args):
     lat = wc.Lattice(dims, tbc, stream=stream).load_gauge(U).load_clover(csw, kappa)
     peak, _ = measured_peaks()
     out = {"lattice": list(dims)}
-    rng = np.random.default_rng(3)
-    sites = rng.choice(V, 2000, replace=False)
-    ref = oracle.apply_M(dims, tbc, kappa, csw, U, src, sites=sites)
+    f64_in, f64_out = lat.field(wc.F64).load(src), lat.field(wc.F64)
+    lat.apply_M(f64_out, f64_in)
+    ref = f64_out.store(np.zeros_like(src))
+    f64_in.close()
+    f64_out.close()
     for name, prec, bps in (("f32", wc.F32, BYTES_PER_SITE["f32"]), ("f16", wc.F16, BYTES_PER_SITE["f16"])):
         if args.apply_shape >= 0:
             lat.apply_shape(prec, 0, args.apply_shape)
@@ -446,25 +449,32 @@ def large_lattice(wc, args):
         outs = [lat.field(prec) for _ in range(2)]
         ms = time_applies(lat, outs, ins, "M", 200, stream)
         lat.apply_M(outs[0], ins[0])
-        res = outs[0].store(np.zeros_like(src))[sites]
+        res = outs[0].store(np.zeros_like(src))
         err = float(np.linalg.norm(res - ref) / np.linalg.norm(ref))
         gbs = bps * V / (ms * 1e-3) / 1e9
         out["apply_" + name] = {"ms": ms, "gflops": FLOPS_PER_SITE * V / (ms * 1e-3) / 1e9, "algorithmic_gbs": gbs,
                                 "roofline_frac": gbs / peak, "bytes_per_site": bps,
-                                "rel_err_vs_oracle_2000_sites": err}
+                                "rel_err_vs_fp64_apply": err}
         for f in ins + outs:
             f.close()
+    # near-critical (kappa 0.128, csw 1.6): plain and reliable-update
+    # BiCGStab stagnate near 1e-8 here; the paper's three-level structure
+    # (FP64 flexible outer, FP32 inner BiCGStab) converges.  FP16 storage as
+    # prescribed: inner BiCGStab + RAS with FP16 spinors, links and clover;
+    # fastest: inner BiCGStab on the even-odd operator.
+    b = lat.field(wc.F64).load(src)
+    solves = [("solve_nested_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16, max_iter=20)),
+              ("solve_eo_nested_f32", dict(precond=wc.PRECOND_NONE, even_odd=True, max_iter=60))]
     if args.large_solve:
-        # near-critical (kappa 0.128, csw 1.6): many iterations; a
-        # minutes-long experiment, not part of the default run
-        b = lat.field(wc.F64).load(src)
-        for name, kw in (("solve_eo_reliable_f32", dict(precond=wc.PRECOND_NONE, even_odd=True)),):
-            x = lat.field(wc.F64)
-            info = lat.solve(x, b, tol=1e-10, max_iter=args.large_solve, solver=wc.SOLVER_RELIABLE, delta=0.01,
-                             check=False, **kw)
-            out[name] = {"seconds": info.seconds, "steps": info.iters, "true_rel_resid": info.true_rel_resid,
-                         "status": wc.STATUS.get(info.status, info.status)}
-            x.close()
+        solves.append(("solve_eo_reliable_f32", dict(precond=wc.PRECOND_NONE, even_odd=True, max_iter=args.large_solve,
+                                                     solver=wc.SOLVER_RELIABLE, delta=0.01)))
+    for name, kw in solves:
+        kw.setdefault("solver", wc.SOLVER_NESTED)
+        x = lat.field(wc.F64)
+        info = lat.solve(x, b, tol=1e-10, inner_tol=0.01, inner_iters=100, check=False, **kw)
+        out[name] = {"seconds": info.seconds, "steps": info.iters, "true_rel_resid": info.true_rel_resid,
+                     "status": wc.STATUS.get(info.status, info.status)}
+        x.close()
     return out
 
 
@@ -505,13 +515,13 @@ def solve_comparison(wc, lat, src, args):
                      ("reliable_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
                                                solver=wc.SOLVER_RELIABLE, delta=0.01)),
                      ("nested_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
-                                             solver=wc.SOLVER_NESTED, inner_tol=0.1, inner_iters=8)),
+                                             solver=wc.SOLVER_NESTED, inner_tol=0.01, inner_iters=100)),
                      ("fp64_plain", dict(precond=wc.PRECOND_NONE)),
                      ("eo_fp64_plain", dict(precond=wc.PRECOND_NONE, even_odd=True)),
                      ("eo_reliable_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE, delta=0.01,
                                               even_odd=True)),
-                     ("eo_nested_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED, inner_tol=0.1,
-                                            inner_iters=8, even_odd=True))):
+                     ("eo_nested_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED, inner_tol=0.01,
+                                            inner_iters=100, even_odd=True))):
         x = lat.field(wc.F64)
         lat.solve(x, b, tol=1e-10, max_iter=20000, check=False, **kw)   # warm-up (allocations)
         x.close()
@@ -545,7 +555,7 @@ def main():
     ap.add_argument("--apply-shape", type=int, default=-1,
                     help="pin launch shape #N (0..21) of the timed applies instead of autotuning it")
     ap.add_argument("--large-solve", type=int, default=0,
-                    help="also solve the 32^3x64 near-critical system (max steps)")
+                    help="also run the even-odd reliable-update solve of the 32^3x64 system (max steps)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -114,8 +114,8 @@ typedef struct {
     wc_ras_params ras;
     wc_solver_kind solver; /* FLEXIBLE, RELIABLE or NESTED */
     double delta;          /* RELIABLE refresh threshold, 0 < delta < 1 (0: 0.01) */
-    double inner_tol;      /* NESTED inner relative tolerance, 0 < inner_tol < 1 (0: 0.1) */
-    int inner_iters;       /* NESTED inner step limit, >= 0 (0: 8) */
+    double inner_tol;      /* NESTED inner relative tolerance, 0 < inner_tol < 1 (0: 0.01) */
+    int inner_iters;       /* NESTED inner step limit, >= 0 (0: 100) */
     int even_odd;          /* 1: solve the even-site Schur complement (see wc_apply_schur) and
                               reconstruct the odd sites; needs even extents and precond NONE
                               (any solver kind); 0: full lattice */

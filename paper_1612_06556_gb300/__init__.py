@@ -131,8 +131,8 @@ def ras_params(block=(4, 4, 4, 4), overlap=1, mr_iters=4) -> RasParams:
 
 
 def solve_params(tol=1e-10, max_iter=10000, max_restarts=5, precond=PRECOND_NONE, inner_prec=F32,
-                 block=(4, 4, 4, 4), overlap=1, mr_iters=4, solver=SOLVER_FLEXIBLE, delta=0.01, inner_tol=0.1,
-                 inner_iters=8, even_odd=False) -> SolveParams:
+                 block=(4, 4, 4, 4), overlap=1, mr_iters=4, solver=SOLVER_FLEXIBLE, delta=0.01, inner_tol=0.01,
+                 inner_iters=100, even_odd=False) -> SolveParams:
     return SolveParams(float(tol), int(max_iter), int(max_restarts), int(precond), int(inner_prec),
                        ras_params(block, overlap, mr_iters), int(solver), float(delta), float(inner_tol),
                        int(inner_iters), int(bool(even_odd)))

@@ -467,8 +467,8 @@ static wc_status nested_inner(wc_lattice lat, SolverState &S, const wc_solve_par
     LoVecs w;
     st = lo_vectors(lat, I, p, &w);
     if (st != WC_OK) return st;
-    const double itol = (p.inner_tol > 0.0 && p.inner_tol < 1.0) ? p.inner_tol : 0.1;
-    const int iters = p.inner_iters > 0 ? p.inner_iters : 8;
+    const double itol = (p.inner_tol > 0.0 && p.inner_tol < 1.0) ? p.inner_tol : 0.01;
+    const int iters = p.inner_iters > 0 ? p.inner_iters : 100;
     st = check_cuda(lat, launch_copy(lat, w.r, u, 1.0, norm2_dev, 1, I.stream), "cast to unit norm");
     if (st == WC_OK)
         st = check_cuda(lat, lo_init(lat, I, f4(w.r), f4(w.rhat), f4(w.p), f4(w.v), f4(w.xlo)), "lo_init");
