@@ -1,7 +1,6 @@
 // Overlapped Restricted Additive Schwarz preconditioner with minimal-residual
-// block solves, one CTA per block (paper Sec. 2: the single-precision solver
-// is "further preconditioned with the even-odd site and the overlapped RAS
-// preconditioning").
+// block solves, one CTA per block (Sec. 2: the paper's single-precision
+// solver is preconditioned by even-odd site ordering and by overlapped RAS).
 //
 //   z = sum_i Rtilde_i^T MR_k(A_i, R_i^delta v)
 //
