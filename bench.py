@@ -284,6 +284,7 @@ def run_ours(args, world, rank, local):
     clk = clocks.summary()
     shape = lat.apply_shape(wc.F32, 0)
     mdag_ms = time_applies(lat, outs, ins, "Mdag", 500, stream)
+    copy_gbs = copy_rate(BYTES_PER_SITE["f32"] * V, stream)
     large = large_lattice(wc, args) if not args.skip_large else None
     batch = batch_comparison(wc, args) if not args.skip_batch else None
     force = force_timing(wc, args) if not args.skip_force else None
@@ -313,7 +314,8 @@ def run_ours(args, world, rank, local):
                                     "chosen_by": "pinned" if args.apply_shape >= 0 else "autotuner"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_apply<P32, M>",
-                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_alg},
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_alg,
+                     "same_size_copy_gbs": copy_gbs, "frac_of_same_size_copy": achieved / copy_gbs},
         "e2e": {"value": whole_job_rate(flops, world, e2e_ms) / 1e9, "unit": "GFlop/s",
                 "h2d_bytes_per_step": V * 12 * 16, "d2h_bytes_per_step": V * 12 * 16,
                 "ms_per_step": e2e_ms},
@@ -402,6 +404,27 @@ def batch_comparison(wc, args):
             "even_odd_steps": [min(i.iters for i in infos_eo), max(i.iters for i in infos_eo)],
             "even_odd_max_true_rel_resid": max(i.true_rel_resid for i in infos_eo),
             "ras_blocks_autotuned": shapes}
+
+
+def copy_rate(total_bytes, stream, reps=200):
+    """Read+write GB/s of a plain device copy (torch) that moves the same
+    bytes per launch as one apply, rotating over 4 buffer pairs: context for
+    the roofline fraction, since the measured peak comes from 4.3 GB copies
+    and a 55 us launch pays its ramp-up and drain on every call."""
+    import torch
+    n = int(total_bytes // 8)   # float32 elements per buffer (half read, half written)
+    src = [torch.ones(n, device="cuda") for _ in range(4)]
+    dst = [torch.empty(n, device="cuda") for _ in range(4)]
+    for i in range(8):
+        dst[i % 4].copy_(src[i % 4])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(reps):
+        dst[i % 4].copy_(src[i % 4])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return 8 * n / (e0.elapsed_time(e1) / reps * 1e-3) / 1e9
 
 
 def time_applies(lat, outs, ins, kind, steps, stream):
@@ -520,6 +543,8 @@ def solve_comparison(wc, lat, src, args):
                      ("eo_fp64_plain", dict(precond=wc.PRECOND_NONE, even_odd=True)),
                      ("eo_reliable_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE, delta=0.01,
                                               even_odd=True)),
+                     ("eo_reliable_f32_delta1e-4", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE,
+                                                        delta=1e-4, even_odd=True)),
                      ("eo_nested_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED, inner_tol=0.01,
                                             inner_iters=100, even_odd=True))):
         x = lat.field(wc.F64)
