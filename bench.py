@@ -285,6 +285,7 @@ def run_ours(args, world, rank, local):
     shape = lat.apply_shape(wc.F32, 0)
     mdag_ms = time_applies(lat, outs, ins, "Mdag", 500, stream)
     copy_gbs = copy_rate(BYTES_PER_SITE["f32"] * V, stream)
+    multi = multi_rhs_apply(wc, lat, dims, ms / args.steps, stream)
     large = large_lattice(wc, args) if not args.skip_large else None
     batch = batch_comparison(wc, args) if not args.skip_batch else None
     force = force_timing(wc, args) if not args.skip_force else None
@@ -332,6 +333,7 @@ def run_ours(args, world, rank, local):
         line["batch"] = batch
     if force is not None:
         line["force"] = force
+    line["apply_multi"] = multi
     if world == 1 and not args.skip_cpu:
         smp = OracleSampler(dims, U, src, csw, kappa, tbc, args.ref_seconds)
         g, dt = smp.step()
@@ -404,6 +406,35 @@ def batch_comparison(wc, args):
             "even_odd_steps": [min(i.iters for i in infos_eo), max(i.iters for i in infos_eo)],
             "even_odd_max_true_rel_resid": max(i.true_rel_resid for i in infos_eo),
             "ras_blocks_autotuned": shapes}
+
+
+def multi_rhs_apply(wc, lat, dims, single_ms, stream, n=12, reps=100):
+    """The 12 spin-colour sources of a propagator through one multi-RHS
+    launch (wc_apply_multi) on the same lattice: links and clover read once
+    per site for all 12 fields, 192 + 480/12 = 232 B per site and field."""
+    import torch
+    import synth
+    V = int(np.prod(dims))
+    ins = [lat.field(wc.F32).load(synth.z2_source(dims, 3000 + r)) for r in range(n)]
+    outs = [lat.field(wc.F32) for _ in range(n)]
+    for _ in range(3):
+        lat.apply_multi(outs, ins)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        lat.apply_multi(outs, ins)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    for f in ins + outs:
+        f.close()
+    bps = 192 + 480 / n
+    peak, _ = measured_peaks()
+    gbs = bps * n * V / (ms * 1e-3) / 1e9
+    return {"rhs": n, "ms_per_launch": ms, "gflops": FLOPS_PER_SITE * V * n / (ms * 1e-3) / 1e9,
+            "bytes_per_site_per_rhs": bps, "algorithmic_gbs": gbs, "roofline_frac": gbs / peak,
+            "speedup_vs_single_applies": n * single_ms / ms}
 
 
 def copy_rate(total_bytes, stream, reps=200):

@@ -177,6 +177,16 @@ wc_status wc_apply_Mdag(wc_lattice lat, wc_field out, wc_field in);
 /* out = H in (hopping term only, no clover, no kappa).  Same rules. */
 wc_status wc_apply_hop(wc_lattice lat, wc_field out, wc_field in);
 
+/* Multi-right-hand-side operator for the sources of a propagator (Sec. 2:
+ * the solver is applied per source; the sources share U and A):
+ * outs[r] = M ins[r] (dagger = 0) or M^+ ins[r] (dagger != 0), r < n,
+ * 1 <= n <= 16, all FP32 fields of lat.  One launch reads the links and the
+ * clover term once per site for all n fields: 192 + 480/n bytes per site and
+ * field instead of 672.  Every out distinct from every other out and every
+ * in.  Asynchronous on the lattice stream; WC_ERR_ARG for other precisions
+ * or sizes, before any launch. */
+wc_status wc_apply_multi(wc_lattice lat, int n, wc_field *outs, wc_field *ins, int dagger);
+
 /* Even-odd preconditioned operator (the matrix the paper's CCS-QCD solver
  * works on, Sec. 2).  With sites ordered by parity (even: x+y+z+t even),
  * M = [[A_ee, -k H_eo], [-k H_oe, A_oo]] and its Schur complement on the

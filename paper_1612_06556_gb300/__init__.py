@@ -38,7 +38,7 @@ EXPORTED = [
     "wc_field_create", "wc_field_destroy", "wc_field_import", "wc_field_export", "wc_field_copy",
     "wc_apply_M", "wc_apply_Mdag", "wc_apply_hop", "wc_dot", "wc_norm2", "wc_axpy_norm",
     "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
-    "wc_dot_noalloc", "wc_ras_autotune", "wc_apply_shape", "wc_apply_schur",
+    "wc_dot_noalloc", "wc_ras_autotune", "wc_apply_shape", "wc_apply_schur", "wc_apply_multi",
 ]
 
 
@@ -87,6 +87,7 @@ _L.wc_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(
                               ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]
 _L.wc_action_force.argtypes = [_vp, _vp, _dp, _vp, ctypes.POINTER(SolveParams)]
 _L.wc_apply_schur.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+_L.wc_apply_multi.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]
 _L.wc_apply_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
 _L.wc_ras_autotune.argtypes = [_vp, _vp, ctypes.POINTER(SolveParams), ctypes.POINTER(RasParams)]
 _L.wc_dot_noalloc.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
@@ -218,6 +219,16 @@ class Lattice:
 
     def apply_hop(self, out: Field, inp: Field):
         _check(_L.wc_apply_hop(self.handle, out.handle, inp.handle), self.handle)
+
+    def apply_multi(self, outs, inps, dagger: bool = False):
+        """outs[r] = M inps[r] (or M^+) for up to 16 FP32 fields in one launch
+        (see wc_apply_multi)."""
+        n = len(outs)
+        if len(inps) != n:
+            raise ValueError("outs and inps must have the same length")
+        O = (_vp * n)(*[f.handle for f in outs])
+        I = (_vp * n)(*[f.handle for f in inps])
+        _check(_L.wc_apply_multi(self.handle, n, O, I, int(bool(dagger))), self.handle)
 
     def apply_schur(self, out: Field, inp: Field, dagger: bool = False):
         """out (even sites) = M^ in (even sites), M^ = A_ee - k^2 H_eo A_oo^-1 H_oe;

@@ -629,6 +629,26 @@ static wc_status apply_common(wc_lattice lat, wc_field out, wc_field in, int kin
 
 wc_status wc_apply_M(wc_lattice lat, wc_field out, wc_field in) { return apply_common(lat, out, in, 0); }
 
+wc_status wc_apply_multi(wc_lattice lat, int n, wc_field *outs, wc_field *ins, int dagger)
+{
+    if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
+    if (n < 1 || n > kMrhsMax || !outs || !ins)
+        return set_error(lat, WC_ERR_ARG, "n must be in 1.." + std::to_string(kMrhsMax) + ", outs/ins non-NULL");
+    for (int r = 0; r < n; ++r) {
+        wc_status st = check_field(lat, outs[r], "out");
+        if (st == WC_OK) st = check_field(lat, ins[r], "in");
+        if (st != WC_OK) return st;
+        if (outs[r]->prec != WC_F32 || ins[r]->prec != WC_F32)
+            return set_error(lat, WC_ERR_ARG, "the multi-RHS operator takes FP32 fields");
+        for (int q = 0; q < n; ++q)
+            if (outs[r] == ins[q] || (q < r && outs[r] == outs[q]))
+                return set_error(lat, WC_ERR_ARG, "out fields must be distinct from each other and from the inputs");
+    }
+    if (!lat->gauge_loaded || !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "gauge/clover not loaded");
+    return check_cuda(lat, launch_apply_multi(lat, n, outs, ins, dagger ? 1 : 0, nullptr, lat->stream),
+                      "apply_multi");
+}
+
 wc_status wc_apply_schur(wc_lattice lat, wc_field out, wc_field in, int dagger)
 {
     if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");

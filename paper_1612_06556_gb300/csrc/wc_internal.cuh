@@ -473,6 +473,13 @@ cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_p
 
 bool apply_shape(wc_lattice lat, wc_prec prec, int kind, int force, int out[6]);
 
+// multi-right-hand-side FP32 operator (wc_mrhs.cu): outs[r] = M ins[r]
+// (kind 0) or M^+ ins[r] (kind 1) for r < n <= kMrhsMax, links and clover
+// read once per site; active (nullable, device): 0 skips right-hand side r
+constexpr int kMrhsMax = 16;
+cudaError_t launch_apply_multi(wc_lattice lat, int n, const wc_field *outs, const wc_field *ins, int kind,
+                               const int *active, cudaStream_t stream);
+
 // even-odd preconditioning (wc_evenodd.cu)
 // tmp: a half-lattice field of out's precision for the odd-site
 // intermediate (nullptr: the half lattice's own, shared by its callers)
