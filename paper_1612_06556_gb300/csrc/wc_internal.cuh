@@ -407,15 +407,17 @@ namespace wc {
 // Per-solve state: device scalars and their pinned host mirror, reduction
 // scratch, solver work fields (created on first use: slots 0-9 FP64, 10-21
 // FP32, 22-23 FP16, 24 + precision: the odd-site intermediate of the
-// even-odd operator on a half lattice) and the stream the solve is queued
-// on.  A lattice owns one for its single-RHS calls; a batched solve creates
-// one per RHS.
+// even-odd operator on a half lattice, 27-31: the half-lattice FP64 fields
+// b_e, b_o, x_e, x_o, b^_e of an even-odd solve) and the stream the solve
+// is queued on.  A lattice owns one for its single-RHS calls; a batched
+// solve creates one per RHS.
 constexpr int kSchurSlot = 24;
+constexpr int kEoSlot = 27;
 struct SolverState {
     SolverScalars *scal = nullptr;
     SolverScalars *scal_host = nullptr;
     ReduceScratch red;
-    wc_field_s *work[27] = {};
+    wc_field_s *work[32] = {};
     cudaStream_t stream = nullptr;
     SolverState *inner = nullptr;   // state of a nested inner solve, created on first use
 };

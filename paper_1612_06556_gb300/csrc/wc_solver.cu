@@ -19,6 +19,11 @@
 // stay FP64 on the GPU.  Every scalar (rho, alpha, omega, beta, norms) is
 // computed on the device by the last block of the fused reduction kernels;
 // the host reads one small struct per iteration to test convergence.
+//
+// The other drivers here: the reliable-update solver (the same recurrence
+// in FP32 with FP64 refreshes of x and r), the nested three-level solver
+// (the flexible one with an FP32 BiCGStab as K), and the even-odd wrapper
+// that runs any of them on the Schur complement of a half lattice.
 #include <math.h>
 
 #include <chrono>
@@ -206,8 +211,8 @@ static wc_status eo_bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, c
     if (st != WC_OK) return inf.status = st;
     cudaStream_t s = lat->stream;
     h->st.stream = s;
-    wc_field f[5] = {};   // be, bo, xe, xo, bh
-    for (int i = 0; i < 5 && st == WC_OK; ++i) st = wc_field_create(h, WC_F64, &f[i]);
+    wc_field f[5] = {};   // be, bo, xe, xo, bh: kept in the half lattice's state between solves
+    for (int i = 0; i < 5 && st == WC_OK; ++i) f[i] = state_work(h, h->st, kEoSlot + i, WC_F64, &st);
     wc_field be = f[0], bo = f[1], xe = f[2], xo = f[3], bh = f[4], t = h->schur_tmp[WC_F64];
     const double k = lat->kappa;
     if (st == WC_OK) st = check_cuda(lat, launch_split(lat, b, be, bo, s), "split");
@@ -236,7 +241,6 @@ static wc_status eo_bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, c
     if (st == WC_OK) st = solver_vectors(lat, lat->st, p0, &w);
     if (st == WC_OK) st = enqueue_true_residual(lat, lat->st, kind, x, b, w);
     if (st == WC_OK) st = read_scalars(lat, lat->st);
-    for (auto &fi : f) wc_field_destroy(fi);
     if (st != WC_OK) return inf.status = st;
     inf = wc_solve_info{};
     inf.iters = iters;
