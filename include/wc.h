@@ -288,6 +288,16 @@ wc_status wc_ras_autotune(wc_lattice lat, wc_field b, const wc_solve_params *p, 
 wc_status wc_action_force(wc_lattice lat, wc_field phi, double *S_out, double *force,
                           const wc_solve_params *p);
 
+/* out = scale * F U for every link (3x3 complex products, canonical force
+ * and gauge layouts [V][4][3][3]; all three device pointers; out may alias
+ * neither input).  With F from wc_action_force and scale = -dL/dS this is
+ * the gradient of a loss L(S) with respect to U on the tangent space of
+ * SU(3): for U -> exp(eps X) U, dS/deps = tr(X F) = Re sum tr(G^+ X U) with
+ * G = -F U.  The paper has no gradient; this is the step that turns the
+ * force into the autograd gradient of the binding.  Asynchronous on the
+ * lattice stream. */
+wc_status wc_force_times_links(wc_lattice lat, const double *force, const double *U, double scale, double *out);
+
 const char *wc_last_error(wc_lattice lat);
 
 #ifdef __cplusplus

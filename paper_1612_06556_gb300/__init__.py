@@ -39,6 +39,7 @@ EXPORTED = [
     "wc_apply_M", "wc_apply_Mdag", "wc_apply_hop", "wc_dot", "wc_norm2", "wc_axpy_norm",
     "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
     "wc_dot_noalloc", "wc_ras_autotune", "wc_apply_shape", "wc_apply_schur", "wc_apply_multi",
+    "wc_force_times_links",
 ]
 
 
@@ -88,6 +89,7 @@ _L.wc_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(
 _L.wc_action_force.argtypes = [_vp, _vp, _dp, _vp, ctypes.POINTER(SolveParams)]
 _L.wc_apply_schur.argtypes = [_vp, _vp, _vp, ctypes.c_int]
 _L.wc_apply_multi.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]
+_L.wc_force_times_links.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp]
 _L.wc_apply_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
 _L.wc_ras_autotune.argtypes = [_vp, _vp, ctypes.POINTER(SolveParams), ctypes.POINTER(RasParams)]
 _L.wc_dot_noalloc.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
@@ -287,6 +289,16 @@ class Lattice:
                                   ctypes.byref(p)), self.handle)
         return S.value
 
+    def force_times_links(self, F, U, scale: float, out):
+        """out = scale * F U per link (contiguous CUDA complex128 tensors
+        [V,4,3,3]); see wc_force_times_links."""
+        for t in (F, U, out):
+            if not (t.is_cuda and t.numel() == self.volume * 36):
+                raise ValueError("F, U and out must be CUDA tensors of V*4*3*3 complex128")
+        _check(_L.wc_force_times_links(self.handle, _vp(_ptr(F)), _vp(_ptr(U)), float(scale), _vp(_ptr(out))),
+               self.handle)
+        return out
+
     def last_error(self) -> str:
         return _L.wc_last_error(self.handle).decode()
 
@@ -359,13 +371,15 @@ def _torch_autograd_function():
             F = torch.empty_like(U)
             S = lattice.action_force(f_phi, F, params)
             ctx.save_for_backward(U, F)
+            ctx.lattice = lattice
             return torch.tensor(S, dtype=torch.float64, device=U.device)
 
         @staticmethod
         def backward(ctx, grad_S):
             U, F = ctx.saved_tensors
-            FU = (F.unsqueeze(-1) * U.unsqueeze(-3)).sum(-2)   # F U per link (3x3)
-            grad_U = -FU * grad_S.to(U.dtype)
+            grad_U = torch.empty_like(U)
+            # grad_U = -grad_S * F U, per link, in the library's kernel
+            ctx.lattice.force_times_links(F, U, -float(grad_S), grad_U)
             return grad_U, None, None, None, None, None
 
     return PseudofermionAction

@@ -404,7 +404,49 @@ wc_status force_from_solutions(wc_lattice lat, wc_field X, wc_field Y, double2 *
 
 using namespace wc;
 
+namespace wc {
+namespace {
+
+// out = scale * F U per link (3x3 complex, canonical [4V][3][3] order)
+__global__ void k_force_times_links(long long nlinks, const double2 *F, const double2 *U, double scale, double2 *out)
+{
+    const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (l >= nlinks) return;
+    const double2 *f = F + 9 * l, *u = U + 9 * l;
+    cx<double> a[9], b[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        a[k] = mkc(f[k].x, f[k].y);
+        b[k] = mkc(u[k].x, u[k].y);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cx<double> acc = a[3 * i] * b[j];
+            acc = cfma(a[3 * i + 1], b[3 + j], acc);
+            acc = cfma(a[3 * i + 2], b[6 + j], acc);
+            out[9 * l + 3 * i + j] = make_double2(scale * acc.re, scale * acc.im);
+        }
+}
+
+}  // namespace
+}  // namespace wc
+
 extern "C" {
+
+wc_status wc_force_times_links(wc_lattice lat, const double *force, const double *U, double scale, double *out)
+{
+    if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
+    if (!force || !U || !out) return set_error(lat, WC_ERR_ARG, "NULL argument");
+    if (!is_device_ptr(force) || !is_device_ptr(U) || !is_device_ptr(out))
+        return set_error(lat, WC_ERR_ARG, "force, U and out must be device pointers");
+    const long long n = 4LL * lat->g.V;
+    k_force_times_links<<<(unsigned)((n + 255) / 256), 256, 0, lat->stream>>>(
+        n, reinterpret_cast<const double2 *>(force), reinterpret_cast<const double2 *>(U), scale,
+        reinterpret_cast<double2 *>(out));
+    return check_cuda(lat, cudaGetLastError(), "force_times_links");
+}
 
 wc_status wc_action_force(wc_lattice lat, wc_field phi, double *S_out, double *force, const wc_solve_params *p)
 {

@@ -90,3 +90,24 @@ def test_autograd_gradient_matches_oracle_and_tangent_derivative():
     fd = (Sp - Sm) / (2 * h)
     an = np.real(np.sum(np.conj(g) * (Lam @ U)))
     assert abs(fd - an) <= 1e-6 * abs(an) + 1e-10 * S_ref
+
+
+def test_force_times_links_kernel():
+    """wc_force_times_links: scale * F U per link against numpy matmuls, and
+    its argument checks (host pointers are rejected)."""
+    import torch
+    w = wc()
+    dims = (4, 2, 2, 6)
+    V = synth.volume(dims)
+    rng = np.random.default_rng(7)
+    F = (rng.standard_normal((V, 4, 3, 3)) + 1j * rng.standard_normal((V, 4, 3, 3)))
+    U = synth.exp_links(dims, 0.5, 8)
+    lat = w.Lattice(dims, -1)
+    Ft, Ut = torch.from_numpy(F).cuda(), torch.from_numpy(U).cuda()
+    out = torch.empty_like(Ut)
+    lat.force_times_links(Ft, Ut, -2.5, out)
+    torch.cuda.synchronize()
+    ref = -2.5 * (F @ U)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-13 * np.max(np.abs(ref))
+    with pytest.raises(ValueError):
+        lat.force_times_links(torch.from_numpy(F), Ut, 1.0, out)
