@@ -24,7 +24,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "volume", "gell_mann", "exp_links", "haar_links", "unit_links",
+    "volume", "gell_mann", "exp_links", "haar_links", "pool_links", "unit_links",
     "random_su3", "random_su3_algebra", "point_source", "z2_source",
     "gaussian_source", "config_inputs", "CONFIGS",
 ]
@@ -83,6 +83,17 @@ def haar_links(dims, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     u = random_su3(volume(dims) * 4, rng)
     return np.ascontiguousarray(u.reshape(volume(dims), 4, 3, 3))
+
+
+def pool_links(dims, seed: int, pool: int = 4096) -> np.ndarray:
+    """Haar-like SU(3) links drawn (seeded) from a pool of `pool` random
+    matrices: every link is a valid SU(3) matrix and neighbouring links
+    differ, at a generation cost independent of the volume's 3x3 algebra
+    (for very large lattices)."""
+    rng = np.random.default_rng(seed)
+    base = random_su3(pool, rng)
+    idx = rng.integers(0, pool, size=volume(dims) * 4)
+    return np.ascontiguousarray(base[idx].reshape(volume(dims), 4, 3, 3))
 
 
 def unit_links(dims) -> np.ndarray:

@@ -211,3 +211,20 @@ def test_persistent_launch_walks_all_blocks(shape):
         ref = oracle.apply_M(dims, tbc, kappa, csw, U, psi, sites=sites)
         assert rel_err(out[sites], ref) <= 1e-5
         assert np.count_nonzero(np.all(out.reshape(V, -1) == 0, axis=1)) == 0
+
+
+def test_large_lattice_48x48x48x64_sampled():
+    """A 48^3x64 lattice (7.1 M sites; the FP64 link and clover arrays hold
+    255 M 16-byte elements, 4 GB each): FP64, FP32 and FP16 applies on
+    sampled sites against the oracle, so that no index or plane offset
+    overflows at this size."""
+    dims, kappa, csw, tbc = (48, 48, 48, 64), 0.125, 1.2, -1
+    U = synth.pool_links(dims, 77)
+    psi = synth.z2_source(dims, 78)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    V = synth.volume(dims)
+    sites = np.concatenate([np.random.default_rng(79).choice(V, 1000, replace=False), [0, V - 1]])
+    ref = oracle.apply_M(dims, tbc, kappa, csw, U, psi, sites=sites)
+    for prec in (0, 1, 2):
+        out = gpu_apply(lat, psi, prec, "M")[sites]
+        assert rel_err(out, ref) <= TOL[prec], prec
