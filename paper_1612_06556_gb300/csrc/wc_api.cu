@@ -446,6 +446,7 @@ wc_status wc_destroy_lattice(wc_lattice lat)
     free_gauge(lat->gauge);
     free_clover(lat->clover);
     free_clover(lat->cinv);
+    free_clover(lat->ceo);
     cudaFree(lat->staging);
     delete lat;
     return WC_OK;

@@ -103,29 +103,45 @@ __device__ bool invert6(cx<double> a[6][6])
     return true;
 }
 
-__global__ void k_clover_invert(int V, CloverStore C, CloverStore Ci, int *bad)
+// one packed block (36 reals) at position pos of a clover store, in all
+// three precisions
+__device__ void store_block(const CloverStore &S, int V, int pos, int b, const double r[36])
 {
+#pragma unroll
+    for (int q = 0; q < 18; ++q) S.c64[((size_t)b * 18 + q) * V + pos] = make_double2(r[2 * q], r[2 * q + 1]);
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+        S.c32[((size_t)b * 9 + q) * V + pos] =
+            make_float4((float)r[4 * q], (float)r[4 * q + 1], (float)r[4 * q + 2], (float)r[4 * q + 3]);
+    unsigned *c16 = reinterpret_cast<unsigned *>(S.c16);
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        const int gq = 18 * b + q;
+        c16[((size_t)(gq >> 2) * V + pos) * 4 + (gq & 3)] = c2h((float)r[2 * q], (float)r[2 * q + 1]);
+    }
+}
+
+// Parity-ordered copies for the even-odd kernels: within every component
+// plane, position parity(x) * V/2 + (x >> 1), so that the threads of one
+// parity read contiguous memory (full-volume order would fetch every other
+// site's entries with them).  Ce: A = 1 + T; Ci: A^-1.
+__global__ void k_clover_invert(Geom g, CloverStore C, CloverStore Ce, CloverStore Ci, int *bad)
+{
+    const int V = g.V;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= V) return;
+    int c[4];
+    site_coords(g, x, c);
+    const int pos = ((c[0] + c[1] + c[2] + c[3]) & 1) * (V >> 1) + (x >> 1);
     for (int b = 0; b < 2; ++b) {
         double r[36];
         P64::load_clover(C, V, x, b, r);
+        store_block(Ce, V, pos, b, r);
         cx<double> m[6][6];
         unpack_block(r, m);
         if (!invert6(m)) atomicExch(bad, 1);
         pack_block(m, r);
-#pragma unroll
-        for (int q = 0; q < 18; ++q) Ci.c64[((size_t)b * 18 + q) * V + x] = make_double2(r[2 * q], r[2 * q + 1]);
-#pragma unroll
-        for (int q = 0; q < 9; ++q)
-            Ci.c32[((size_t)b * 9 + q) * V + x] =
-                make_float4((float)r[4 * q], (float)r[4 * q + 1], (float)r[4 * q + 2], (float)r[4 * q + 3]);
-        unsigned *c16 = reinterpret_cast<unsigned *>(Ci.c16);
-#pragma unroll
-        for (int q = 0; q < 18; ++q) {
-            const int gq = 18 * b + q;
-            c16[((size_t)(gq >> 2) * V + x) * 4 + (gq & 3)] = c2h((float)r[2 * q], (float)r[2 * q + 1]);
-        }
+        store_block(Ci, V, pos, b, r);
     }
 }
 
@@ -190,6 +206,7 @@ __device__ __forceinline__ void clover_apply(const R r0[36], const R r1[36], con
 
 // For the sites of parity p (half index i):
 //   HOP: h = sum of hops of `hin` (opposite parity)
+//   C, Ci: clover and inverse in parity order (k_clover_invert)
 //   MODE 0: out = Cinv h
 //        1: out = C vin + beta h
 //        2: out = vin + beta h
@@ -227,8 +244,8 @@ __global__ void __launch_bounds__(128) k_eo(Geom g, int p, GaugeStore U, CloverS
         P::load_spinor(vin, vin_nrm, Vh, i, v);
         if (MODE == 1) {
             R r0[36], r1[36];
-            P::load_clover(C, g.V, x, 0, r0);
-            P::load_clover(C, g.V, x, 1, r1);
+            P::load_clover(C, g.V, p * Vh + i, 0, r0);
+            P::load_clover(C, g.V, p * Vh + i, 1, r1);
             clover_apply(r0, r1, v, o);
 #pragma unroll
             for (int k = 0; k < 12; ++k) o[k] = o[k] + bt * h[k];
@@ -244,8 +261,8 @@ __global__ void __launch_bounds__(128) k_eo(Geom g, int p, GaugeStore U, CloverS
         }
     }
     R r0[36], r1[36];
-    P::load_clover(Ci, g.V, x, 0, r0);
-    P::load_clover(Ci, g.V, x, 1, r1);
+    P::load_clover(Ci, g.V, p * Vh + i, 0, r0);
+    P::load_clover(Ci, g.V, p * Vh + i, 1, r1);
     clover_apply(r0, r1, v, o);
     P::store_spinor(out, out_nrm, Vh, i, o);
 }
@@ -297,7 +314,7 @@ cudaError_t launch_eo_p(const wc_lattice_s *full, int parity, int mode, const wc
     const void *vd = vin ? vin->data : nullptr;
     const float *vn = vin ? vin->nrm : nullptr;
 #define WC_EO(M)                                                                                                \
-    k_eo<P, DAG, M><<<grid, block, 0, stream>>>(full->g, parity, full->gauge, full->clover, full->cinv, hd, hn, \
+    k_eo<P, DAG, M><<<grid, block, 0, stream>>>(full->g, parity, full->gauge, full->ceo, full->cinv, hd, hn,    \
                                                 vd, vn, out->data, out->nrm, beta)
     switch (mode) {
     case 0: WC_EO(0); break;
@@ -379,21 +396,21 @@ wc_status build_clover_inverse(wc_lattice lat)
 {
     if (lat->cinv_loaded) return WC_OK;
     const int V = lat->g.V;
-    CloverStore &c = lat->cinv;
     wc_status st = WC_OK;
-    if (!c.c64) {
-        st = check_cuda(lat, cudaMalloc(&c.c64, sizeof(double2) * 36 * (size_t)V), "cudaMalloc(clover inverse)");
+    for (CloverStore *c : {&lat->cinv, &lat->ceo}) {
+        if (c->c64) continue;
+        st = check_cuda(lat, cudaMalloc(&c->c64, sizeof(double2) * 36 * (size_t)V), "cudaMalloc(clover inverse)");
         if (st == WC_OK)
-            st = check_cuda(lat, cudaMalloc(&c.c32, sizeof(float4) * 18 * (size_t)V), "cudaMalloc(clover inverse)");
+            st = check_cuda(lat, cudaMalloc(&c->c32, sizeof(float4) * 18 * (size_t)V), "cudaMalloc(clover inverse)");
         if (st == WC_OK)
-            st = check_cuda(lat, cudaMalloc(&c.c16, sizeof(uint4) * 9 * (size_t)V), "cudaMalloc(clover inverse)");
+            st = check_cuda(lat, cudaMalloc(&c->c16, sizeof(uint4) * 9 * (size_t)V), "cudaMalloc(clover inverse)");
         if (st != WC_OK) return st;
     }
     int *bad = nullptr;
     st = check_cuda(lat, cudaMalloc(&bad, sizeof(int)), "cudaMalloc");
     if (st != WC_OK) return st;
     cudaMemsetAsync(bad, 0, sizeof(int), lat->stream);
-    k_clover_invert<<<(V + 63) / 64, 64, 0, lat->stream>>>(V, lat->clover, c, bad);
+    k_clover_invert<<<(V + 63) / 64, 64, 0, lat->stream>>>(lat->g, lat->clover, lat->ceo, lat->cinv, bad);
     int h = 0;
     st = check_launch(lat, "clover_invert");
     if (st == WC_OK) st = check_cuda(lat, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, lat->stream),

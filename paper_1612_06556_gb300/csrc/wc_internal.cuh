@@ -66,7 +66,8 @@ struct wc_lattice_s {
     size_t staging_bytes = 0;
     // even-odd: A^-1 (built on first use) and the half lattice whose
     // operator is the Schur complement M^ (V/2 sites, shares gauge/clover)
-    wc::CloverStore cinv;
+    wc::CloverStore cinv;                     // A^-1, parity-ordered planes (even-odd kernels)
+    wc::CloverStore ceo;                      // A, parity-ordered copy (even-odd kernels)
     bool cinv_loaded = false;
     wc_lattice_s *half = nullptr;
     wc_lattice_s *schur_parent = nullptr;     // set on a half lattice
