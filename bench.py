@@ -48,12 +48,12 @@ METRIC = "Wilson-Clover apply GFlop/s & % HBM roofline; mixed vs FP64 solve time
 # dram__bytes_write.sum), valid only while the kernel source is unchanged.
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one k_apply<P32, M>
-    # launch at 24^3x32 (shape #11; the persistent shape runs the same
-    # kernel body), from the capture summarised in
-    # profiles/apply_fp32_24x24x24x32.md; valid while the kernel sources hash
-    # to sources_sha
-    "sources_sha": "9dbf8568a8e5be39",
-    "bytes_per_launch": 291716096,
+    # launch at 24^3x32 (shape #20: persistent, programmatic dependent launch;
+    # the other lexicographic shapes run the same kernel body), from the
+    # capture summarised in profiles/apply_fp32_24x24x24x32.md; valid while
+    # the operator's device sources hash to sources_sha
+    "sources_sha": "718dcb13f99240ae",
+    "bytes_per_launch": 295534848,
 }
 
 
