@@ -26,6 +26,43 @@ __device__ __forceinline__ double warp_sum(double v)
 
 }  // namespace
 
+// Last block of a grid reduction: every thread adds the partials of blocks
+// t, t + blockDim, ... (independent loads, unrolled), then the block sums
+// the thread totals by warp shuffles and one warp over the warp totals --
+// a fixed order, so the result is the same on every run.  (One warp
+// walking all partials serialises ~gridDim/32 L2 round trips per value,
+// 15-20 us per reduction kernel at 8 blocks per SM.)  sm: >= 32 * N
+// doubles of shared scratch.  Resets the ticket.
+template <int N>
+__device__ __forceinline__ void final_sum(const ReduceScratch &rs, double *out, double *sm)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double t[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) t[i] = 0.0;
+#pragma unroll 4
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int i = 0; i < N; ++i) t[i] += __ldcg(rs.partials + (size_t)b * 8 + i);
+#pragma unroll
+    for (int i = 0; i < N; ++i) t[i] = warp_sum(t[i]);
+    __syncthreads();   // sm may still be read by the first stage
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) sm[wid * N + i] = t[i];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double u = lane < nw ? sm[lane * N + i] : 0.0;
+            u = warp_sum(u);
+            if (lane == 0) out[i] = u;
+        }
+        if (lane == 0) *rs.ticket = 0u;
+    }
+    __syncthreads();   // out[] is read by thread 0 after return
+}
+
 // Reduce v[0..N) over the grid.  Returns true in thread 0 of the last block,
 // after out[0..N) holds the grid totals (summed in a fixed order).
 template <int N>
@@ -56,16 +93,7 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[N], const ReduceScratch 
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if (wid == 0) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            double s = 0.0;
-            for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(rs.partials + (size_t)b * 8 + i);
-            s = warp_sum(s);
-            if (lane == 0) out[i] = s;
-        }
-        if (lane == 0) *rs.ticket = 0u;
-    }
+    final_sum<N>(rs, out, &sm[0][0]);
     return threadIdx.x == 0;
 }
 
@@ -457,16 +485,8 @@ __device__ __forceinline__ bool grid_reduce_f(float (&v)[N], const ReduceScratch
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if (wid == 0) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            double t = 0.0;
-            for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(rs.partials + (size_t)b * 8 + i);
-            t = warp_sum(t);
-            if (lane == 0) out[i] = t;
-        }
-        if (lane == 0) *rs.ticket = 0u;
-    }
+    __shared__ double smd[32 * N];
+    final_sum<N>(rs, out, smd);
     return threadIdx.x == 0;
 }
 
