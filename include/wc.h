@@ -160,12 +160,12 @@ wc_status wc_load_clover(wc_lattice lat, double csw, double kappa);
 wc_status wc_field_create(wc_lattice lat, wc_prec prec, wc_field *out);
 wc_status wc_field_destroy(wc_field f);
 /* canonical complex128 (device or host) -> field (rounded to nearest).
- * Page-locked host data is read by the conversion kernel directly over the
- * host link; pageable host data goes through a device staging copy.
- * Device data: asynchronous on the lattice stream; host data: blocking. */
+ * Host data goes through one copy-engine transfer into a device staging
+ * buffer (reading host memory from the conversion kernel itself measured
+ * 2.6x slower per import + export on GB300).  Device data: asynchronous on
+ * the lattice stream; host data: blocking. */
 wc_status wc_field_import(wc_field f, const double *data);
-/* field -> canonical complex128 (device or host; page-locked host memory
- * is written directly by the conversion kernel).  Same blocking rules. */
+/* field -> canonical complex128 (device or host).  Same rules. */
 wc_status wc_field_export(wc_field f, double *data);
 /* dst = src converted to dst's precision, times scale (any precisions). */
 wc_status wc_field_copy(wc_field dst, wc_field src, double scale);

@@ -56,20 +56,6 @@ bool is_device_pointer(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Device-accessible address of page-locked host memory (cudaHostAlloc /
-// cudaHostRegister, e.g. a pinned torch tensor), else nullptr.  Kernels read
-// and write such memory directly over the host link, so a host field
-// import/export needs no device staging copy.
-const void *pinned_device_address(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
-}
-
 // ------------------------------------------------------------------------
 // canonical <-> internal
 // ------------------------------------------------------------------------
@@ -568,11 +554,8 @@ wc_status wc_field_import(wc_field f, const double *data)
     const size_t bytes = sizeof(double2) * 12 * (size_t)V;
     const double2 *src = reinterpret_cast<const double2 *>(data);
     wc_status st = WC_OK;
-    const void *pinned = is_device_pointer(data) ? nullptr : pinned_device_address(data);
     const bool host = !is_device_pointer(data);
-    if (pinned) {
-        src = static_cast<const double2 *>(pinned);
-    } else if (host) {
+    if (host) {
         st = need_staging(lat, bytes);
         if (st != WC_OK) return st;
         st = check_cuda(lat, cudaMemcpyAsync(lat->staging, data, bytes, cudaMemcpyHostToDevice, lat->stream),
@@ -600,12 +583,9 @@ wc_status wc_field_export(wc_field f, double *data)
     const int V = lat->g.V;
     const size_t bytes = sizeof(double2) * 12 * (size_t)V;
     const bool host = !is_device_pointer(data);
-    const void *pinned = host ? pinned_device_address(data) : nullptr;
     double2 *dst = reinterpret_cast<double2 *>(data);
     wc_status st = WC_OK;
-    if (pinned) {
-        dst = static_cast<double2 *>(const_cast<void *>(pinned));
-    } else if (host) {
+    if (host) {
         st = need_staging(lat, bytes);
         if (st != WC_OK) return st;
         dst = lat->staging;
@@ -618,10 +598,11 @@ wc_status wc_field_export(wc_field f, double *data)
     else
         k_export<P16><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
     st = check_launch(lat, "export");
-    if (st == WC_OK && host && !pinned)
+    if (st == WC_OK && host) {
         st = check_cuda(lat, cudaMemcpyAsync(data, lat->staging, bytes, cudaMemcpyDeviceToHost, lat->stream),
                         "cudaMemcpyAsync(export)");
-    if (st == WC_OK && host) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync(export)");
+        if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync(export)");
+    }
     return st;
 }
 

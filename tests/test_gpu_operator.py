@@ -88,8 +88,7 @@ def test_import_export_round_trip_and_fp16_scale():
 
 def test_import_export_memory_kinds():
     """Pageable (numpy), page-locked (pinned torch) and device (CUDA torch)
-    buffers give identical imports and exports (the pinned path is read and
-    written by the conversion kernels directly)."""
+    buffers give identical imports and exports."""
     import torch
     dims = (6, 4, 4, 6)
     lat = make_lattice(dims, synth.unit_links(dims), 1.0, 0.1, -1)
