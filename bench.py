@@ -385,6 +385,13 @@ def batch_comparison(wc, args):
     run_batch(eo)                           # warm-up: clover inverses, half-lattice fields
     infos_eo, t_eo = run_batch(eo)
     t0 = time.perf_counter()
+    seq_eo = []
+    for lat, b in zip(lats, bs):
+        x = lat.field(wc.F64)
+        seq_eo.append(lat.solve(x, b, eo, check=False))
+        x.close()
+    t_seq_eo = time.perf_counter() - t0
+    t0 = time.perf_counter()
     seq = []
     for lat, b in zip(lats, bs):
         x = lat.field(wc.F64)
@@ -403,6 +410,7 @@ def batch_comparison(wc, args):
             "flexible_batch_seconds": t_flex, "flexible_all_ok": all(i.status == 0 for i in infos_flex),
             "flexible_steps": [min(i.iters for i in infos_flex), max(i.iters for i in infos_flex)],
             "even_odd_batch_seconds": t_eo, "even_odd_all_ok": all(i.status == 0 for i in infos_eo),
+            "even_odd_sequential_seconds": t_seq_eo, "even_odd_sequential_all_ok": all(i.status == 0 for i in seq_eo),
             "even_odd_steps": [min(i.iters for i in infos_eo), max(i.iters for i in infos_eo)],
             "even_odd_max_true_rel_resid": max(i.true_rel_resid for i in infos_eo),
             "ras_blocks_autotuned": shapes}
