@@ -99,8 +99,8 @@ typedef struct {
  *   falls below inner_tol or for inner_iters steps.
  * With precond NONE, FLEXIBLE is plain FP64 BiCGStab, RELIABLE is FP32
  * BiCGStab with FP64 reliable updates and NESTED's inner FP32 BiCGStab runs
- * without RAS.  even_odd = 1 (precond NONE) runs any of the three on the
- * even-site Schur complement (the paper's two outer levels, Sec. 2).
+ * without RAS.  even_odd = 1 runs any of the three on the even-site Schur
+ * complement (with or without RAS), as the paper's solvers do (Sec. 2).
  * The true residual |b - M x| / |b| reported and tested against tol is FP64
  * in all of them, on the full lattice. */
 typedef enum { WC_SOLVER_FLEXIBLE = 0, WC_SOLVER_RELIABLE = 1, WC_SOLVER_NESTED = 2 } wc_solver_kind;
@@ -117,8 +117,11 @@ typedef struct {
     double inner_tol;      /* NESTED inner relative tolerance, 0 < inner_tol < 1 (0: 0.01) */
     int inner_iters;       /* NESTED inner step limit, >= 0 (0: 100) */
     int even_odd;          /* 1: solve the even-site Schur complement (see wc_apply_schur) and
-                              reconstruct the odd sites; needs even extents and precond NONE
-                              (any solver kind); 0: full lattice */
+                              reconstruct the odd sites; needs even extents; any solver kind;
+                              with precond RAS the preconditioner is the full lattice's RAS on
+                              the even vector extended by zeros, restricted to the even sites
+                              (Sec. 2: the inner solver is even-odd and RAS preconditioned);
+                              0: full lattice */
 } wc_solve_params;
 
 typedef struct {

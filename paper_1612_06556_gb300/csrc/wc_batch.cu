@@ -342,6 +342,8 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
     if (p->solver == WC_SOLVER_NESTED)
         return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: the nested solver is host-driven; use FLEXIBLE "
                                               "or RELIABLE");
+    if (p->even_odd && p->precond == WC_PRECOND_RAS && p->ras.block[0] == 0)
+        return set_error(nullptr, WC_ERR_ARG, "wc_solve_batch: with even_odd give the RAS block shape explicitly");
     for (int i = 0; i < n; ++i) {
         // the RAS shape is checked after autotuning when it is left to it
         wc_solve_params q = *p;

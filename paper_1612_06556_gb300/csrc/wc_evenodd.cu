@@ -279,6 +279,7 @@ __global__ void k_split(Geom g, const void *full, const float *full_nrm, void *e
     cx<typename P::real> s[12];
     P::load_spinor(full, full_nrm, g.V, full_site(g, i, 0, c), s);
     P::store_spinor(ev, ev_nrm, Vh, i, s);
+    if (!od) return;   // odd half not wanted
     P::load_spinor(full, full_nrm, g.V, full_site(g, i, 1, c), s);
     P::store_spinor(od, od_nrm, Vh, i, s);
 }
@@ -344,17 +345,20 @@ cudaError_t launch_eo(const wc_lattice_s *full, int parity, int mode, int dagger
                   : launch_eo_p<P16, 0>(full, parity, mode, hin, vin, out, beta, stream);
 }
 
+// od may be NULL: only the even half is written
 cudaError_t launch_split(const wc_lattice_s *full, const wc_field_s *f, wc_field_s *ev, wc_field_s *od,
                          cudaStream_t stream)
 {
     const int Vh = full->g.V >> 1;
     dim3 grid((Vh + 255) / 256), block(256);
+    void *od_d = od ? od->data : nullptr;
+    float *od_n = od ? od->nrm : nullptr;
     if (f->prec == WC_F64)
-        k_split<P64><<<grid, block, 0, stream>>>(full->g, f->data, f->nrm, ev->data, ev->nrm, od->data, od->nrm);
+        k_split<P64><<<grid, block, 0, stream>>>(full->g, f->data, f->nrm, ev->data, ev->nrm, od_d, od_n);
     else if (f->prec == WC_F32)
-        k_split<P32><<<grid, block, 0, stream>>>(full->g, f->data, f->nrm, ev->data, ev->nrm, od->data, od->nrm);
+        k_split<P32><<<grid, block, 0, stream>>>(full->g, f->data, f->nrm, ev->data, ev->nrm, od_d, od_n);
     else
-        k_split<P16><<<grid, block, 0, stream>>>(full->g, f->data, f->nrm, ev->data, ev->nrm, od->data, od->nrm);
+        k_split<P16><<<grid, block, 0, stream>>>(full->g, f->data, f->nrm, ev->data, ev->nrm, od_d, od_n);
     return cudaGetLastError();
 }
 
@@ -409,10 +413,12 @@ wc_status build_clover_inverse(wc_lattice lat)
     int *bad = nullptr;
     st = check_cuda(lat, cudaMalloc(&bad, sizeof(int)), "cudaMalloc");
     if (st != WC_OK) return st;
-    cudaMemsetAsync(bad, 0, sizeof(int), lat->stream);
-    k_clover_invert<<<(V + 63) / 64, 64, 0, lat->stream>>>(lat->g, lat->clover, lat->ceo, lat->cinv, bad);
+    st = check_cuda(lat, cudaMemsetAsync(bad, 0, sizeof(int), lat->stream), "memset");
+    if (st == WC_OK) {
+        k_clover_invert<<<(V + 63) / 64, 64, 0, lat->stream>>>(lat->g, lat->clover, lat->ceo, lat->cinv, bad);
+        st = check_launch(lat, "clover_invert");
+    }
     int h = 0;
-    st = check_launch(lat, "clover_invert");
     if (st == WC_OK) st = check_cuda(lat, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, lat->stream),
                                      "copy");
     if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync");

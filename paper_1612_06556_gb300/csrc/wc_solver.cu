@@ -71,6 +71,8 @@ wc_status read_scalars(wc_lattice lat, SolverState &S)
     return st;
 }
 
+static wc_status eo_ras_temps(wc_lattice lat, SolverState &S, wc_prec prec);
+
 wc_status solver_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &p, SolverVecs *w)
 {
     wc_status st = WC_OK;
@@ -89,10 +91,42 @@ wc_status solver_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &
         if (st == WC_OK) w->shat = state_work(lat, S, 7, WC_F64, &st);
     }
     if (st == WC_OK && p.precond == WC_PRECOND_RAS && p.solver != WC_SOLVER_NESTED) {
+        st = eo_ras_temps(lat, S, p.inner_prec);
         const int lo = p.inner_prec == WC_F16 ? 22 : 10;
         if (st == WC_OK) w->lo_in = state_work(lat, S, lo, p.inner_prec, &st);
         if (st == WC_OK) w->lo_out = state_work(lat, S, lo + 1, p.inner_prec, &st);
     }
+    return st;
+}
+
+// The full-lattice fields the RAS of an even-odd solve works in (on the
+// parent lattice, precision prec), created with the solver's vectors so
+// that nothing is allocated while a batch is being captured.
+static wc_status eo_ras_temps(wc_lattice lat, SolverState &S, wc_prec prec)
+{
+    if (!lat->schur_parent) return WC_OK;
+    const int base = kRasEoSlot + 2 * (prec == WC_F16);
+    wc_status st = WC_OK;
+    for (int i = 0; i < 2 && st == WC_OK; ++i)
+        if (!S.work[base + i]) st = wc_field_create(lat->schur_parent, prec, &S.work[base + i]);
+    return st;
+}
+
+// RAS for the operator of lat.  On a half lattice (even-odd) it is the full
+// lattice's RAS applied to the even vector extended by zeros on the odd
+// sites and restricted back to the even sites: M^^-1 is exactly the
+// even-even block of M^-1, and RAS approximates M^-1.
+static wc_status ras_apply(wc_lattice lat, SolverState &S, wc_field out, wc_field in, const wc_ras_params &ras,
+                           int kind)
+{
+    if (!lat->schur_parent) return check_cuda(lat, launch_ras(lat, out, in, ras, kind, S.stream), "ras");
+    wc_lattice full = lat->schur_parent;
+    const int base = kRasEoSlot + 2 * (in->prec == WC_F16);
+    wc_field a = S.work[base], b = S.work[base + 1];
+    if (!a || !b) return set_error(lat, WC_ERR_STATE, "even-odd RAS fields missing");
+    wc_status st = check_cuda(lat, launch_merge(full, in, nullptr, a, S.stream), "embed");
+    if (st == WC_OK) st = check_cuda(lat, launch_ras(full, b, a, ras, kind, S.stream), "ras");
+    if (st == WC_OK) st = check_cuda(lat, launch_split(full, b, out, nullptr, S.stream), "restrict");
     return st;
 }
 
@@ -106,7 +140,7 @@ static wc_status apply_precond(wc_lattice lat, SolverState &S, const wc_solve_pa
     if (p.solver == WC_SOLVER_NESTED) return nested_inner(lat, S, p, kind, u, uhat, norm2_dev);
     if (p.precond == WC_PRECOND_NONE) return WC_OK;   // uhat aliases u
     wc_status st = check_cuda(lat, launch_copy(lat, w.lo_in, u, 1.0, norm2_dev, 1, S.stream), "defect cast down");
-    if (st == WC_OK) st = check_cuda(lat, launch_ras(lat, w.lo_out, w.lo_in, p.ras, kind, S.stream), "ras");
+    if (st == WC_OK) st = ras_apply(lat, S, w.lo_out, w.lo_in, p.ras, kind);
     if (st == WC_OK)
         st = check_cuda(lat, launch_copy(lat, uhat, w.lo_out, 1.0, norm2_dev, 0, S.stream), "defect cast up");
     return st;
@@ -369,6 +403,8 @@ wc_status lo_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &p, L
     w->lo_in = w->lo_out = nullptr;
     if (st == WC_OK && lat->schur_parent) state_work(lat, S, kSchurSlot + WC_F32, WC_F32, &st);
     if (st == WC_OK && lat->schur_parent) state_work(lat, S, kSchurSlot + WC_F64, WC_F64, &st);
+    if (st == WC_OK && p.precond == WC_PRECOND_RAS)
+        st = eo_ras_temps(lat, S, p.inner_prec == WC_F16 ? WC_F16 : WC_F32);
     if (st == WC_OK && p.precond == WC_PRECOND_RAS && p.inner_prec == WC_F16) {
         w->lo_in = state_work(lat, S, 22, WC_F16, &st);
         if (st == WC_OK) w->lo_out = state_work(lat, S, 23, WC_F16, &st);
@@ -384,9 +420,9 @@ wc_status lo_precond(wc_lattice lat, SolverState &S, const wc_solve_params &p, i
                      wc_field u, wc_field uhat)
 {
     if (p.precond == WC_PRECOND_NONE) return WC_OK;
-    if (p.inner_prec != WC_F16) return check_cuda(lat, launch_ras(lat, uhat, u, p.ras, kind, S.stream), "ras");
+    if (p.inner_prec != WC_F16) return ras_apply(lat, S, uhat, u, p.ras, kind);
     wc_status st = check_cuda(lat, launch_copy(lat, w.lo_in, u, 1.0, nullptr, 0, S.stream), "cast to FP16");
-    if (st == WC_OK) st = check_cuda(lat, launch_ras(lat, w.lo_out, w.lo_in, p.ras, kind, S.stream), "ras");
+    if (st == WC_OK) st = ras_apply(lat, S, w.lo_out, w.lo_in, p.ras, kind);
     if (st == WC_OK) st = check_cuda(lat, launch_copy(lat, uhat, w.lo_out, 1.0, nullptr, 0, S.stream), "cast");
     return st;
 }
@@ -645,8 +681,6 @@ wc_status check_solve_args(wc_lattice lat, wc_field x, wc_field b, const wc_solv
         return set_error(lat, WC_ERR_ARG, "unknown preconditioner");
     if (p->solver != WC_SOLVER_FLEXIBLE && p->solver != WC_SOLVER_RELIABLE && p->solver != WC_SOLVER_NESTED)
         return set_error(lat, WC_ERR_ARG, "unknown solver kind");
-    if (p->even_odd && p->precond != WC_PRECOND_NONE)
-        return set_error(lat, WC_ERR_ARG, "even-odd solves take no RAS preconditioner (precond NONE)");
     if (p->solver == WC_SOLVER_NESTED && (!(p->inner_tol >= 0.0 && p->inner_tol < 1.0) || p->inner_iters < 0))
         return set_error(lat, WC_ERR_ARG, "inner_tol must be in [0, 1) and inner_iters >= 0");
     if (p->solver == WC_SOLVER_RELIABLE && !(p->delta >= 0.0 && p->delta < 1.0))

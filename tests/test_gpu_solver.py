@@ -241,8 +241,10 @@ def test_reliable_update_argument_errors():
     with pytest.raises(w.WCError) as e:
         lat.solve(x, b, precond=w.PRECOND_RAS, solver=w.SOLVER_RELIABLE, delta=1.5)
     assert e.value.status == 1
-    with pytest.raises(w.WCError) as e:
-        lat.solve(x, b, precond=w.PRECOND_RAS, even_odd=True)          # even-odd takes no RAS
+    dims_odd = (8, 8, 8, 7)
+    lat_odd = make_lattice(dims_odd, synth.unit_links(dims_odd), 1.0, 0.1, -1)
+    with pytest.raises(w.WCError) as e:                                # even-odd needs even extents
+        lat_odd.solve(lat_odd.field(0), lat_odd.field(0).load(synth.gaussian_source(dims_odd, 2)), even_odd=True)
     assert e.value.status == 1
 
 
