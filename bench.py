@@ -522,10 +522,13 @@ def large_lattice(wc, args):
     # near-critical (kappa 0.128, csw 1.6): plain and reliable-update
     # BiCGStab stagnate near 1e-8 here; the paper's three-level structure
     # (FP64 flexible outer, FP32 inner BiCGStab) converges.  FP16 storage as
-    # prescribed: inner BiCGStab + RAS with FP16 spinors, links and clover;
-    # fastest: inner BiCGStab on the even-odd operator.
+    # prescribed: inner BiCGStab + RAS with FP16 spinors, links and clover,
+    # on the full lattice and on the even-odd operator (the paper's inner
+    # configuration); fastest: inner BiCGStab on the even-odd operator.
     b = lat.field(wc.F64).load(src)
     solves = [("solve_nested_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16, max_iter=20)),
+              ("solve_eo_nested_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16, even_odd=True,
+                                               max_iter=20)),
               ("solve_eo_nested_f32", dict(precond=wc.PRECOND_NONE, even_odd=True, max_iter=60))]
     if args.large_solve:
         solves.append(("solve_eo_reliable_f32", dict(precond=wc.PRECOND_NONE, even_odd=True, max_iter=args.large_solve,
@@ -586,7 +589,9 @@ def solve_comparison(wc, lat, src, args):
                      ("eo_reliable_f32_delta1e-4", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE,
                                                         delta=1e-4, even_odd=True)),
                      ("eo_nested_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED, inner_tol=0.01,
-                                            inner_iters=100, even_odd=True))):
+                                            inner_iters=100, even_odd=True)),
+                     ("eo_reliable_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
+                                                  solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True))):
         if args.solves and name not in args.solves.split(","):
             continue
         x = lat.field(wc.F64)
