@@ -29,7 +29,10 @@
  *   operator         M = (1 + T) - kappa H
  *   RAS block solve  k minimal-residual steps of M restricted (Dirichlet) to
  *                    a block extended by delta sites per face, from zero;
- *                    only the block's core is written back
+ *                    only the block's core is written back.  Pinned to this
+ *                    definition by dense brute force in the tests; against
+ *                    the paper's own RAS variant: parity unpinned (the paper
+ *                    gives no formula and its cited RAS paper is not at hand)
  *   force            S = phi^+ (M^+ M)^-1 phi, dS/deps = Re tr(Lambda G) for
  *                    U -> exp(eps Lambda) U; F = TA(G)
  */
