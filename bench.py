@@ -384,6 +384,10 @@ def batch_comparison(wc, args):
                          delta=0.01, even_odd=True)
     run_batch(eo)                           # warm-up: clover inverses, half-lattice fields
     infos_eo, t_eo = run_batch(eo)
+    eo_ras = wc.solve_params(tol=1e-10, max_iter=5000, precond=wc.PRECOND_RAS, inner_prec=wc.F32,
+                             block=(4, 4, 4, 4), solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True)
+    run_batch(eo_ras)
+    infos_eo_ras, t_eo_ras = run_batch(eo_ras)
     t0 = time.perf_counter()
     seq_eo = []
     for lat, b in zip(lats, bs):
@@ -411,6 +415,8 @@ def batch_comparison(wc, args):
             "flexible_steps": [min(i.iters for i in infos_flex), max(i.iters for i in infos_flex)],
             "even_odd_batch_seconds": t_eo, "even_odd_all_ok": all(i.status == 0 for i in infos_eo),
             "even_odd_sequential_seconds": t_seq_eo, "even_odd_sequential_all_ok": all(i.status == 0 for i in seq_eo),
+            "even_odd_ras_batch_seconds": t_eo_ras, "even_odd_ras_all_ok": all(i.status == 0 for i in infos_eo_ras),
+            "even_odd_ras_steps": [min(i.iters for i in infos_eo_ras), max(i.iters for i in infos_eo_ras)],
             "even_odd_steps": [min(i.iters for i in infos_eo), max(i.iters for i in infos_eo)],
             "even_odd_max_true_rel_resid": max(i.true_rel_resid for i in infos_eo),
             "ras_blocks_autotuned": shapes}
