@@ -535,7 +535,9 @@ def large_lattice(wc, args):
     solves = [("solve_nested_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16, max_iter=20)),
               ("solve_eo_nested_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16, even_odd=True,
                                                max_iter=20)),
-              ("solve_eo_nested_f32", dict(precond=wc.PRECOND_NONE, even_odd=True, max_iter=60))]
+              ("solve_eo_nested_f32", dict(precond=wc.PRECOND_NONE, even_odd=True, max_iter=60)),
+              ("solve_eo_nested_h16", dict(precond=wc.PRECOND_NONE, even_odd=True, krylov_prec=wc.F16,
+                                           max_iter=60))]
     if args.large_solve:
         solves.append(("solve_eo_reliable_f32", dict(precond=wc.PRECOND_NONE, even_odd=True, max_iter=args.large_solve,
                                                      solver=wc.SOLVER_RELIABLE, delta=0.01)))
@@ -597,7 +599,11 @@ def solve_comparison(wc, lat, src, args):
                      ("eo_nested_f32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED, inner_tol=0.01,
                                             inner_iters=100, even_odd=True)),
                      ("eo_reliable_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
-                                                  solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True))):
+                                                  solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True)),
+                     ("eo_reliable_h16", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE, delta=0.01,
+                                              krylov_prec=wc.F16, even_odd=True)),
+                     ("eo_nested_h16", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED, inner_tol=0.01,
+                                            inner_iters=100, krylov_prec=wc.F16, even_odd=True))):
         if args.solves and name not in args.solves.split(","):
             continue
         x = lat.field(wc.F64)

@@ -116,6 +116,11 @@ typedef struct {
     double delta;          /* RELIABLE refresh threshold, 0 < delta < 1 (0: 0.01) */
     double inner_tol;      /* NESTED inner relative tolerance, 0 < inner_tol < 1 (0: 0.01) */
     int inner_iters;       /* NESTED inner step limit, >= 0 (0: 100) */
+    wc_prec krylov_prec;   /* RELIABLE and NESTED: storage of the low-precision BiCGStab vectors and
+                              of their operator: WC_F16 (values + one FP32 scale per site, FP32
+                              arithmetic; RAS then also on FP16 storage) or WC_F32 (also for
+                              WC_F64, the zero value); the accumulated FP32 correction and
+                              every FP64 quantity are unaffected */
     int even_odd;          /* 1: solve the even-site Schur complement (see wc_apply_schur) and
                               reconstruct the odd sites; needs even extents; any solver kind;
                               with precond RAS the preconditioner is the full lattice's RAS on

@@ -51,7 +51,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("precond", ctypes.c_int), ("inner_prec", ctypes.c_int), ("ras", RasParams),
                 ("solver", ctypes.c_int), ("delta", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("inner_iters", ctypes.c_int), ("even_odd", ctypes.c_int)]
+                ("inner_iters", ctypes.c_int), ("krylov_prec", ctypes.c_int), ("even_odd", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -135,10 +135,10 @@ def ras_params(block=(4, 4, 4, 4), overlap=1, mr_iters=4) -> RasParams:
 
 def solve_params(tol=1e-10, max_iter=10000, max_restarts=5, precond=PRECOND_NONE, inner_prec=F32,
                  block=(4, 4, 4, 4), overlap=1, mr_iters=4, solver=SOLVER_FLEXIBLE, delta=0.01, inner_tol=0.01,
-                 inner_iters=100, even_odd=False) -> SolveParams:
+                 inner_iters=100, krylov_prec=F32, even_odd=False) -> SolveParams:
     return SolveParams(float(tol), int(max_iter), int(max_restarts), int(precond), int(inner_prec),
                        ras_params(block, overlap, mr_iters), int(solver), float(delta), float(inner_tol),
-                       int(inner_iters), int(bool(even_odd)))
+                       int(inner_iters), int(krylov_prec), int(bool(even_odd)))
 
 
 class Field:

@@ -507,8 +507,7 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
             continue;
         }
         if (reliable)
-            st = check_cuda(lats[i], hp_add_lo(lats[i], S, static_cast<double2 *>(xs[i]->data),
-                                               static_cast<float4 *>(R.LW[i].xlo->data)), "hp_add_lo");
+            st = check_cuda(lats[i], hp_add_lo(lats[i], S, static_cast<double2 *>(xs[i]->data), R.LW[i].xlo), "hp_add_lo");
         if (st == WC_OK) st = enqueue_true_residual(lats[i], S, 0, xs[i], bs[i], R.W[i]);
         if (st == WC_OK)
             st = check_cuda(lats[i], cudaMemcpyAsync(S.scal_host, S.scal, sizeof(SolverScalars),

@@ -498,6 +498,80 @@ __device__ __forceinline__ cx<double> cdiv2(cx<double> a, cx<double> b)
     return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
 }
 
+// Scalar updates of the low-precision BiCGStab, run by one thread of the
+// last block once the grid sums res[] are final (shared by the FP32 and the
+// FP16-storage kernels).
+__device__ void lo_init_update(const double *res, SolverScalars *sc)
+{
+    const double rr = res[0];
+    sc->rr = rr;
+    sc->rho = make_double2(rr, 0.0);
+    sc->rho0 = make_double2(1.0, 0.0);
+    sc->alpha = make_double2(1.0, 0.0);
+    sc->omega = make_double2(1.0, 0.0);
+    sc->beta = make_double2(rr, 0.0);
+    sc->flags = isfinite(rr) ? 0 : FLAG_NAN;
+    if (rr == 0.0) sc->flags |= FLAG_BREAKDOWN;
+}
+
+// alpha = rho / <rhat, v>
+__device__ void lo_alpha_update(const double *res, SolverScalars *sc)
+{
+    const cx<double> rv = mkc(res[0], res[1]);
+    if (!isfinite(rv.re) || !isfinite(rv.im)) sc->flags |= FLAG_NAN;
+    if (rv.re == 0.0 && rv.im == 0.0) {
+        sc->flags |= FLAG_BREAKDOWN;
+        sc->alpha = make_double2(0.0, 0.0);
+    } else {
+        sc->alpha = d2_of2(cdiv2(c_of2(sc->rho), rv));
+    }
+}
+
+// omega from <t, s>, <t, t>, <s, s>
+__device__ void lo_omega_update(const double *res, SolverScalars *sc)
+{
+    const double tr = res[0], ti = res[1], tt = res[2], ss = res[3];
+    sc->tt = tt;
+    if (!isfinite(tt) || !isfinite(tr) || !isfinite(ti) || !isfinite(ss)) sc->flags |= FLAG_NAN;
+    double2 om = tt > 0.0 ? make_double2(tr / tt, ti / tt) : make_double2(0.0, 0.0);
+    // omega stabilisation (Sleijpen & van der Vorst): when t and s are
+    // nearly orthogonal, |<t,s>| / (|t||s|) < 0.7, the minimising omega is
+    // tiny and BiCGStab loses accuracy in finite precision; enlarge it
+    const double rho_t = (tt > 0.0 && ss > 0.0) ? sqrt(tr * tr + ti * ti) / sqrt(tt * ss) : 1.0;
+    if (rho_t > 0.0 && rho_t < 0.7) {
+        const double f = 0.7 / rho_t;
+        om.x *= f;
+        om.y *= f;
+    }
+    sc->omega = om;
+}
+
+// rho' = <rhat, r>, rr = |r|^2, beta
+__device__ void lo_xr_update(const double *res, SolverScalars *sc)
+{
+    const cx<double> rho_new = mkc(res[0], res[1]);
+    const cx<double> rho = c_of2(sc->rho), om = c_of2(sc->omega), al = c_of2(sc->alpha);
+    sc->rr = res[2];
+    if (!isfinite(sc->rr) || !isfinite(rho_new.re) || !isfinite(rho_new.im)) sc->flags |= FLAG_NAN;
+    if ((om.re == 0.0 && om.im == 0.0) || (rho.re == 0.0 && rho.im == 0.0))
+        sc->flags |= FLAG_BREAKDOWN;
+    else
+        sc->beta = d2_of2(cdiv2(rho_new, rho) * cdiv2(al, om));
+    if (rho_new.re == 0.0 && rho_new.im == 0.0 && sc->rr > 0.0) sc->flags |= FLAG_BREAKDOWN;
+    sc->rho0 = sc->rho;
+    sc->rho = d2_of2(rho_new);
+}
+
+// after r was replaced: rho = <rhat, r>, beta from rho0 (rr untouched)
+__device__ void lo_rho_update(const double *res, SolverScalars *sc)
+{
+    const cx<double> rho_new = mkc(res[0], res[1]);
+    const cx<double> rho0 = c_of2(sc->rho0), om = c_of2(sc->omega), al = c_of2(sc->alpha);
+    if ((om.re != 0.0 || om.im != 0.0) && (rho0.re != 0.0 || rho0.im != 0.0))
+        sc->beta = d2_of2(cdiv2(rho_new, rho0) * cdiv2(al, om));
+    sc->rho = d2_of2(rho_new);
+}
+
 // rhat = r, p = v = 0, xlo = 0; rr = |r|^2, rho = rr, alpha = omega = rho0 = 1
 __global__ void __launch_bounds__(kRedBlock) k_lo_init(long long n, const float4 *r, float4 *rhat, float4 *p,
                                                        float4 *v, float4 *xlo, ReduceScratch rs, SolverScalars *sc)
@@ -512,17 +586,7 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_init(long long n, const float4
         xlo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         acc[0] = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, fmaf(ri.z, ri.z, fmaf(ri.w, ri.w, acc[0]))));
     }
-    if (grid_reduce_f<1>(acc, rs, rs.result)) {
-        const double rr = rs.result[0];
-        sc->rr = rr;
-        sc->rho = make_double2(rr, 0.0);
-        sc->rho0 = make_double2(1.0, 0.0);
-        sc->alpha = make_double2(1.0, 0.0);
-        sc->omega = make_double2(1.0, 0.0);
-        sc->beta = make_double2(rr, 0.0);
-        sc->flags = isfinite(rr) ? 0 : FLAG_NAN;
-        if (rr == 0.0) sc->flags |= FLAG_BREAKDOWN;
-    }
+    if (grid_reduce_f<1>(acc, rs, rs.result)) lo_init_update(rs.result, sc);
 }
 
 // p = r + beta (p - omega v)
@@ -554,16 +618,7 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_alpha(long long n, const float
         acc[0] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc[0]))));
         acc[1] = fmaf(a.x, b.y, fmaf(-a.y, b.x, fmaf(a.z, b.w, fmaf(-a.w, b.z, acc[1]))));
     }
-    if (grid_reduce_f<2>(acc, rs, rs.result)) {
-        const cx<double> rv = mkc(rs.result[0], rs.result[1]);
-        if (!isfinite(rv.re) || !isfinite(rv.im)) sc->flags |= FLAG_NAN;
-        if (rv.re == 0.0 && rv.im == 0.0) {
-            sc->flags |= FLAG_BREAKDOWN;
-            sc->alpha = make_double2(0.0, 0.0);
-        } else {
-            sc->alpha = d2_of2(cdiv2(c_of2(sc->rho), rv));
-        }
-    }
+    if (grid_reduce_f<2>(acc, rs, rs.result)) lo_alpha_update(rs.result, sc);
 }
 
 // s = r - alpha v
@@ -593,22 +648,7 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_omega(long long n, const float
         acc[2] = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, acc[2]))));
         acc[3] = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, acc[3]))));
     }
-    if (grid_reduce_f<4>(acc, rs, rs.result)) {
-        const double tr = rs.result[0], ti = rs.result[1], tt = rs.result[2], ss = rs.result[3];
-        sc->tt = tt;
-        if (!isfinite(tt) || !isfinite(tr) || !isfinite(ti) || !isfinite(ss)) sc->flags |= FLAG_NAN;
-        double2 om = tt > 0.0 ? make_double2(tr / tt, ti / tt) : make_double2(0.0, 0.0);
-        // omega stabilisation (Sleijpen & van der Vorst): when t and s are
-        // nearly orthogonal, |<t,s>| / (|t||s|) < 0.7, the minimising omega is
-        // tiny and BiCGStab loses accuracy in finite precision; enlarge it
-        const double rho_t = (tt > 0.0 && ss > 0.0) ? sqrt(tr * tr + ti * ti) / sqrt(tt * ss) : 1.0;
-        if (rho_t > 0.0 && rho_t < 0.7) {
-            const double f = 0.7 / rho_t;
-            om.x *= f;
-            om.y *= f;
-        }
-        sc->omega = om;
-    }
+    if (grid_reduce_f<4>(acc, rs, rs.result)) lo_omega_update(rs.result, sc);
 }
 
 // xlo += alpha phat + omega shat; r = s - omega t; rho' = <rhat, r>, rr = |r|^2
@@ -638,19 +678,7 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_xr(long long n, float4 *xlo, c
         acc[1] += h0.re * r0.im - h0.im * r0.re + h1.re * r1.im - h1.im * r1.re;
         acc[2] += r0.re * r0.re + r0.im * r0.im + r1.re * r1.re + r1.im * r1.im;
     }
-    if (grid_reduce_f<3>(acc, rs, rs.result)) {
-        const cx<double> rho_new = mkc(rs.result[0], rs.result[1]);
-        const cx<double> rho = c_of2(sc->rho), om = c_of2(sc->omega), al = c_of2(sc->alpha);
-        sc->rr = rs.result[2];
-        if (!isfinite(sc->rr) || !isfinite(rho_new.re) || !isfinite(rho_new.im)) sc->flags |= FLAG_NAN;
-        if ((om.re == 0.0 && om.im == 0.0) || (rho.re == 0.0 && rho.im == 0.0))
-            sc->flags |= FLAG_BREAKDOWN;
-        else
-            sc->beta = d2_of2(cdiv2(rho_new, rho) * cdiv2(al, om));
-        if (rho_new.re == 0.0 && rho_new.im == 0.0 && sc->rr > 0.0) sc->flags |= FLAG_BREAKDOWN;
-        sc->rho0 = sc->rho;
-        sc->rho = d2_of2(rho_new);
-    }
+    if (grid_reduce_f<3>(acc, rs, rs.result)) lo_xr_update(rs.result, sc);
 }
 
 // r was replaced by the true residual: rho = <rhat, r>,
@@ -666,13 +694,152 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_rho(long long n, const float4 
         acc[0] = fmaf(h.x, a.x, fmaf(h.y, a.y, fmaf(h.z, a.z, fmaf(h.w, a.w, acc[0]))));
         acc[1] = fmaf(h.x, a.y, fmaf(-h.y, a.x, fmaf(h.z, a.w, fmaf(-h.w, a.z, acc[1]))));
     }
-    if (grid_reduce_f<2>(acc, rs, rs.result)) {
-        const cx<double> rho_new = mkc(rs.result[0], rs.result[1]);
-        const cx<double> rho0 = c_of2(sc->rho0), om = c_of2(sc->omega), al = c_of2(sc->alpha);
-        if ((om.re != 0.0 || om.im != 0.0) && (rho0.re != 0.0 || rho0.im != 0.0))
-            sc->beta = d2_of2(cdiv2(rho_new, rho0) * cdiv2(al, om));
-        sc->rho = d2_of2(rho_new);
+    if (grid_reduce_f<2>(acc, rs, rs.result)) lo_rho_update(rs.result, sc);
+}
+
+// ------------------------------------------------------------------------
+// The same updates with FP16 storage (per-site scale) of the BiCGStab
+// vectors: one site per thread, FP32 arithmetic, FP32 partial sums; the
+// accumulated correction xlo stays FP32.  The scalar updates are shared.
+// ------------------------------------------------------------------------
+
+struct HF {   // FP16 field: values and per-site scales
+    void *d;
+    float *n;
+};
+
+__device__ __forceinline__ void hld(const HF &f, int V, int x, cx<float> s[12]) { P16::load_spinor(f.d, f.n, V, x, s); }
+__device__ __forceinline__ void hst(const HF &f, int V, int x, const cx<float> s[12])
+{
+    P16::store_spinor(f.d, f.n, V, x, s);
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_lo_init_h(int V, HF r, HF rhat, HF p, HF v, float4 *xlo,
+                                                         ReduceScratch rs, SolverScalars *sc)
+{
+    float acc[1] = {0.f};
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        cx<float> a[12], z[12];
+        hld(r, V, x, a);
+        hst(rhat, V, x, a);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            z[k] = mkc(0.f, 0.f);
+            acc[0] = fmaf(a[k].re, a[k].re, fmaf(a[k].im, a[k].im, acc[0]));
+        }
+        hst(p, V, x, z);
+        hst(v, V, x, z);
+        P32::store_spinor(xlo, nullptr, V, x, z);
     }
+    if (grid_reduce_f<1>(acc, rs, rs.result)) lo_init_update(rs.result, sc);
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_lo_p_h(int V, HF r, HF v, HF p, const SolverScalars *sc)
+{
+    const cx<float> beta = mkc((float)sc->beta.x, (float)sc->beta.y);
+    const cx<float> omega = mkc((float)sc->omega.x, (float)sc->omega.y);
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        cx<float> a[12], b[12], c[12];
+        hld(r, V, x, a);
+        hld(v, V, x, b);
+        hld(p, V, x, c);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) c[k] = a[k] + beta * (c[k] - omega * b[k]);
+        hst(p, V, x, c);
+    }
+}
+
+// acc[0] + i acc[1] += <a, b> over 12 components
+__device__ __forceinline__ void cdot_acc(const cx<float> a[12], const cx<float> b[12], float acc[2])
+{
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        acc[0] = fmaf(a[k].re, b[k].re, fmaf(a[k].im, b[k].im, acc[0]));
+        acc[1] = fmaf(a[k].re, b[k].im, fmaf(-a[k].im, b[k].re, acc[1]));
+    }
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_lo_alpha_h(int V, HF rhat, HF v, ReduceScratch rs,
+                                                          SolverScalars *sc)
+{
+    float acc[2] = {0.f, 0.f};
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        cx<float> a[12], b[12];
+        hld(rhat, V, x, a);
+        hld(v, V, x, b);
+        cdot_acc(a, b, acc);
+    }
+    if (grid_reduce_f<2>(acc, rs, rs.result)) lo_alpha_update(rs.result, sc);
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_lo_s_h(int V, HF r, HF v, HF s, const SolverScalars *sc)
+{
+    const cx<float> alpha = mkc((float)sc->alpha.x, (float)sc->alpha.y);
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        cx<float> a[12], b[12];
+        hld(r, V, x, a);
+        hld(v, V, x, b);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) a[k] = a[k] - alpha * b[k];
+        hst(s, V, x, a);
+    }
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_lo_omega_h(int V, HF t, HF s, ReduceScratch rs, SolverScalars *sc)
+{
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        cx<float> a[12], b[12];
+        hld(t, V, x, a);
+        hld(s, V, x, b);
+        cdot_acc(a, b, acc);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            acc[2] = fmaf(a[k].re, a[k].re, fmaf(a[k].im, a[k].im, acc[2]));
+            acc[3] = fmaf(b[k].re, b[k].re, fmaf(b[k].im, b[k].im, acc[3]));
+        }
+    }
+    if (grid_reduce_f<4>(acc, rs, rs.result)) lo_omega_update(rs.result, sc);
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_lo_xr_h(int V, float4 *xlo, HF phat, HF shat, HF s, HF t, HF r,
+                                                       HF rhat, ReduceScratch rs, SolverScalars *sc)
+{
+    const cx<float> alpha = mkc((float)sc->alpha.x, (float)sc->alpha.y);
+    const cx<float> omega = mkc((float)sc->omega.x, (float)sc->omega.y);
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        cx<float> xs[12], a[12], b[12];
+        P32::load_spinor(xlo, nullptr, V, x, xs);
+        hld(phat, V, x, a);
+        hld(shat, V, x, b);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) xs[k] = cfma(omega, b[k], cfma(alpha, a[k], xs[k]));
+        P32::store_spinor(xlo, nullptr, V, x, xs);
+        hld(s, V, x, a);
+        hld(t, V, x, b);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            a[k] = a[k] - omega * b[k];
+            acc[2] = fmaf(a[k].re, a[k].re, fmaf(a[k].im, a[k].im, acc[2]));
+        }
+        hst(r, V, x, a);
+        hld(rhat, V, x, b);
+        cdot_acc(b, a, acc);
+    }
+    if (grid_reduce_f<3>(acc, rs, rs.result)) lo_xr_update(rs.result, sc);
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_lo_rho_h(int V, HF rhat, HF r, ReduceScratch rs, SolverScalars *sc)
+{
+    float acc[2] = {0.f, 0.f};
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        cx<float> a[12], b[12];
+        hld(rhat, V, x, a);
+        hld(r, V, x, b);
+        cdot_acc(a, b, acc);
+    }
+    if (grid_reduce_f<2>(acc, rs, rs.result)) lo_rho_update(rs.result, sc);
 }
 
 // x (FP64) += xlo (FP32); xlo = 0.  FP32 plane j holds components 2j and
@@ -740,52 +907,89 @@ cudaError_t residual(wc_lattice lat, SolverState &S, const double2 *b, double2 *
     k_residual<<<WC_GRID(n)>>>(n, b, r, S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t lo_init(wc_lattice lat, SolverState &S, const float4 *r, float4 *rhat, float4 *p, float4 *v,
-                    float4 *xlo)
+namespace {
+float4 *f4(wc_field f) { return static_cast<float4 *>(f->data); }
+HF hf(wc_field f) { return HF{f->data, f->nrm}; }
+bool half_vectors(wc_field f) { return f->prec == WC_F16; }
+}  // namespace
+
+#define WC_GRID_SITES(V) reduce_grid(S.red, (V)), kRedBlock, 0, S.stream
+
+cudaError_t lo_init(wc_lattice lat, SolverState &S, wc_field r, wc_field rhat, wc_field p, wc_field v, wc_field xlo)
 {
-    const long long n = 6LL * lat->g.V;
-    k_lo_init<<<WC_GRID(n)>>>(n, r, rhat, p, v, xlo, S.red, S.scal);
+    const int V = lat->g.V;
+    const long long n = 6LL * V;
+    if (half_vectors(r))
+        k_lo_init_h<<<WC_GRID_SITES(V)>>>(V, hf(r), hf(rhat), hf(p), hf(v), f4(xlo), S.red, S.scal);
+    else
+        k_lo_init<<<WC_GRID(n)>>>(n, f4(r), f4(rhat), f4(p), f4(v), f4(xlo), S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t lo_p(wc_lattice lat, SolverState &S, const float4 *r, const float4 *v, float4 *p)
+cudaError_t lo_p(wc_lattice lat, SolverState &S, wc_field r, wc_field v, wc_field p)
 {
-    const long long n = 6LL * lat->g.V;
-    k_lo_p<<<WC_GRID(n)>>>(n, r, v, p, S.scal);
+    const int V = lat->g.V;
+    const long long n = 6LL * V;
+    if (half_vectors(r))
+        k_lo_p_h<<<WC_GRID_SITES(V)>>>(V, hf(r), hf(v), hf(p), S.scal);
+    else
+        k_lo_p<<<WC_GRID(n)>>>(n, f4(r), f4(v), f4(p), S.scal);
     return cudaGetLastError();
 }
-cudaError_t lo_alpha(wc_lattice lat, SolverState &S, const float4 *rhat, const float4 *v)
+cudaError_t lo_alpha(wc_lattice lat, SolverState &S, wc_field rhat, wc_field v)
 {
-    const long long n = 6LL * lat->g.V;
-    k_lo_alpha<<<WC_GRID(n)>>>(n, rhat, v, S.red, S.scal);
+    const int V = lat->g.V;
+    const long long n = 6LL * V;
+    if (half_vectors(v))
+        k_lo_alpha_h<<<WC_GRID_SITES(V)>>>(V, hf(rhat), hf(v), S.red, S.scal);
+    else
+        k_lo_alpha<<<WC_GRID(n)>>>(n, f4(rhat), f4(v), S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t lo_s(wc_lattice lat, SolverState &S, const float4 *r, const float4 *v, float4 *s)
+cudaError_t lo_s(wc_lattice lat, SolverState &S, wc_field r, wc_field v, wc_field s)
 {
-    const long long n = 6LL * lat->g.V;
-    k_lo_s<<<WC_GRID(n)>>>(n, r, v, s, S.scal);
+    const int V = lat->g.V;
+    const long long n = 6LL * V;
+    if (half_vectors(r))
+        k_lo_s_h<<<WC_GRID_SITES(V)>>>(V, hf(r), hf(v), hf(s), S.scal);
+    else
+        k_lo_s<<<WC_GRID(n)>>>(n, f4(r), f4(v), f4(s), S.scal);
     return cudaGetLastError();
 }
-cudaError_t lo_omega(wc_lattice lat, SolverState &S, const float4 *t, const float4 *s)
+cudaError_t lo_omega(wc_lattice lat, SolverState &S, wc_field t, wc_field s)
 {
-    const long long n = 6LL * lat->g.V;
-    k_lo_omega<<<WC_GRID(n)>>>(n, t, s, S.red, S.scal);
+    const int V = lat->g.V;
+    const long long n = 6LL * V;
+    if (half_vectors(t))
+        k_lo_omega_h<<<WC_GRID_SITES(V)>>>(V, hf(t), hf(s), S.red, S.scal);
+    else
+        k_lo_omega<<<WC_GRID(n)>>>(n, f4(t), f4(s), S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t lo_xr(wc_lattice lat, SolverState &S, float4 *xlo, const float4 *phat, const float4 *shat,
-                  const float4 *s, const float4 *t, float4 *r, const float4 *rhat)
+cudaError_t lo_xr(wc_lattice lat, SolverState &S, wc_field xlo, wc_field phat, wc_field shat, wc_field s,
+                  wc_field t, wc_field r, wc_field rhat)
 {
-    const long long n = 6LL * lat->g.V;
-    k_lo_xr<<<WC_GRID(n)>>>(n, xlo, phat, shat, s, t, r, rhat, S.red, S.scal);
+    const int V = lat->g.V;
+    const long long n = 6LL * V;
+    if (half_vectors(r))
+        k_lo_xr_h<<<WC_GRID_SITES(V)>>>(V, f4(xlo), hf(phat), hf(shat), hf(s), hf(t), hf(r), hf(rhat), S.red,
+                                         S.scal);
+    else
+        k_lo_xr<<<WC_GRID(n)>>>(n, f4(xlo), f4(phat), f4(shat), f4(s), f4(t), f4(r), f4(rhat), S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t lo_rho(wc_lattice lat, SolverState &S, const float4 *rhat, const float4 *r)
+cudaError_t lo_rho(wc_lattice lat, SolverState &S, wc_field rhat, wc_field r)
 {
-    const long long n = 6LL * lat->g.V;
-    k_lo_rho<<<WC_GRID(n)>>>(n, rhat, r, S.red, S.scal);
+    const int V = lat->g.V;
+    const long long n = 6LL * V;
+    if (half_vectors(r))
+        k_lo_rho_h<<<WC_GRID_SITES(V)>>>(V, hf(rhat), hf(r), S.red, S.scal);
+    else
+        k_lo_rho<<<WC_GRID(n)>>>(n, f4(rhat), f4(r), S.red, S.scal);
     return cudaGetLastError();
 }
-cudaError_t hp_add_lo(wc_lattice lat, SolverState &S, double2 *x, float4 *xlo)
+cudaError_t hp_add_lo(wc_lattice lat, SolverState &S, double2 *x, wc_field xlo_f)
 {
+    float4 *xlo = f4(xlo_f);
     const long long n = 6LL * lat->g.V;
     k_hp_add_lo<<<WC_GRID(n)>>>(n, lat->g.V, x, xlo);
     return cudaGetLastError();

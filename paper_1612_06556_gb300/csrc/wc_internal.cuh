@@ -38,17 +38,19 @@ namespace wc {
 // FP32, 22-23 FP16, 24 + precision: the odd-site intermediate of the
 // even-odd operator on a half lattice, 27-31: the half-lattice FP64 fields
 // b_e, b_o, x_e, x_o, b^_e of an even-odd solve, 32-35: full-lattice FP32
-// and FP16 in/out fields of the RAS preconditioner of an even-odd solve)
-// and the stream the solve is queued on.  A lattice owns one for its
-// single-RHS calls; a batched solve creates one per RHS.
+// and FP16 in/out fields of the RAS preconditioner of an even-odd solve,
+// 36-43: the low-precision BiCGStab vectors when they are FP16) and the
+// stream the solve is queued on.  A lattice owns one for its single-RHS
+// calls; a batched solve creates one per RHS.
 constexpr int kSchurSlot = 24;
 constexpr int kEoSlot = 27;
 constexpr int kRasEoSlot = 32;
+constexpr int kHalfKrylovSlot = 36;
 struct SolverState {
     SolverScalars *scal = nullptr;
     SolverScalars *scal_host = nullptr;
     ReduceScratch red;
-    wc_field_s *work[36] = {};
+    wc_field_s *work[44] = {};
     cudaStream_t stream = nullptr;
     SolverState *inner = nullptr;   // state of a nested inner solve, created on first use
 };

@@ -387,25 +387,31 @@ static wc_status bicgstab_impl(wc_lattice lat, SolverState &S, int kind, wc_fiel
 
 namespace {
 
-float4 *f4(wc_field f) { return static_cast<float4 *>(f->data); }
 
 }  // namespace
 
 wc_status lo_vectors(wc_lattice lat, SolverState &S, const wc_solve_params &p, LoVecs *w)
 {
     wc_status st = WC_OK;
-    wc_field *slots[9] = {&w->r, &w->rhat, &w->p, &w->v, &w->s, &w->t, &w->phat, &w->shat, &w->xlo};
-    for (int i = 0; i < 9 && st == WC_OK; ++i) *slots[i] = state_work(lat, S, 12 + i, WC_F32, &st);
+    // the eight BiCGStab vectors in FP32 (slots 12-19) or FP16 (36-43); the
+    // correction xlo is always FP32 (slot 20)
+    const bool half = p.krylov_prec == WC_F16;
+    wc_field *slots[8] = {&w->r, &w->rhat, &w->p, &w->v, &w->s, &w->t, &w->phat, &w->shat};
+    for (int i = 0; i < 8 && st == WC_OK; ++i)
+        *slots[i] = half ? state_work(lat, S, kHalfKrylovSlot + i, WC_F16, &st) : state_work(lat, S, 12 + i, WC_F32, &st);
+    if (st == WC_OK) w->xlo = state_work(lat, S, 20, WC_F32, &st);
     if (p.precond == WC_PRECOND_NONE) {   // no preconditioner: phat, shat are p, s
         w->phat = w->p;
         w->shat = w->s;
     }
     w->lo_in = w->lo_out = nullptr;
-    if (st == WC_OK && lat->schur_parent) state_work(lat, S, kSchurSlot + WC_F32, WC_F32, &st);
+    const wc_prec kp = half ? WC_F16 : WC_F32;
+    if (st == WC_OK && lat->schur_parent) state_work(lat, S, kSchurSlot + kp, kp, &st);
     if (st == WC_OK && lat->schur_parent) state_work(lat, S, kSchurSlot + WC_F64, WC_F64, &st);
-    if (st == WC_OK && p.precond == WC_PRECOND_RAS)
-        st = eo_ras_temps(lat, S, p.inner_prec == WC_F16 ? WC_F16 : WC_F32);
-    if (st == WC_OK && p.precond == WC_PRECOND_RAS && p.inner_prec == WC_F16) {
+    // RAS on FP16 storage when either the vectors or inner_prec are FP16
+    const bool ras16 = half || p.inner_prec == WC_F16;
+    if (st == WC_OK && p.precond == WC_PRECOND_RAS) st = eo_ras_temps(lat, S, ras16 ? WC_F16 : WC_F32);
+    if (st == WC_OK && p.precond == WC_PRECOND_RAS && ras16 && !half) {
         w->lo_in = state_work(lat, S, 22, WC_F16, &st);
         if (st == WC_OK) w->lo_out = state_work(lat, S, 23, WC_F16, &st);
     }
@@ -420,7 +426,7 @@ wc_status lo_precond(wc_lattice lat, SolverState &S, const wc_solve_params &p, i
                      wc_field u, wc_field uhat)
 {
     if (p.precond == WC_PRECOND_NONE) return WC_OK;
-    if (p.inner_prec != WC_F16) return ras_apply(lat, S, uhat, u, p.ras, kind);
+    if (u->prec == WC_F16 || p.inner_prec != WC_F16) return ras_apply(lat, S, uhat, u, p.ras, kind);
     wc_status st = check_cuda(lat, launch_copy(lat, w.lo_in, u, 1.0, nullptr, 0, S.stream), "cast to FP16");
     if (st == WC_OK) st = ras_apply(lat, S, w.lo_out, w.lo_in, p.ras, kind);
     if (st == WC_OK) st = check_cuda(lat, launch_copy(lat, uhat, w.lo_out, 1.0, nullptr, 0, S.stream), "cast");
@@ -432,16 +438,16 @@ wc_status lo_precond(wc_lattice lat, SolverState &S, const wc_solve_params &p, i
 wc_status enqueue_lo_iteration(wc_lattice lat, SolverState &S, const wc_solve_params &p, int kind,
                                const LoVecs &w)
 {
-    wc_status st = check_cuda(lat, lo_p(lat, S, f4(w.r), f4(w.v), f4(w.p)), "lo_p");
+    wc_status st = check_cuda(lat, lo_p(lat, S, w.r, w.v, w.p), "lo_p");
     if (st == WC_OK) st = lo_precond(lat, S, p, kind, w, w.p, w.phat);
     if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.v, w.phat, kind, S), "apply");
-    if (st == WC_OK) st = check_cuda(lat, lo_alpha(lat, S, f4(w.rhat), f4(w.v)), "lo_alpha");
-    if (st == WC_OK) st = check_cuda(lat, lo_s(lat, S, f4(w.r), f4(w.v), f4(w.s)), "lo_s");
+    if (st == WC_OK) st = check_cuda(lat, lo_alpha(lat, S, w.rhat, w.v), "lo_alpha");
+    if (st == WC_OK) st = check_cuda(lat, lo_s(lat, S, w.r, w.v, w.s), "lo_s");
     if (st == WC_OK) st = lo_precond(lat, S, p, kind, w, w.s, w.shat);
     if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, w.t, w.shat, kind, S), "apply");
-    if (st == WC_OK) st = check_cuda(lat, lo_omega(lat, S, f4(w.t), f4(w.s)), "lo_omega");
+    if (st == WC_OK) st = check_cuda(lat, lo_omega(lat, S, w.t, w.s), "lo_omega");
     if (st == WC_OK)
-        st = check_cuda(lat, lo_xr(lat, S, f4(w.xlo), f4(w.phat), f4(w.shat), f4(w.s), f4(w.t), f4(w.r), f4(w.rhat)),
+        st = check_cuda(lat, lo_xr(lat, S, w.xlo, w.phat, w.shat, w.s, w.t, w.r, w.rhat),
                         "lo_xr");
     return st;
 }
@@ -458,7 +464,7 @@ wc_status enqueue_lo_start(wc_lattice lat, SolverState &S, int kind, wc_field x,
                                       static_cast<double2 *>(r_hp->data)), "residual");
     if (st == WC_OK) st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
     if (st == WC_OK)
-        st = check_cuda(lat, lo_init(lat, S, f4(w.r), f4(w.rhat), f4(w.p), f4(w.v), f4(w.xlo)), "lo_init");
+        st = check_cuda(lat, lo_init(lat, S, w.r, w.rhat, w.p, w.v, w.xlo), "lo_init");
     return st;
 }
 
@@ -466,7 +472,7 @@ wc_status enqueue_lo_start(wc_lattice lat, SolverState &S, int kind, wc_field x,
 static wc_status enqueue_refresh(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
                                  const LoVecs &w)
 {
-    wc_status st = check_cuda(lat, hp_add_lo(lat, S, static_cast<double2 *>(x->data), f4(w.xlo)), "hp_add_lo");
+    wc_status st = check_cuda(lat, hp_add_lo(lat, S, static_cast<double2 *>(x->data), w.xlo), "hp_add_lo");
     if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S), "apply");
     if (st == WC_OK)
         st = check_cuda(lat, residual(lat, S, static_cast<const double2 *>(b->data), static_cast<double2 *>(r_hp->data)),
@@ -479,7 +485,7 @@ wc_status enqueue_refresh_full(wc_lattice lat, SolverState &S, int kind, wc_fiel
 {
     wc_status st = enqueue_refresh(lat, S, kind, x, b, r_hp, w);
     if (st == WC_OK) st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
-    if (st == WC_OK) st = check_cuda(lat, lo_rho(lat, S, f4(w.rhat), f4(w.r)), "lo_rho");
+    if (st == WC_OK) st = check_cuda(lat, lo_rho(lat, S, w.rhat, w.r), "lo_rho");
     return st;
 }
 
@@ -511,7 +517,7 @@ static wc_status nested_inner(wc_lattice lat, SolverState &S, const wc_solve_par
     const int iters = p.inner_iters > 0 ? p.inner_iters : 100;
     st = check_cuda(lat, launch_copy(lat, w.r, u, 1.0, norm2_dev, 1, I.stream), "cast to unit norm");
     if (st == WC_OK)
-        st = check_cuda(lat, lo_init(lat, I, f4(w.r), f4(w.rhat), f4(w.p), f4(w.v), f4(w.xlo)), "lo_init");
+        st = check_cuda(lat, lo_init(lat, I, w.r, w.rhat, w.p, w.v, w.xlo), "lo_init");
     if (st == WC_OK) st = read_scalars(lat, I);
     if (st != WC_OK) return st;
     const double rr0 = I.scal_host->rr;
@@ -593,7 +599,7 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
         }
         st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
         if (st == WC_OK)
-            st = check_cuda(lat, lo_init(lat, S, f4(w.r), f4(w.rhat), f4(w.p), f4(w.v), f4(w.xlo)), "lo_init");
+            st = check_cuda(lat, lo_init(lat, S, w.r, w.rhat, w.p, w.v, w.xlo), "lo_init");
         if (st != WC_OK) return st;
         double rmax2 = rr_true, rr_refresh = rr_true;
         bool breakdown = false, converged = false, diverged = false;
@@ -627,7 +633,7 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
                     break;
                 }
                 st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
-                if (st == WC_OK) st = check_cuda(lat, lo_rho(lat, S, f4(w.rhat), f4(w.r)), "lo_rho");
+                if (st == WC_OK) st = check_cuda(lat, lo_rho(lat, S, w.rhat, w.r), "lo_rho");
                 if (st != WC_OK) return st;
                 rmax2 = rr_true;
                 rr_refresh = rr_true;
@@ -683,6 +689,8 @@ wc_status check_solve_args(wc_lattice lat, wc_field x, wc_field b, const wc_solv
         return set_error(lat, WC_ERR_ARG, "unknown solver kind");
     if (p->solver == WC_SOLVER_NESTED && (!(p->inner_tol >= 0.0 && p->inner_tol < 1.0) || p->inner_iters < 0))
         return set_error(lat, WC_ERR_ARG, "inner_tol must be in [0, 1) and inner_iters >= 0");
+    if (p->krylov_prec != WC_F64 && p->krylov_prec != WC_F32 && p->krylov_prec != WC_F16)
+        return set_error(lat, WC_ERR_ARG, "krylov_prec must be WC_F32 or WC_F16 (WC_F64 means WC_F32)");
     if (p->solver == WC_SOLVER_RELIABLE && !(p->delta >= 0.0 && p->delta < 1.0))
         return set_error(lat, WC_ERR_ARG, "delta must be in [0, 1)");
     if (p->precond == WC_PRECOND_RAS) {

@@ -28,20 +28,22 @@ cudaError_t residual(wc_lattice lat, SolverState &S, const double2 *b, double2 *
 // S.red.result[0] = |a|^2
 cudaError_t norm2_to_result(wc_lattice lat, SolverState &S, const double2 *a);
 
-// FP32 counterparts for the reliable-update solver (FP32 fields)
+// Low-precision counterparts for the reliable-update and nested solvers:
+// the BiCGStab vectors are FP32 fields, or FP16 fields (per-site scale,
+// FP32 arithmetic); xlo, the accumulated correction, is always FP32.
 // rhat = r, p = v = xlo = 0; scalars reset from |r|^2
-cudaError_t lo_init(wc_lattice lat, SolverState &S, const float4 *r, float4 *rhat, float4 *p, float4 *v,
-                    float4 *xlo);
-cudaError_t lo_p(wc_lattice lat, SolverState &S, const float4 *r, const float4 *v, float4 *p);
-cudaError_t lo_alpha(wc_lattice lat, SolverState &S, const float4 *rhat, const float4 *v);
-cudaError_t lo_s(wc_lattice lat, SolverState &S, const float4 *r, const float4 *v, float4 *s);
-cudaError_t lo_omega(wc_lattice lat, SolverState &S, const float4 *t, const float4 *s);
+cudaError_t lo_init(wc_lattice lat, SolverState &S, wc_field r, wc_field rhat, wc_field p, wc_field v,
+                    wc_field xlo);
+cudaError_t lo_p(wc_lattice lat, SolverState &S, wc_field r, wc_field v, wc_field p);
+cudaError_t lo_alpha(wc_lattice lat, SolverState &S, wc_field rhat, wc_field v);
+cudaError_t lo_s(wc_lattice lat, SolverState &S, wc_field r, wc_field v, wc_field s);
+cudaError_t lo_omega(wc_lattice lat, SolverState &S, wc_field t, wc_field s);
 // xlo += alpha phat + omega shat; r = s - omega t; rho, beta, rr updated
-cudaError_t lo_xr(wc_lattice lat, SolverState &S, float4 *xlo, const float4 *phat, const float4 *shat,
-                  const float4 *s, const float4 *t, float4 *r, const float4 *rhat);
+cudaError_t lo_xr(wc_lattice lat, SolverState &S, wc_field xlo, wc_field phat, wc_field shat, wc_field s,
+                  wc_field t, wc_field r, wc_field rhat);
 // after r was replaced: rho = <rhat, r>, beta from rho0 (rr untouched)
-cudaError_t lo_rho(wc_lattice lat, SolverState &S, const float4 *rhat, const float4 *r);
+cudaError_t lo_rho(wc_lattice lat, SolverState &S, wc_field rhat, wc_field r);
 // x (FP64) += xlo (FP32); xlo = 0
-cudaError_t hp_add_lo(wc_lattice lat, SolverState &S, double2 *x, float4 *xlo);
+cudaError_t hp_add_lo(wc_lattice lat, SolverState &S, double2 *x, wc_field xlo);
 
 }  // namespace wc

@@ -222,3 +222,32 @@ def test_even_odd_with_ras(solver, inner):
         with pytest.raises(w.WCError):
             w.solve_batch([lat], [lat.field(0)], [b], tol=1e-10, even_odd=True, precond=w.PRECOND_RAS,
                           block=(0, 0, 0, 0))
+
+
+@pytest.mark.parametrize("solver,even_odd,precond", [(1, True, 0), (2, True, 0), (1, False, 1), (2, True, 1)])
+def test_fp16_krylov_vectors(solver, even_odd, precond):
+    """krylov_prec = FP16: the low-precision BiCGStab vectors and operator of
+    the reliable-update and nested solvers on FP16 storage (per-site scale,
+    FP32 arithmetic), with and without even-odd and RAS; the FP64 true
+    residual still reaches 1e-10, checked with the oracle's M; also inside
+    the batched graph."""
+    w = wc()
+    dims, kappa, csw, tbc = (8, 8, 8, 16), 0.124, 1.0, -1
+    U = synth.exp_links(dims, 0.3, 161)
+    src = synth.gaussian_source(dims, 162)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    x, b = lat.field(0), lat.field(0).load(src)
+    kw = dict(tol=1e-10, solver=solver, even_odd=even_odd, precond=precond, krylov_prec=w.F16, max_iter=3000,
+              block=(4, 4, 4, 4))
+    info = lat.solve(x, b, **kw)
+    assert info.status == 0 and info.true_rel_resid <= 1e-10
+    sol = x.store(np.zeros_like(src))
+    r = src - oracle.apply_M(dims, tbc, kappa, csw, U, sol)
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+    if solver == 1:
+        xs = [lat.field(0), lat.field(0)]
+        infos = w.solve_batch([lat, lat], xs, [b, b], **kw)
+        for i, xx in zip(infos, xs):
+            assert i.status == 0
+            r = src - oracle.apply_M(dims, tbc, kappa, csw, U, xx.store(np.zeros_like(src)))
+            assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
