@@ -384,6 +384,10 @@ def batch_comparison(wc, args):
                          delta=0.01, even_odd=True)
     run_batch(eo)                           # warm-up: clover inverses, half-lattice fields
     infos_eo, t_eo = run_batch(eo)
+    eo_h16 = wc.solve_params(tol=1e-10, max_iter=5000, precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE,
+                             delta=0.01, krylov_prec=wc.F16, even_odd=True)
+    run_batch(eo_h16)
+    infos_eo_h16, t_eo_h16 = run_batch(eo_h16)
     eo_ras = wc.solve_params(tol=1e-10, max_iter=5000, precond=wc.PRECOND_RAS, inner_prec=wc.F32,
                              block=(4, 4, 4, 4), solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True)
     run_batch(eo_ras)
@@ -415,6 +419,8 @@ def batch_comparison(wc, args):
             "flexible_steps": [min(i.iters for i in infos_flex), max(i.iters for i in infos_flex)],
             "even_odd_batch_seconds": t_eo, "even_odd_all_ok": all(i.status == 0 for i in infos_eo),
             "even_odd_sequential_seconds": t_seq_eo, "even_odd_sequential_all_ok": all(i.status == 0 for i in seq_eo),
+            "even_odd_fp16_vectors_batch_seconds": t_eo_h16,
+            "even_odd_fp16_vectors_all_ok": all(i.status == 0 for i in infos_eo_h16),
             "even_odd_ras_batch_seconds": t_eo_ras, "even_odd_ras_all_ok": all(i.status == 0 for i in infos_eo_ras),
             "even_odd_ras_steps": [min(i.iters for i in infos_eo_ras), max(i.iters for i in infos_eo_ras)],
             "even_odd_steps": [min(i.iters for i in infos_eo), max(i.iters for i in infos_eo)],
