@@ -56,9 +56,14 @@ __device__ void pack_block(cx<double> m[6][6], double r[36])
 }
 
 // Gauss-Jordan inverse with partial pivoting (6x6 complex, in place).
-// Returns false if a pivot vanishes.
+// Returns false if a pivot is below 1e-12 of the block's largest entry
+// (numerically singular: the inverse would carry no significant digit).
 __device__ bool invert6(cx<double> a[6][6])
 {
+    double amax = 0.0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) amax = fmax(amax, fabs(a[i][j].re) + fabs(a[i][j].im));
+    const double tiny2 = (1e-12 * amax) * (1e-12 * amax);
     cx<double> inv[6][6];
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j) inv[i][j] = mkc(i == j ? 1.0 : 0.0, 0.0);
@@ -72,7 +77,7 @@ __device__ bool invert6(cx<double> a[6][6])
                 piv = r;
             }
         }
-        if (!(best > 0.0)) return false;
+        if (!(best > tiny2) || !(best > 0.0)) return false;
         if (piv != c)
             for (int j = 0; j < 6; ++j) {
                 cx<double> t = a[c][j];

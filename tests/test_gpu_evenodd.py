@@ -252,3 +252,35 @@ def test_fp16_krylov_vectors(solver, even_odd, precond):
             assert i.status == 0
             r = src - oracle.apply_M(dims, tbc, kappa, csw, U, xx.store(np.zeros_like(src)))
             assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+
+
+def test_singular_clover_block_is_reported():
+    """A constant abelian flux b = pi/2 in the xy plane gives A = 1 + T with
+    T = csw kappa sin(b) diag(1,-1,1,-1) (x) diag(1,-1,0) at every site; with
+    csw kappa = 1 the blocks of A are singular, so the even-odd operator and
+    solves report WC_ERR_BREAKDOWN instead of dividing by (almost) zero,
+    while the full-lattice operator still applies."""
+    w = wc()
+    dims = (4, 4, 2, 2)
+    Lx, Ly = dims[0], dims[1]
+    b = 2 * np.pi * 4 / (Lx * Ly)
+    tau = np.array([1.0, -1.0, 0.0])
+    U = synth.unit_links(dims)
+    V = synth.volume(dims)
+    for s in range(V):
+        x, y = s % Lx, (s // Lx) % Ly
+        U[s, 1] = np.diag(np.exp(1j * b * x * tau))
+        if x == Lx - 1:
+            U[s, 0] = np.diag(np.exp(-1j * b * Lx * y * tau))
+    lat = make_lattice(dims, U, 8.0, 0.125, -1)
+    psi = synth.gaussian_source(dims, 3)
+    with pytest.raises(w.WCError) as e:
+        lat.apply_schur(lat.field(0), lat.field(0).load(psi))
+    assert e.value.status == 5
+    with pytest.raises(w.WCError) as e:
+        lat.solve(lat.field(0), lat.field(0).load(psi), tol=1e-10, even_odd=True)
+    assert e.value.status == 5
+    out = lat.field(0)
+    lat.apply_M(out, lat.field(0).load(psi))
+    ref = oracle.apply_M(dims, -1, 0.125, 8.0, U, psi)
+    assert_elementwise(out.store(np.zeros_like(psi)), ref, 1e-12)
