@@ -510,7 +510,9 @@ def copy_rate(total_bytes, stream, reps=200):
     and a 55 us launch pays its ramp-up and drain on every call."""
     import torch
     n = int(total_bytes // 8)   # float32 elements per buffer (half read, half written)
-    src = [torch.ones(n, device="cuda") for _ in range(4)]
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    # random contents: a constant buffer could be moved faster than real data
+    src = [torch.randn(n, device="cuda", generator=gen) for _ in range(4)]
     dst = [torch.empty(n, device="cuda") for _ in range(4)]
     for i in range(8):
         dst[i % 4].copy_(src[i % 4])
