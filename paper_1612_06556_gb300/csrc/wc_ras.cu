@@ -150,11 +150,8 @@ __device__ __forceinline__ void ras_hops(const Geom &g, const RasGeom &rg, const
     }
 }
 
-// 96 registers: 21 warps x 32 x 96 = 64,512 of the SM's 65,536 (one CTA
-// per SM is set by the shared memory anyway); the launch-bounds default
-// would stop at 80 and spill ~280 bytes per thread.
 template <class P, int SF>
-__global__ void __maxnreg__(96)
+__global__ void __launch_bounds__(kRasMaxThreads, 1)
     k_ras(Geom g, RasGeom rg, GaugeStore U, CloverStore C, const void *vin, const float *vin_nrm, void *zout,
           float *zout_nrm, float kappa)
 {
