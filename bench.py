@@ -286,6 +286,7 @@ def run_ours(args, world, rank, local):
     mdag_ms = time_applies(lat, outs, ins, "Mdag", 500, stream)
     copy_gbs = copy_rate(BYTES_PER_SITE["f32"] * V, stream)
     multi = multi_rhs_apply(wc, lat, dims, ms / args.steps, stream)
+    ras = ras_timing(wc, lat, dims, src, stream)
     large = large_lattice(wc, args) if not args.skip_large else None
     batch = batch_comparison(wc, args) if not args.skip_batch else None
     force = force_timing(wc, args) if not args.skip_force else None
@@ -334,6 +335,7 @@ def run_ours(args, world, rank, local):
     if force is not None:
         line["force"] = force
     line["apply_multi"] = multi
+    line["ras"] = ras
     if world == 1 and not args.skip_cpu:
         smp = OracleSampler(dims, U, src, csw, kappa, tbc, args.ref_seconds)
         g, dt = smp.step()
@@ -501,6 +503,61 @@ def multi_rhs_apply(wc, lat, dims, single_ms, stream, n=12, reps=100):
     return {"rhs": n, "ms_per_launch": ms, "gflops": FLOPS_PER_SITE * V * n / (ms * 1e-3) / 1e9,
             "bytes_per_site_per_rhs": bps, "algorithmic_gbs": gbs, "roofline_frac": gbs / peak,
             "speedup_vs_single_applies": n * single_ms / ms}
+
+
+def fp32_fma_peak():
+    """Measured FP32 FMA throughput (TFLOP/s): cuBLAS FP32 GEMM (TF32 off, so
+    it runs on the FMA pipe, not the tensor cores), 8192^3, best of 5 --
+    the denominator of the RAS block solver's effective rate."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        torch.mm(a, b)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.mm(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def ras_timing(wc, lat, dims, src, stream, reps=50):
+    """One RAS application (4^4 blocks, overlap 1, 4 MR steps) at 24^3x32 on
+    FP32 and FP16 storage: seconds per application and the effective rate
+    4 MR steps x 1296 extended sites x blocks x (1824 + 96) flop."""
+    import torch
+    V = int(np.prod(dims))
+    blocks = V // 256
+    flops = 4 * 1296 * blocks * (FLOPS_PER_SITE + 96)
+    peak = fp32_fma_peak()
+    out = {"blocks": blocks, "fp32_fma_peak_tflops_measured": peak}
+    for name, prec in (("f32", wc.F32), ("f16", wc.F16)):
+        a, z = lat.field(prec).load(src), lat.field(prec)
+        for _ in range(3):
+            lat.ras(z, a)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            lat.ras(z, a)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        tf = flops / (ms * 1e-3) / 1e12
+        out[name] = {"ms": ms, "effective_tflops": tf, "frac_of_fp32_fma_peak": tf / peak}
+        a.close()
+        z.close()
+    return out
 
 
 def copy_rate(total_bytes, stream, reps=200):
