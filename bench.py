@@ -667,6 +667,7 @@ def force_timing(wc, args):
     csw 1.0, exp(0.3 iH) links, Gaussian phi): two solves to 1e-12 (FP64
     flexible BiCGStab + FP32 RAS, or even-odd reliable update), then the
     force kernels."""
+    import torch
     import synth
     dims, U, phi, csw, kappa, tbc = synth.config_inputs(5)
     lat = wc.Lattice(dims, tbc).load_gauge(U).load_clover(csw, kappa)
@@ -680,7 +681,9 @@ def force_timing(wc, args):
              "even-odd FP32 BiCGStab with FP64 reliable updates")):
         lat.action_force(f_phi, F, **kw)
         t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("force_" + name)   # lets a profiler select the timed call
         S = lat.action_force(f_phi, F, **kw)
+        torch.cuda.nvtx.range_pop()
         dt = time.perf_counter() - t0
         out[name] = {"seconds": dt, "S": S, "solves": f"M^+ Y = phi then M X = Y, {what}, tol 1e-12"}
     return out
