@@ -3,13 +3,16 @@
  *
  * The library applies the Wilson-Clover quark matrix
  *     M = (1 + T) - kappa H
- * to colour-spinor fields on a 4-D lattice and solves M x = b with BiCGStab,
- * plain in FP64 or as an FP64 flexible (defect-correction) outer loop around
+ * to colour-spinor fields on a 4-D lattice and solves M x = b with BiCGStab:
+ * plain in FP64, as an FP64 flexible (defect-correction) outer loop around
  * an FP32/FP16-storage overlapped Restricted Additive Schwarz (RAS)
- * preconditioner whose blocks are solved inside CTAs.  This is the solver
- * stack of the paper's CCS-QCD benchmark (Sec. 2: double-precision flexible
- * BiCGStab, single-precision preconditioner, overlapped RAS, SU(3)
- * reconstruction; Sec. 3: the hopping multiplication "MULT").
+ * preconditioner whose blocks are solved inside CTAs, as FP32/FP16
+ * BiCGStab with FP64 reliable updates, or as the three-level nested solver,
+ * each on the full lattice or on its even-odd Schur complement.  This is the
+ * solver stack of the paper's CCS-QCD benchmark (Sec. 2: double-precision
+ * flexible BiCGStab, single-precision preconditioner, even-odd and
+ * overlapped RAS preconditioning, SU(3) reconstruction; Sec. 3: the hopping
+ * multiplication "MULT").
  *
  * Conventions (the paper names the operator but prints no formula; these
  * are this library's reading, identical to the test oracle's):
