@@ -66,3 +66,19 @@ def test_36_rhs_batch_on_three_lattices():
         sites = np.concatenate([[0], np.random.default_rng(k).choice(np.arange(1, V), 1999, replace=False)])
         r = src[sites] - oracle.apply_M(dims, cfg["tbc"], cfg["kappa"], cfg["csw"], U, sol, sites=sites)
         assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 2e-5), (2, 1e-2)])
+def test_ras_24x24x24x32_matches_oracle(prec, tol):
+    """The RAS application of the 24^3x32 solve workload (4^4 blocks,
+    overlap 1, 4 MR steps; 1728 blocks, the launch the bench times) on FP32
+    and FP16 storage against the oracle's FP64 RAS on the whole lattice."""
+    dims, U, src, csw, kappa, tbc = synth.config_inputs(2)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    op = oracle.Operator(dims, U, csw, kappa, tbc)
+    ref = op.ras(src, block=(4, 4, 4, 4), delta=1, k=4)
+    fi, fo = lat.field(prec).load(src), lat.field(prec)
+    lat.ras(fo, fi, block=(4, 4, 4, 4), overlap=1, mr_iters=4)
+    out = fo.store(np.zeros_like(src))
+    assert np.linalg.norm(out - ref) <= tol * np.linalg.norm(ref)
+    assert np.max(np.abs(out - ref)) <= tol * np.max(np.abs(ref))
