@@ -672,18 +672,21 @@ def force_timing(wc, args):
     dims, U, phi, csw, kappa, tbc = synth.config_inputs(5)
     lat = wc.Lattice(dims, tbc).load_gauge(U).load_clover(csw, kappa)
     f_phi = lat.field(wc.F64).load(phi)
-    F = np.zeros((int(np.prod(dims)), 4, 3, 3), dtype=np.complex128)
-    out = {"lattice": list(dims)}
+    # the force stays on the device (a CUDA tensor), as an HMC update would use it
+    F = torch.zeros((int(np.prod(dims)), 4, 3, 3), dtype=torch.complex128, device="cuda")
+    out = {"lattice": list(dims), "force_buffer": "device"}
     for name, kw, what in (
             ("flexible_ras", dict(tol=1e-12, precond=wc.PRECOND_RAS, inner_prec=wc.F32),
              "FP64 flexible BiCGStab + FP32 RAS"),
             ("eo_reliable", dict(tol=1e-12, precond=wc.PRECOND_NONE, even_odd=True, solver=wc.SOLVER_RELIABLE),
              "even-odd FP32 BiCGStab with FP64 reliable updates")):
         lat.action_force(f_phi, F, **kw)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         torch.cuda.nvtx.range_push("force_" + name)   # lets a profiler select the timed call
         S = lat.action_force(f_phi, F, **kw)
         torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         out[name] = {"seconds": dt, "S": S, "solves": f"M^+ Y = phi then M X = Y, {what}, tol 1e-12"}
     return out

@@ -5,24 +5,37 @@
 //   dS/deps = -2 Re <Y, (dM/deps) X> = Re tr(L G_mu(x)),
 // and the force is the traceless anti-Hermitian projection
 //   F = TA(G) = (G - G^+)/2 - tr(G - G^+)/6.
+// TA is the orthogonal projection onto su(3) for <A, B> = Re tr(A^+ B), so G
+// only matters through Re tr(L G) with L anti-Hermitian: G and G' give the
+// same F whenever they differ by a Hermitian matrix or a multiple of 1.  In
+// particular, for any complex c and matrix B, c B^+ and -conj(c) B give the
+// same F.  The kernel uses this to move U_mu(x) to the far left of every
+// term and forms F = TA(U H) from one 3x3 matrix H per link.
 //
 // Hopping part (the forward hop at x and the backward hop at x+mu use the
-// link):  G += 2 kappa p [ sum_s (U (1-g_mu) X(x+mu))_s Y_s(x)^+
-//                          - sum_s ((1+g_mu) X(x))_s Y_s(x+mu)^+ U^+ ]
-// (p the time-boundary factor of the hop; for M^+-free form see above).
+// link; p the time-boundary factor of the hop):
+//   G_hop = 2 kappa p [ sum_s (U (1-g_mu) X(x+mu))_s Y_s(x)^+
+//                       - sum_s ((1+g_mu) X(x))_s Y_s(x+mu)^+ U^+ ]
+//   H_hop = 2 kappa p sum_s [ ((1-g_mu) X(x+mu))_s Y_s(x)^+
+//                             + Y_s(x+mu) ((1+g_mu) X(x))_s^+ ].
 //
 // Clover part: T = i csw kappa sum_{a<b} sigma_ab (x) Fhat_ab, so
 //   <Y, dT X> = sum_y sum_{a<b} (i csw kappa / 8)(tr(dQ Xi) - tr(dQ^+ Xi))
-// with Xi_ab(y) the traceless part of sum_{s,t} sigma_ab[s][t] X_t(y) Y_s(y)^+
-// (kernel k_xi).  For the link (x, mu) and each plaquette containing it --
-// corners c0 = x, c1 = x+mu, c2 = x+mu+d nu, c3 = x+d nu (d = +-1), loop
-// links L0 = U_mu(x), L1, L2, L3 in that order -- every clover leaf based at
-// corner c_k contributes through W_k(Z) = L0 ... L_{k-1} Z L_k ... L3
-// (k = 1..4, corner c_{k mod 4}):
-//   G += -(i csw kappa / 4) sigma sum_k [W_k(Xi(c_k)) + W_k(Xi(c_k)^+)^+]
+// with Xi_ab(y) the traceless part of sum_{s,t} sigma_ab[s][t] X_t(y) Y_s(y)^+.
+// For the link (x, mu) and each plaquette containing it -- corners c0 = x,
+// c1 = x+mu, c2 = x+mu+d nu, c3 = x+d nu (d = +-1), loop links U = L0, L1,
+// L2, L3 in that order -- every clover leaf based at corner c_k contributes
+// through W_k(Z) = L0 ... L_{k-1} Z L_k ... L3 (k = 1..4, corner c_{k mod 4}):
+//   G += c sum_k [W_k(Xi(c_k)) + W_k(Xi(c_k)^+)^+],  c = -(i csw kappa / 4) sigma
 // where sigma = +1 when the loop c0 c1 c2 c3 runs counter-clockwise in the
 // (a, b) = (min(mu,nu), max(mu,nu)) plane (the leaves' orientation) and -1
-// when the leaves run through the link backwards.
+// when the leaves run through the link backwards.  As c is imaginary, the
+// second term gives the same F as c W_k(Xi^+), so only the Hermitian
+// Xh = Xi + Xi^+ enters (k_xi stores it, 9 reals per plane and site), and
+//   sum_k W_k(Xh_k) = U [ Xh(c1) T + L1 (S2 Xh(x) + (Xh(c2) L2 + L2 Xh(c3)) L3) ]
+// with S2 = L2 L3 and T = L1 S2: eight 3x3 products per leaf pair (nu, d)
+// instead of twenty-one for the four insertions taken one by one.
+
 #include <math.h>
 
 #include "wc_internal.cuh"
@@ -112,7 +125,7 @@ __device__ __forceinline__ int plane_of(int a, int b)
 // 2x2 block of sigma_ab on spin pair blk (chiral basis), as complex entries
 // sigma_xy = -s3, sigma_xz = s2, sigma_yz = -s1 on both pairs;
 // sigma_xt = eta s1, sigma_yt = eta s2, sigma_zt = eta s3, eta = -1, +1
-__device__ void sigma_block(int plane, int blk, cx<double> s[2][2])
+__device__ __forceinline__ void sigma_block(int plane, int blk, cx<double> s[2][2])
 {
     const double eta = blk == 0 ? -1.0 : 1.0;
     int pauli;
@@ -139,8 +152,67 @@ __device__ void sigma_block(int plane, int blk, cx<double> s[2][2])
     }
 }
 
-// Xi_ab(y) for the six planes, traceless part: xi[(plane*9 + 3i + j) * V + y]
-__global__ void k_xi(Geom g, const double2 *X, const double2 *Y, double2 *xi)
+// Hermitian 3x3 matrix: real diagonal d, upper entries o = (h01, h02, h12)
+struct H3 {
+    double d[3];
+    cx<double> o[3];
+};
+
+// off-diagonal entry (i, k), i != k (constants once the callers are unrolled)
+__device__ __forceinline__ cx<double> hoff(const H3 &h, int i, int k)
+{
+    const cx<double> v = h.o[i + k - 1];
+    return i < k ? v : conj(v);
+}
+
+// acc + H B
+__device__ __forceinline__ void fma_hm(const H3 &h, const M3 &b, M3 &acc)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cx<double> s = acc.m[i][j];
+            s.re = fma(h.d[i], b.m[i][j].re, s.re);
+            s.im = fma(h.d[i], b.m[i][j].im, s.im);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (k != i) s = cfma(hoff(h, i, k), b.m[k][j], s);
+            acc.m[i][j] = s;
+        }
+}
+
+// acc + A H
+__device__ __forceinline__ void fma_mh(const M3 &a, const H3 &h, M3 &acc)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cx<double> s = acc.m[i][j];
+            s.re = fma(a.m[i][j].re, h.d[j], s.re);
+            s.im = fma(a.m[i][j].im, h.d[j], s.im);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (k != j) s = cfma(a.m[i][k], hoff(h, k, j), s);
+            acc.m[i][j] = s;
+        }
+}
+
+__device__ __forceinline__ M3 zero3()
+{
+    M3 r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) r.m[i][j] = mkc(0.0, 0.0);
+    return r;
+}
+
+// Xh_ab(y) = Xi + Xi^+ for the six planes, Xi the traceless part of
+// sum_{s,t} sigma_ab[s][t] X_t(y) Y_s(y)^+.  Layout [6][9][V] doubles:
+// h00 h11 h22, re/im of h01, h02, h12.
+__global__ void k_xi(Geom g, const double2 *X, const double2 *Y, double *xh)
 {
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= g.V) return;
@@ -152,16 +224,16 @@ __global__ void k_xi(Geom g, const double2 *X, const double2 *Y, double2 *xi)
         xs[k] = mkc(a.x, a.y);
         ys[k] = mkc(b.x, b.y);
     }
+#pragma unroll
     for (int pl = 0; pl < 6; ++pl) {
-        M3 Z;
+        M3 Z = zero3();
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) Z.m[i][j] = mkc(0.0, 0.0);
         for (int blk = 0; blk < 2; ++blk) {
             cx<double> sg[2][2];
             sigma_block(pl, blk, sg);
+#pragma unroll
             for (int s = 0; s < 2; ++s)
+#pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     const cx<double> w = sg[s][t];
                     if (w.re == 0.0 && w.im == 0.0) continue;
@@ -173,33 +245,36 @@ __global__ void k_xi(Geom g, const double2 *X, const double2 *Y, double2 *xi)
                             Z.m[i][j] = cfma(w, xs[3 * tt + i] * conj(ys[3 * ss + j]), Z.m[i][j]);
                 }
         }
-        const cx<double> tr = (1.0 / 3.0) * (Z.m[0][0] + Z.m[1][1] + Z.m[2][2]);
+        const double tr = (2.0 / 3.0) * (Z.m[0][0].re + Z.m[1][1].re + Z.m[2][2].re);
+        double *o = xh + (size_t)pl * 9 * V + y;
+        o[0] = 2.0 * Z.m[0][0].re - tr;
+        o[(size_t)V] = 2.0 * Z.m[1][1].re - tr;
+        o[2 * (size_t)V] = 2.0 * Z.m[2][2].re - tr;
+        const int ij[3][2] = {{0, 1}, {0, 2}, {1, 2}};
 #pragma unroll
-        for (int i = 0; i < 3; ++i) Z.m[i][i] = Z.m[i][i] - tr;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                xi[((size_t)pl * 9 + 3 * i + j) * V + y] = make_double2(Z.m[i][j].re, Z.m[i][j].im);
+        for (int k = 0; k < 3; ++k) {
+            const cx<double> v = Z.m[ij[k][0]][ij[k][1]] + conj(Z.m[ij[k][1]][ij[k][0]]);
+            o[(size_t)(3 + 2 * k) * V] = v.re;
+            o[(size_t)(4 + 2 * k) * V] = v.im;
+        }
     }
 }
 
-__device__ M3 load_xi(const double2 *xi, int V, int plane, int y)
+__device__ __forceinline__ H3 load_xh(const double *xh, int V, int plane, int y)
 {
-    M3 r;
+    const double *p = xh + (size_t)plane * 9 * V + y;
+    H3 h;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) h.d[k] = __ldg(p + (size_t)k * V);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const double2 v = xi[((size_t)plane * 9 + 3 * i + j) * V + y];
-            r.m[i][j] = mkc(v.x, v.y);
-        }
-    return r;
+    for (int k = 0; k < 3; ++k) h.o[k] = mkc(__ldg(p + (size_t)(3 + 2 * k) * V), __ldg(p + (size_t)(4 + 2 * k) * V));
+    return h;
 }
 
 // (1 + s gamma_mu) psi as a full spinor (chiral basis)
-__device__ void project_full(int mu, int s, const cx<double> p[12], cx<double> o[12])
+__device__ __forceinline__ void project_full(int mu, int s, const cx<double> p[12], cx<double> o[12])
 {
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
         const cx<double> u0 = p[c], u1 = p[3 + c], d0 = p[6 + c], d1 = p[9 + c];
         const double sd = (double)s;
@@ -232,18 +307,52 @@ __device__ void project_full(int mu, int s, const cx<double> p[12], cx<double> o
     }
 }
 
-__device__ void load_sp(const double2 *f, int V, int x, cx<double> s[12])
+__device__ __forceinline__ void load_sp(const double2 *f, int V, int x, cx<double> s[12])
 {
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        const double2 v = f[(size_t)k * V + x];
+        const double2 v = __ldg(f + (size_t)k * V + x);
         s[k] = mkc(v.x, v.y);
     }
 }
 
-// one thread per link (x, mu): F = TA(G_hop + G_clover), canonical layout
-__global__ void k_force(Geom g, GaugeStore G, const double2 *X, const double2 *Y, const double2 *xi,
-                        double kappa, double csw, double2 *F)
+// acc + sum_s a_s b_s^+ (a, b spinors; 3x3 colour outer products summed over spin)
+__device__ __forceinline__ void fma_outer(const cx<double> a[12], const cx<double> b[12], M3 &acc)
+{
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc.m[p][q] = cfma(a[3 * s + p], conj(b[3 * s + q]), acc.m[p][q]);
+}
+
+// The four insertions of the leaf pair (nu, D) with U = L0 factored out:
+// Xh(c1) T + L1 (S2 Xh(x) + (Xh(c2) L2 + L2 Xh(c3)) L3), S2 = L2 L3, T = L1 S2.
+template <int D>
+__device__ __forceinline__ M3 leaf_pair(const Geom &g, const GaugeStore &G, const double *xh, int x, const int c[4],
+                                        int mu, int nu, int pl, int c1)
+{
+    const int V = g.V;
+    const int c2 = shift(g, c, mu, 1, nu, D), c3 = shift(g, c, mu, 0, nu, D);
+    const M3 L2 = dag(link(G, V, mu, c3));                          // c2 -> c3
+    const M3 L3 = D == 1 ? dag(link(G, V, nu, x)) : link(G, V, nu, c3);   // c3 -> x
+    const M3 S2 = mul(L2, L3);
+    M3 K = zero3();
+    fma_hm(load_xh(xh, V, pl, c2), L2, K);
+    fma_mh(L2, load_xh(xh, V, pl, c3), K);
+    K = mul(K, L3);
+    fma_mh(S2, load_xh(xh, V, pl, x), K);
+    const M3 L1 = D == 1 ? link(G, V, nu, c1) : dag(link(G, V, nu, c2));  // c1 -> c2
+    M3 E = mul(L1, K);
+    const M3 T = mul(L1, S2);
+    fma_hm(load_xh(xh, V, pl, c1), T, E);
+    return E;
+}
+
+// one thread per link (x, mu): F = TA(U H), canonical layout [V][4][3][3]
+__global__ void __launch_bounds__(128) k_force(Geom g, GaugeStore G, const double2 *X, const double2 *Y,
+                                               const double *xh, double kappa, double csw, double2 *F)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 4 * g.V) return;
@@ -251,105 +360,59 @@ __global__ void k_force(Geom g, GaugeStore G, const double2 *X, const double2 *Y
     const int x = i % V, mu = i / V;
     int c[4];
     site_coords(g, x, c);
-    const M3 U = link(G, V, mu, x);
-    M3 Gm;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) Gm.m[a][b] = mkc(0.0, 0.0);
+    M3 H = zero3();
 
-    // hopping part
+    // clover part: H = -(i csw kappa / 4) sum_{nu, d} sigma E(nu, d)
+    if (csw != 0.0) {
+        M3 A = zero3();
+        const int c1 = shift(g, c, mu, 1, mu, 0);
+#pragma unroll 1
+        for (int nu = 0; nu < 4; ++nu) {
+            if (nu == mu) continue;
+            const int pl = plane_of(mu < nu ? mu : nu, mu < nu ? nu : mu);
+            // d = +1 runs counter-clockwise in the (a, b) plane when mu < nu
+            const double sp = mu < nu ? 1.0 : -1.0;
+            const M3 Ep = leaf_pair<1>(g, G, xh, x, c, mu, nu, pl, c1);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) A.m[a][b] = A.m[a][b] + sp * Ep.m[a][b];
+            const M3 Em = leaf_pair<-1>(g, G, xh, x, c, mu, nu, pl, c1);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) A.m[a][b] = A.m[a][b] - sp * Em.m[a][b];
+        }
+        const double beta = -csw * kappa / 4.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) H.m[a][b] = beta * times_i(A.m[a][b]);
+    }
+
+    // hopping part: H += 2 kappa p sum_s [((1-g) X(x+mu))_s Y_s(x)^+ + Y_s(x+mu) ((1+g) X(x))_s^+]
     {
         const bool wrap = c[mu] == g.L[mu] - 1;
         const int xf = wrap ? x - (g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
-        const double ph = (mu == 3 && wrap) ? (double)g.tbc : 1.0;
-        cx<double> xf_s[12], x_s[12], a[12], cpl[12], yx[12], yf[12];
-        load_sp(X, V, xf, xf_s);
-        load_sp(X, V, x, x_s);
-        load_sp(Y, V, x, yx);
-        load_sp(Y, V, xf, yf);
-        project_full(mu, -1, xf_s, a);    // (1 - g) X(x+mu)
-        project_full(mu, +1, x_s, cpl);   // (1 + g) X(x)
-        M3 Z1, Z2;
+        const double k2 = 2.0 * kappa * ((mu == 3 && wrap) ? (double)g.tbc : 1.0);
+        M3 Z = zero3();
+        cx<double> a[12], b[12];
+        load_sp(X, V, xf, b);
+        project_full(mu, -1, b, a);
+        load_sp(Y, V, x, b);
+        fma_outer(a, b, Z);
+        load_sp(X, V, x, b);
+        project_full(mu, +1, b, a);
+        load_sp(Y, V, xf, b);
+        fma_outer(b, a, Z);
 #pragma unroll
         for (int p = 0; p < 3; ++p)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                Z1.m[p][q] = mkc(0.0, 0.0);
-                Z2.m[p][q] = mkc(0.0, 0.0);
-            }
-        for (int s = 0; s < 4; ++s) {
-            cx<double> ua[3];
-            for (int p = 0; p < 3; ++p) {
-                ua[p] = U.m[p][0] * a[3 * s];
-                ua[p] = cfma(U.m[p][1], a[3 * s + 1], ua[p]);
-                ua[p] = cfma(U.m[p][2], a[3 * s + 2], ua[p]);
-            }
-            for (int p = 0; p < 3; ++p)
-                for (int q = 0; q < 3; ++q) {
-                    Z1.m[p][q] = Z1.m[p][q] + ua[p] * conj(yx[3 * s + q]);
-                    Z2.m[p][q] = Z2.m[p][q] + cpl[3 * s + p] * conj(yf[3 * s + q]);
-                }
-        }
-        Z2 = mul(Z2, dag(U));
-        const cx<double> k2 = mkc(2.0 * kappa * ph, 0.0);
-        add_scaled(Gm, k2, Z1);
-        add_scaled(Gm, (-1.0) * k2, Z2);
+            for (int q = 0; q < 3; ++q) H.m[p][q] = H.m[p][q] + k2 * Z.m[p][q];
     }
 
-    // clover part
-    if (csw != 0.0) {
-        const cx<double> pref = mkc(0.0, -csw * kappa / 4.0);   // -(i csw kappa / 4)
-        for (int nu = 0; nu < 4; ++nu) {
-            if (nu == mu) continue;
-            const int a = mu < nu ? mu : nu, b = mu < nu ? nu : mu;
-            const int pl = plane_of(a, b);
-            for (int d = -1; d <= 1; d += 2) {
-                const bool ccw = (d == 1) == (mu < nu);
-                const double sigma = ccw ? 1.0 : -1.0;
-                // corners and loop links
-                const int c1 = shift(g, c, mu, 1, nu, 0);
-                const int c2 = shift(g, c, mu, 1, nu, d);
-                const int c3 = shift(g, c, mu, 0, nu, d);
-                M3 L[4];
-                L[0] = U;
-                if (d == 1) {
-                    L[1] = link(G, V, nu, c1);            // c1 -> c1 + nu
-                    L[3] = dag(link(G, V, nu, x));        // c3 = x + nu -> x
-                } else {
-                    L[1] = dag(link(G, V, nu, c2));       // c1 -> c1 - nu
-                    L[3] = link(G, V, nu, c3);            // c3 = x - nu -> x
-                }
-                L[2] = dag(link(G, V, mu, c3));           // c2 -> c3
-                const int corner[4] = {x, c1, c2, c3};
-                M3 pre = L[0];
-                M3 suf[5];
-                suf[4] = ident();
-                suf[3] = L[3];
-                suf[2] = mul(L[2], L[3]);
-                suf[1] = mul(L[1], suf[2]);
-                M3 acc;
-#pragma unroll
-                for (int p = 0; p < 3; ++p)
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) acc.m[p][q] = mkc(0.0, 0.0);
-                for (int k = 1; k <= 4; ++k) {
-                    // pre = L0 ... L_{k-1}, suf[k] = L_k ... L3
-                    const M3 Xi = load_xi(xi, V, pl, corner[k & 3]);
-                    const M3 w1 = mul(mul(pre, Xi), suf[k]);
-                    const M3 w2 = dag(mul(mul(pre, dag(Xi)), suf[k]));
-#pragma unroll
-                    for (int p = 0; p < 3; ++p)
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) acc.m[p][q] = acc.m[p][q] + w1.m[p][q] + w2.m[p][q];
-                    if (k < 4) pre = mul(pre, L[k]);
-                }
-                add_scaled(Gm, sigma * pref, acc);
-            }
-        }
-    }
-
-    // F = (G - G^+)/2 - tr(G - G^+)/6
+    // F = TA(U H) = (G - G^+)/2 - tr(G - G^+)/6
+    const M3 Gm = mul(link(G, V, mu, x), H);
     M3 D;
 #pragma unroll
     for (int p = 0; p < 3; ++p)
@@ -383,20 +446,20 @@ bool is_device_ptr(const void *p)
 wc_status force_from_solutions(wc_lattice lat, wc_field X, wc_field Y, double2 *dst)
 {
     const int V = lat->g.V;
-    double2 *xi = nullptr;
-    wc_status st = check_cuda(lat, cudaMalloc(&xi, sizeof(double2) * 54 * (size_t)V), "cudaMalloc(xi)");
+    double *xh = nullptr;
+    wc_status st = check_cuda(lat, cudaMalloc(&xh, sizeof(double) * 54 * (size_t)V), "cudaMalloc(xh)");
     if (st != WC_OK) return st;
     k_xi<<<(V + 127) / 128, 128, 0, lat->stream>>>(lat->g, static_cast<const double2 *>(X->data),
-                                                   static_cast<const double2 *>(Y->data), xi);
+                                                   static_cast<const double2 *>(Y->data), xh);
     st = check_launch(lat, "xi");
     if (st == WC_OK) {
-        k_force<<<(4 * V + 63) / 64, 64, 0, lat->stream>>>(lat->g, lat->gauge, static_cast<const double2 *>(X->data),
-                                                           static_cast<const double2 *>(Y->data), xi, lat->kappa,
+        k_force<<<(4 * V + 127) / 128, 128, 0, lat->stream>>>(lat->g, lat->gauge, static_cast<const double2 *>(X->data),
+                                                           static_cast<const double2 *>(Y->data), xh, lat->kappa,
                                                            lat->csw, dst);
         st = check_launch(lat, "force");
     }
     cudaStreamSynchronize(lat->stream);
-    cudaFree(xi);
+    cudaFree(xh);
     return st;
 }
 
