@@ -284,6 +284,7 @@ def run_ours(args, world, rank, local):
     clk = clocks.summary()
     shape = lat.apply_shape(wc.F32, 0)
     mdag_ms = time_applies(lat, outs, ins, "Mdag", 500, stream)
+    fp64_apply = fp64_apply_timing(wc, lat, dims, src, stream)
     copy_gbs = copy_rate(BYTES_PER_SITE["f32"] * V, stream)
     multi = multi_rhs_apply(wc, lat, dims, ms / args.steps, stream)
     ras = ras_timing(wc, lat, dims, src, stream)
@@ -328,6 +329,7 @@ def run_ours(args, world, rank, local):
         line["solve"] = solve
     line["apply_mdag"] = {"ms": mdag_ms, "gflops": flops / (mdag_ms * 1e-3) / 1e9,
                           "roofline_frac": bytes_alg / (mdag_ms * 1e-3) / 1e9 / peak}
+    line["apply_fp64"] = fp64_apply
     if large is not None:
         line["large_32x32x32x64"] = large
     if batch is not None:
@@ -720,9 +722,22 @@ def solve_comparison(wc, lat, src, args):
                      ("eo_reliable_h16", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE, delta=0.01,
                                               krylov_prec=wc.F16, even_odd=True)),
                      ("eo_nested_h16", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED, inner_tol=0.01,
-                                            inner_iters=100, krylov_prec=wc.F16, even_odd=True))):
+                                            inner_iters=100, krylov_prec=wc.F16, even_odd=True)),
+                     # the same solvers with their FP64 operator steps in double-FP32 arithmetic
+                     ("fp64_plain_df32", dict(precond=wc.PRECOND_NONE)),
+                     ("eo_fp64_plain_df32", dict(precond=wc.PRECOND_NONE, even_odd=True)),
+                     ("reliable_ras_f16_df32", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
+                                                    solver=wc.SOLVER_RELIABLE, delta=0.01)),
+                     ("eo_reliable_f32_df32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE, delta=0.01,
+                                                   even_odd=True)),
+                     ("eo_reliable_h16_df32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE,
+                                                   delta=0.01, krylov_prec=wc.F16, even_odd=True)),
+                     ("eo_nested_h16_df32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED,
+                                                 inner_tol=0.01, inner_iters=100, krylov_prec=wc.F16,
+                                                 even_odd=True))):
         if args.solves and name not in args.solves.split(","):
             continue
+        lat.set_fp64_arith(wc.ARITH_DF32 if name.endswith("_df32") else wc.ARITH_F64)
         x = lat.field(wc.F64)
         lat.solve(x, b, tol=1e-10, max_iter=20000, check=False, **kw)   # warm-up (allocations)
         x.close()
@@ -733,15 +748,45 @@ def solve_comparison(wc, lat, src, args):
         out[name] = {"seconds": info.seconds, "iters": info.iters, "true_rel_resid": info.true_rel_resid,
                      "status": wc.STATUS.get(info.status, info.status)}
         x.close()
+    lat.set_fp64_arith(wc.ARITH_F64)
     if "fp64_plain" in out and "mixed_ras_f32" in out:
         out["speedup_mixed_f32_vs_fp64"] = out["fp64_plain"]["seconds"] / out["mixed_ras_f32"]["seconds"]
-    ok = [k for k, v in out.items() if isinstance(v, dict) and k != "fp64_plain" and v["status"] == "WC_OK"]
+    # mixed-precision solvers only (not the FP64-only ones, in either arithmetic)
+    ok = [k for k, v in out.items() if isinstance(v, dict) and "fp64_plain" not in k and v["status"] == "WC_OK"]
     if ok and "fp64_plain" in out:
         best = min(ok, key=lambda k: out[k]["seconds"])
         out["fastest_mixed"] = best
         out["speedup_fastest_mixed_vs_fp64"] = out["fp64_plain"]["seconds"] / out[best]["seconds"]
     out["ras"] = "4^4 blocks, overlap 1, 4 MR iterations"
+    out["df32"] = "suffix _df32: FP64 operator steps in double-FP32 arithmetic (wc_set_fp64_arith)"
     return out
+
+
+def fp64_apply_timing(wc, lat, dims, src, stream, steps=60):
+    """The FP64 operator on FP64 fields at the bench lattice: FP64
+    arithmetic against double-FP32 arithmetic (each value a pair of floats,
+    FP32 pipes), same 1536 B per site; rate in FP64-equivalent flops and the
+    largest difference between the two results relative to the largest
+    output."""
+    import torch
+    V = int(np.prod(dims))
+    ins = [lat.field(wc.F64).load(src * (1.0 + 0.1 * k)) for k in range(4)]
+    outs = [lat.field(wc.F64) for _ in range(4)]
+    res = {}
+    got = {}
+    for name, mode in (("f64", wc.ARITH_F64), ("df32", wc.ARITH_DF32)):
+        lat.set_fp64_arith(mode)
+        ms = time_applies(lat, outs, ins, "M", steps, stream)
+        lat.apply_M(outs[0], ins[0])
+        got[name] = outs[0].store(np.zeros_like(src))
+        res[name] = {"ms": ms, "fp64_equiv_tflops": FLOPS_PER_SITE * V / (ms * 1e-3) / 1e12,
+                     "gbs": BYTES_PER_SITE["f64"] * V / (ms * 1e-3) / 1e9}
+    lat.set_fp64_arith(wc.ARITH_F64)
+    for f in ins + outs:
+        f.close()
+    res["speedup_df32_vs_f64"] = res["f64"]["ms"] / res["df32"]["ms"]
+    res["df32_max_diff_rel"] = float(np.max(np.abs(got["df32"] - got["f64"])) / np.max(np.abs(got["f64"])))
+    return res
 
 
 def main():

@@ -72,6 +72,9 @@ typedef enum { WC_F64 = 0, WC_F32 = 1, WC_F16 = 2 } wc_prec;
 
 typedef enum { WC_PRECOND_NONE = 0, WC_PRECOND_RAS = 1 } wc_precond;
 
+/* Arithmetic of the operator on FP64 fields (wc_set_fp64_arith). */
+typedef enum { WC_ARITH_F64 = 0, WC_ARITH_DF32 = 1 } wc_fp64_arith;
+
 /* Overlapped RAS (paper Sec. 2, "overlapped Restricted Additive Schwarz"):
  * the lattice is tiled from the origin by blocks of block[mu] sites; each
  * block is extended by `overlap` sites on every face (periodically), M is
@@ -149,6 +152,22 @@ wc_status wc_create_lattice(const int dims[4], int t_bc, void *cuda_stream, wc_l
 wc_status wc_destroy_lattice(wc_lattice lat);
 /* Switch the stream later kernels of this lattice are queued on. */
 wc_status wc_set_stream(wc_lattice lat, void *cuda_stream);
+
+/* Arithmetic of every later FP64 operator application on this lattice:
+ * wc_apply_M / _Mdag / _hop and wc_apply_schur on FP64 fields, and the FP64
+ * operator steps inside the solvers (FP64 BiCGStab iterations, reliable
+ * updates, true residuals, even-odd source preparation and
+ * reconstruction).  WC_ARITH_F64 (the default): FP64 arithmetic.
+ * WC_ARITH_DF32: double-FP32 arithmetic -- each value is carried as the
+ * unevaluated sum of two floats (about 47 significant bits) and the
+ * operations run on the FP32 pipes, which on GB300 are 64 times faster than
+ * its FP64 pipe.  Storage stays FP64.  Results agree with FP64 arithmetic to
+ * ~1e-14 relative to the largest input; inputs with |x| < 2^-103 keep only
+ * 24 bits and |x| < 2^-126 reads as zero.  BLAS-1 steps and the force stay
+ * in FP64.  Returns WC_ERR_ARG for any other value.  Host-side setting
+ * only; graphs captured earlier (wc_solve_batch) keep the arithmetic they
+ * were captured with. */
+wc_status wc_set_fp64_arith(wc_lattice lat, int arith);
 
 /* Load the gauge field U (canonical layout, data = device or host pointer).
  * Links are stored as their first two rows (12 reals; paper Sec. 2,
@@ -230,7 +249,9 @@ wc_status wc_apply_schur(wc_lattice lat, wc_field out, wc_field in, int dagger);
  * start while the previous kernel of the stream drains, prefetches its
  * links and clover into L2, then waits for that kernel; plain launch while
  * the stream is being captured); all -1 if nothing was chosen yet.  The choice is shared by lattices of equal
- * extent in the process. */
+ * extent in the process.  With prec = WC_F64 on a lattice in WC_ARITH_DF32
+ * mode (wc_set_fp64_arith) the call reports or pins the double-FP32
+ * operator's shape, which is chosen separately from the FP64 one. */
 wc_status wc_apply_shape(wc_lattice lat, wc_prec prec, int kind, int force_index, int shape_out[6]);
 
 /* ---- fused BLAS-1 (FP64 accumulation; blocking) ---------------------- */

@@ -29,6 +29,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 F64, F32, F16 = 0, 1, 2
 PRECOND_NONE, PRECOND_RAS = 0, 1
+ARITH_F64, ARITH_DF32 = 0, 1
 SOLVER_FLEXIBLE, SOLVER_RELIABLE, SOLVER_NESTED = 0, 1, 2
 STATUS = {0: "WC_OK", 1: "WC_ERR_ARG", 2: "WC_ERR_CUDA", 3: "WC_ERR_STATE", 4: "WC_ERR_NOT_CONVERGED",
           5: "WC_ERR_BREAKDOWN", 6: "WC_ERR_NAN", 7: "WC_ERR_TIMEOUT"}
@@ -39,7 +40,7 @@ EXPORTED = [
     "wc_apply_M", "wc_apply_Mdag", "wc_apply_hop", "wc_dot", "wc_norm2", "wc_axpy_norm",
     "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
     "wc_dot_noalloc", "wc_ras_autotune", "wc_apply_shape", "wc_apply_schur", "wc_apply_multi",
-    "wc_force_times_links",
+    "wc_force_times_links", "wc_set_fp64_arith",
 ]
 
 
@@ -70,6 +71,7 @@ _L = _lib
 _L.wc_create_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp, ctypes.POINTER(_vp)]
 _L.wc_destroy_lattice.argtypes = [_vp]
 _L.wc_set_stream.argtypes = [_vp, _vp]
+_L.wc_set_fp64_arith.argtypes = [_vp, ctypes.c_int]
 _L.wc_load_gauge.argtypes = [_vp, _vp]
 _L.wc_load_clover.argtypes = [_vp, ctypes.c_double, ctypes.c_double]
 _L.wc_field_create.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(_vp)]
@@ -198,6 +200,12 @@ class Lattice:
     def set_stream(self, stream):
         s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
         _check(_L.wc_set_stream(self.handle, _vp(s)), self.handle)
+
+    def set_fp64_arith(self, arith: int):
+        """ARITH_F64 (default) or ARITH_DF32: arithmetic of the FP64 operator
+        applications on this lattice (see wc_set_fp64_arith)."""
+        _check(_L.wc_set_fp64_arith(self.handle, int(arith)), self.handle)
+        return self
 
     def load_gauge(self, U):
         if _nbytes(U) != self.volume * 36 * 16:

@@ -97,13 +97,20 @@ __global__ void k_pack_gauge(int V, const double2 *U, GaugeStore g)
 #pragma unroll
     for (int k = 0; k < 6; ++k) a[k] = u[k];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) g.u64[((size_t)mu * 9 + k) * V + x] = a[k];
+    for (int k = 0; k < 6; ++k) {
+        g.u64[((size_t)mu * 9 + k) * V + x] = a[k];
+        g.udf[((size_t)mu * 9 + k) * V + x] = df_pack(a[k]);
+    }
     cx<double> r01[6], r2[3];
 #pragma unroll
     for (int k = 0; k < 6; ++k) r01[k] = mkc(a[k].x, a[k].y);
     reconstruct_row2(r01, r2);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) g.u64[((size_t)mu * 9 + 6 + k) * V + x] = make_double2(r2[k].re, r2[k].im);
+    for (int k = 0; k < 3; ++k) {
+        const double2 v = make_double2(r2[k].re, r2[k].im);
+        g.u64[((size_t)mu * 9 + 6 + k) * V + x] = v;
+        g.udf[((size_t)mu * 9 + 6 + k) * V + x] = df_pack(v);
+    }
 #pragma unroll
     for (int j = 0; j < 3; ++j)
         g.u32[((size_t)mu * 3 + j) * V + x] =
@@ -273,7 +280,11 @@ __global__ void k_build_clover(Geom g, GaugeStore G, CloverStore C, double csw, 
                 r[k++] = blk[i][j].im;
             }
 #pragma unroll
-        for (int q = 0; q < 18; ++q) C.c64[((size_t)b * 18 + q) * V + x] = make_double2(r[2 * q], r[2 * q + 1]);
+        for (int q = 0; q < 18; ++q) {
+            const double2 v = make_double2(r[2 * q], r[2 * q + 1]);
+            C.c64[((size_t)b * 18 + q) * V + x] = v;
+            C.cdf[((size_t)b * 18 + q) * V + x] = df_pack(v);
+        }
 #pragma unroll
         for (int q = 0; q < 9; ++q)
             C.c32[((size_t)b * 9 + q) * V + x] =
@@ -300,6 +311,7 @@ cudaError_t dalloc(T **p, size_t bytes)
 void free_gauge(GaugeStore &g)
 {
     cudaFree(g.u64);
+    cudaFree(g.udf);
     cudaFree(g.u32);
     cudaFree(g.u16a);
     cudaFree(g.u16b);
@@ -309,6 +321,7 @@ void free_gauge(GaugeStore &g)
 void free_clover(CloverStore &c)
 {
     cudaFree(c.c64);
+    cudaFree(c.cdf);
     cudaFree(c.c32);
     cudaFree(c.c16);
     c = CloverStore{};
@@ -445,6 +458,14 @@ wc_status wc_set_stream(wc_lattice lat, void *cuda_stream)
     return WC_OK;
 }
 
+wc_status wc_set_fp64_arith(wc_lattice lat, int arith)
+{
+    if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
+    if (arith != WC_ARITH_F64 && arith != WC_ARITH_DF32) return set_error(lat, WC_ERR_ARG, "unknown FP64 arithmetic");
+    lat->fp64_arith = arith;
+    return WC_OK;
+}
+
 wc_status wc_load_gauge(wc_lattice lat, const double *data)
 {
     if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
@@ -454,6 +475,7 @@ wc_status wc_load_gauge(wc_lattice lat, const double *data)
     wc_status st = WC_OK;
     if (!g.u64) {
         st = check_cuda(lat, dalloc(&g.u64, sizeof(double2) * 36 * (size_t)V), "cudaMalloc(gauge)");
+        if (st == WC_OK) st = check_cuda(lat, dalloc(&g.udf, sizeof(float4) * 36 * (size_t)V), "cudaMalloc(gauge)");
         if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u32, sizeof(float4) * 12 * (size_t)V), "cudaMalloc(gauge)");
         if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u16a, sizeof(uint4) * 4 * (size_t)V), "cudaMalloc(gauge)");
         if (st == WC_OK) st = check_cuda(lat, dalloc(&g.u16b, sizeof(uint2) * 4 * (size_t)V), "cudaMalloc(gauge)");
@@ -493,6 +515,7 @@ wc_status wc_load_clover(wc_lattice lat, double csw, double kappa)
     wc_status st = WC_OK;
     if (!c.c64) {
         st = check_cuda(lat, dalloc(&c.c64, sizeof(double2) * 36 * (size_t)V), "cudaMalloc(clover)");
+        if (st == WC_OK) st = check_cuda(lat, dalloc(&c.cdf, sizeof(float4) * 36 * (size_t)V), "cudaMalloc(clover)");
         if (st == WC_OK) st = check_cuda(lat, dalloc(&c.c32, sizeof(float4) * 18 * (size_t)V), "cudaMalloc(clover)");
         if (st == WC_OK) st = check_cuda(lat, dalloc(&c.c16, sizeof(uint4) * 9 * (size_t)V), "cudaMalloc(clover)");
         if (st != WC_OK) {

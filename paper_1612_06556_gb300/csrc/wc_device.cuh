@@ -21,11 +21,16 @@
 //           the 15 complex entries below the diagonal in row order
 //           (1,0) (2,0) (2,1) (3,0) ... (5,4); 72 reals per site
 //           F64: double2 [36][V]       F32: float4 [18][V]    F16: uint4 [9][V]
+//   FP64 links and clover are also kept split into double-FP32 pairs (same
+//   planes, float4 = hi, lo of the real part, hi, lo of the imaginary part)
+//   for the double-FP32 operator (wc_df.cuh).
 #pragma once
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "wc_df.cuh"
 
 namespace wc {
 
@@ -112,6 +117,7 @@ __device__ __forceinline__ void site_coords(const Geom &g, int s, int c[4])
 
 struct GaugeStore {
     double2 *u64 = nullptr;   // [4][9][V]
+    float4 *udf = nullptr;    // [4][9][V] u64 as double-FP32 pairs
     float4 *u32 = nullptr;    // [4][3][V]
     uint4 *u16a = nullptr;    // [4][V]  row 0, row 1 entry 0
     uint2 *u16b = nullptr;    // [4][V]  row 1 entries 1, 2
@@ -119,6 +125,7 @@ struct GaugeStore {
 
 struct CloverStore {
     double2 *c64 = nullptr;   // [36][V]
+    float4 *cdf = nullptr;    // [36][V] c64 as double-FP32 pairs
     float4 *c32 = nullptr;    // [18][V]
     uint4 *c16 = nullptr;     // [9][V]
 };
@@ -172,6 +179,11 @@ __device__ __forceinline__ void reconstruct_row2(const cx<R> u[6], cx<R> c[3])
 
 struct P64 {
     using real = double;
+    // register caps of the operator's launch shapes (bit 0: cap 1, bit 1:
+    // cap 2) and the minimum resident 256-thread CTAs that cap 1 stands for
+    static constexpr int kCaps = 0;   // ALU-bound on the FP64 pipe: no cap
+    static constexpr int kCap1MinBlocks = 1;
+    static constexpr int kEoMinBlocks = 1;   // even-odd kernel: minimum resident CTAs of 128
     static __device__ __forceinline__ void load_spinor(const void *d, const float *, int V, int x,
                                                        cx<double> s[12])
     {
@@ -228,6 +240,9 @@ struct P64 {
 
 struct P32 {
     using real = float;
+    static constexpr int kCaps = 3;   // cap 1: 64 registers, cap 2: 85
+    static constexpr int kCap1MinBlocks = 4;
+    static constexpr int kEoMinBlocks = 1;
     static __device__ __forceinline__ void load_spinor(const void *d, const float *, int V, int x,
                                                        cx<float> s[12])
     {
@@ -280,8 +295,78 @@ struct P32 {
     }
 };
 
+// FP64 storage, double-FP32 arithmetic (the operator's FP64 path when the
+// lattice selects it): spinors are converted on load and store, links and
+// clover come from their pre-split copies.
+struct PDF {
+    using real = df;
+    static constexpr int kCaps = 1;   // cap 1: 128 registers (2 CTAs of 256)
+    static constexpr int kCap1MinBlocks = 2;
+    static constexpr int kEoMinBlocks = 4;   // 128 registers: latency-bound, occupancy pays
+    static __device__ __forceinline__ void load_spinor(const void *d, const float *, int V, int x, cx<df> s[12])
+    {
+        const double2 *p = static_cast<const double2 *>(d);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double2 v = __ldg(p + (size_t)k * V + x);
+            s[k] = {df_from_double(v.x), df_from_double(v.y)};
+        }
+    }
+    static __device__ __forceinline__ df load_spinor_raw(const void *d, const float *n, int V, int x, cx<df> s[12])
+    {
+        load_spinor(d, n, V, x, s);
+        return df(1.0f, 0.0f);
+    }
+    static __device__ __forceinline__ void store_spinor(void *d, float *, int V, int x, const cx<df> s[12])
+    {
+        double2 *p = static_cast<double2 *>(d);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[(size_t)k * V + x] = make_double2(df_to_double(s[k].re), df_to_double(s[k].im));
+    }
+    static __device__ __forceinline__ void load_link(const GaugeStore &g, int V, int mu, int x, cx<df> a[6],
+                                                     cx<df> c[3])
+    {
+        const float4 *p = g.udf + (size_t)mu * 9 * V + x;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 v = __ldg(p + (size_t)k * V);
+            a[k] = {df(v.x, v.y), df(v.z, v.w)};
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 v = __ldg(p + (size_t)(6 + k) * V);
+            c[k] = {df(v.x, v.y), df(v.z, v.w)};
+        }
+    }
+    // real entry t (0..5: the diagonal) and complex lower entry m (0..14) of
+    // block b at position x
+    static __device__ __forceinline__ df clover_real(const CloverStore &c, int V, int x, int b, int t)
+    {
+        const float4 v = __ldg(c.cdf + (size_t)(b * 18 + (t >> 1)) * V + x);
+        return (t & 1) ? df(v.z, v.w) : df(v.x, v.y);
+    }
+    static __device__ __forceinline__ cx<df> clover_lower(const CloverStore &c, int V, int x, int b, int m)
+    {
+        const float4 v = __ldg(c.cdf + (size_t)(b * 18 + 3 + m) * V + x);
+        return {df(v.x, v.y), df(v.z, v.w)};
+    }
+    static __device__ __forceinline__ void load_clover(const CloverStore &c, int V, int x, int b, df r[36])
+    {
+        const float4 *p = c.cdf + (size_t)b * 18 * V + x;
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {
+            const float4 v = __ldg(p + (size_t)k * V);
+            r[2 * k] = df(v.x, v.y);
+            r[2 * k + 1] = df(v.z, v.w);
+        }
+    }
+};
+
 struct P16 {
     using real = float;
+    static constexpr int kCaps = 3;   // cap 1: 64 registers, cap 2: 85
+    static constexpr int kCap1MinBlocks = 4;
+    static constexpr int kEoMinBlocks = 1;
     // stored (unit-scaled) values; returns the site's scale, to be folded
     // into a later coefficient instead of multiplying all 24 components
     static __device__ __forceinline__ float load_spinor_raw(const void *d, const float *nrm, int V, int x,

@@ -98,6 +98,21 @@ __device__ __forceinline__ void apply_site_at(const Geom &g, int x, const GaugeS
     int c[4];
     site_coords(g, x, c);
     cx<R> acc[12];
+    if constexpr (std::is_same<P, PDF>::value) {   // compact form (instruction cache)
+        if (KIND == 2) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k] = mkc(R(0.0f, 0.0f), R(0.0f, 0.0f));
+        } else {
+            cx<R> p[12];
+            P::load_spinor(in, in_nrm, g.V, x, p);
+            clover_block_rt<P>(C, g.V, x, 0, p, acc);
+            clover_block_rt<P>(C, g.V, x, 1, p + 6, acc + 6);
+        }
+        const R k = KIND == 2 ? R(1.0) : R(-kappa);
+        hops_rt<P, KIND == 1 ? +1 : -1>(g, U, in, in_nrm, g.V, x, c, k, acc, [](int y) { return y; });
+        P::store_spinor(out, out_nrm, g.V, x, acc);
+        return;
+    }
     if (KIND == 2) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = mkc(R(0), R(0));
@@ -211,9 +226,10 @@ constexpr ApplyShape kShapes[] = {
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-bool shape_fits(const Geom &g, const ApplyShape &s, bool fp64)
+// caps: bit c-1 set if register cap c is compiled for the operator (P::kCaps)
+bool shape_fits(const Geom &g, const ApplyShape &s, int caps)
 {
-    if (fp64 && s.capped) return false;   // the FP64 operator is ALU-bound: no register cap
+    if (s.capped && !((caps >> (s.capped - 1)) & 1)) return false;
     if (s.tile[0] == 0) return true;
     for (int m = 0; m < 4; ++m)
         if (g.L[m] % s.tile[m] != 0) return false;
@@ -276,19 +292,20 @@ cudaError_t launch_shape(wc_lattice lat, wc_field out, wc_field in, int kind, co
         kern<<<grid, sh.threads, 0, stream>>>(g, tm, nlogical, lat->gauge, lat->clover, in->data, in->nrm,    \
                                               out->data, out->nrm, lat->kappa, 0);                            \
     } while (0)
-    constexpr bool cap_ok = !std::is_same<P, P64>::value;
-    constexpr int MB64 = cap_ok ? 4 : 1, MB85 = cap_ok ? 3 : 1;
+    // minimum resident CTAs of 256 threads for caps 1 and 2 (1: not compiled)
+    constexpr bool c1 = P::kCaps & 1, c2 = P::kCaps & 2;
+    constexpr int MB1 = c1 ? P::kCap1MinBlocks : 1, MB2 = c2 ? 3 : 1;
     if (kind == 0) {
-        if (cap_ok && sh.capped == 1) WC_LAUNCH(0, MB64);
-        else if (cap_ok && sh.capped == 2) WC_LAUNCH(0, MB85);
+        if (c1 && sh.capped == 1) WC_LAUNCH(0, MB1);
+        else if (c2 && sh.capped == 2) WC_LAUNCH(0, MB2);
         else WC_LAUNCH(0, 1);
     } else if (kind == 1) {
-        if (cap_ok && sh.capped == 1) WC_LAUNCH(1, MB64);
-        else if (cap_ok && sh.capped == 2) WC_LAUNCH(1, MB85);
+        if (c1 && sh.capped == 1) WC_LAUNCH(1, MB1);
+        else if (c2 && sh.capped == 2) WC_LAUNCH(1, MB2);
         else WC_LAUNCH(1, 1);
     } else {
-        if (cap_ok && sh.capped == 1) WC_LAUNCH(2, MB64);
-        else if (cap_ok && sh.capped == 2) WC_LAUNCH(2, MB85);
+        if (c1 && sh.capped == 1) WC_LAUNCH(2, MB1);
+        else if (c2 && sh.capped == 2) WC_LAUNCH(2, MB2);
         else WC_LAUNCH(2, 1);
     }
 #undef WC_LAUNCH
@@ -315,7 +332,7 @@ int tune_shape(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t
     for (int i = 0; i < kNumShapes; ++i) best_ms[i] = 1e30f;
     for (int round = 0; round < 2; ++round) {
         for (int i = 0; i < kNumShapes; ++i) {
-            if (!shape_fits(lat->g, kShapes[i], std::is_same<P, P64>::value)) continue;
+            if (!shape_fits(lat->g, kShapes[i], P::kCaps)) continue;
             if (launch_shape<P>(lat, out, in, kind, kShapes[i], stream) != cudaSuccess) continue;
             cudaEventRecord(e0, stream);
             for (int r = 0; r < 8; ++r) launch_shape<P>(lat, out, in, kind, kShapes[i], stream);
@@ -338,7 +355,9 @@ int tune_shape(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t
 template <class P>
 cudaError_t launch_apply_p(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t stream)
 {
-    const std::array<int, 6> key = {lat->g.L[0], lat->g.L[1], lat->g.L[2], lat->g.L[3], (int)in->prec, kind};
+    // the double-FP32 operator has its own entry (precision code 3)
+    const int pcode = std::is_same<P, PDF>::value ? 3 : (int)in->prec;
+    const std::array<int, 6> key = {lat->g.L[0], lat->g.L[1], lat->g.L[2], lat->g.L[3], pcode, kind};
     int choice = -1;
     {
         std::lock_guard<std::mutex> lk(g_shape_mutex);
@@ -413,11 +432,14 @@ cudaError_t launch_copy_s(wc_lattice lat, wc_field dst, wc_field src, double sca
 // all -1 when no shape was chosen yet.
 bool apply_shape(wc_lattice lat, wc_prec prec, int kind, int force, int out[6])
 {
-    const std::array<int, 6> key = {lat->g.L[0], lat->g.L[1], lat->g.L[2], lat->g.L[3], (int)prec, kind};
+    // FP64 fields on a lattice in double-FP32 mode use that operator's entry
+    const int pcode = (prec == WC_F64 && lat->fp64_arith == WC_ARITH_DF32) ? 3 : (int)prec;
+    const std::array<int, 6> key = {lat->g.L[0], lat->g.L[1], lat->g.L[2], lat->g.L[3], pcode, kind};
     for (int i = 0; i < 6; ++i) out[i] = -1;
     std::lock_guard<std::mutex> lk(g_shape_mutex);
     if (force >= 0) {
-        if (force >= kNumShapes || !shape_fits(lat->g, kShapes[force], prec == WC_F64)) return false;
+        const int caps = prec != WC_F64 ? P32::kCaps : pcode == 3 ? PDF::kCaps : P64::kCaps;
+        if (force >= kNumShapes || !shape_fits(lat->g, kShapes[force], caps)) return false;
         g_shape_choice[key] = force;
     }
     auto it = g_shape_choice.find(key);
@@ -435,7 +457,9 @@ cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind, cu
 {
     if (lat->schur_parent) return launch_schur(lat, out, in, kind == 1, stream);   // half lattice: M^
     switch (in->prec) {
-    case WC_F64: return launch_apply_p<P64>(lat, out, in, kind, stream);
+    case WC_F64:
+        return lat->fp64_arith == WC_ARITH_DF32 ? launch_apply_p<PDF>(lat, out, in, kind, stream)
+                                                : launch_apply_p<P64>(lat, out, in, kind, stream);
     case WC_F32: return launch_apply_p<P32>(lat, out, in, kind, stream);
     default: return launch_apply_p<P16>(lat, out, in, kind, stream);
     }

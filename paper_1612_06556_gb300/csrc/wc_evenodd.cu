@@ -113,7 +113,11 @@ __device__ bool invert6(cx<double> a[6][6])
 __device__ void store_block(const CloverStore &S, int V, int pos, int b, const double r[36])
 {
 #pragma unroll
-    for (int q = 0; q < 18; ++q) S.c64[((size_t)b * 18 + q) * V + pos] = make_double2(r[2 * q], r[2 * q + 1]);
+    for (int q = 0; q < 18; ++q) {
+        const double2 v = make_double2(r[2 * q], r[2 * q + 1]);
+        S.c64[((size_t)b * 18 + q) * V + pos] = v;
+        S.cdf[((size_t)b * 18 + q) * V + pos] = df_pack(v);
+    }
 #pragma unroll
     for (int q = 0; q < 9; ++q)
         S.c32[((size_t)b * 9 + q) * V + pos] =
@@ -202,11 +206,22 @@ __device__ __forceinline__ void eo_hop_dir(const Geom &g, const GaugeStore &U, c
     }
 }
 
-template <class R>
-__device__ __forceinline__ void clover_apply(const R r0[36], const R r1[36], const cx<R> v[12], cx<R> y[12])
+// y = A v at position pos of a parity-ordered clover store (A or A^-1)
+template <class P>
+__device__ __forceinline__ void clover_eo(const CloverStore &S, int V, int pos, const cx<typename P::real> v[12],
+                                          cx<typename P::real> y[12])
 {
-    clover_block_mul(r0, v, y);
-    clover_block_mul(r1, v + 6, y + 6);
+    if constexpr (std::is_same<P, PDF>::value) {   // compact form (instruction cache)
+        clover_block_rt<P>(S, V, pos, 0, v, y);
+        clover_block_rt<P>(S, V, pos, 1, v + 6, y + 6);
+    } else {
+        using R = typename P::real;
+        R r0[36], r1[36];
+        P::load_clover(S, V, pos, 0, r0);
+        P::load_clover(S, V, pos, 1, r1);
+        clover_block_mul(r0, v, y);
+        clover_block_mul(r1, v + 6, y + 6);
+    }
 }
 
 // For the sites of parity p (half index i):
@@ -218,7 +233,7 @@ __device__ __forceinline__ void clover_apply(const R r0[36], const R r1[36], con
 //        3: out = Cinv (vin + beta h)
 //        4: out = Cinv vin
 template <class P, int DAG, int MODE>
-__global__ void __launch_bounds__(128) k_eo(Geom g, int p, GaugeStore U, CloverStore C, CloverStore Ci,
+__global__ void __launch_bounds__(128, P::kEoMinBlocks) k_eo(Geom g, int p, GaugeStore U, CloverStore C, CloverStore Ci,
                                             const void *hin, const float *hin_nrm, const void *vin,
                                             const float *vin_nrm, void *out, float *out_nrm, double beta)
 {
@@ -231,7 +246,10 @@ __global__ void __launch_bounds__(128) k_eo(Geom g, int p, GaugeStore U, CloverS
     cx<R> h[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) h[k] = mkc(R(0), R(0));
-    if (MODE != 4) {
+    if constexpr (std::is_same<P, PDF>::value) {   // compact form (instruction cache)
+        if (MODE != 4)
+            hops_rt<P, DAG ? +1 : -1>(g, U, hin, hin_nrm, Vh, x, c, R(1.0), h, [](int y) { return y >> 1; });
+    } else if (MODE != 4) {
         constexpr int SF = DAG ? +1 : -1;
         constexpr int SB = -SF;
         const R one = R(1);
@@ -248,10 +266,7 @@ __global__ void __launch_bounds__(128) k_eo(Geom g, int p, GaugeStore U, CloverS
     } else {
         P::load_spinor(vin, vin_nrm, Vh, i, v);
         if (MODE == 1) {
-            R r0[36], r1[36];
-            P::load_clover(C, g.V, p * Vh + i, 0, r0);
-            P::load_clover(C, g.V, p * Vh + i, 1, r1);
-            clover_apply(r0, r1, v, o);
+            clover_eo<P>(C, g.V, p * Vh + i, v, o);
 #pragma unroll
             for (int k = 0; k < 12; ++k) o[k] = o[k] + bt * h[k];
             P::store_spinor(out, out_nrm, Vh, i, o);
@@ -265,10 +280,7 @@ __global__ void __launch_bounds__(128) k_eo(Geom g, int p, GaugeStore U, CloverS
             return;
         }
     }
-    R r0[36], r1[36];
-    P::load_clover(Ci, g.V, p * Vh + i, 0, r0);
-    P::load_clover(Ci, g.V, p * Vh + i, 1, r1);
-    clover_apply(r0, r1, v, o);
+    clover_eo<P>(Ci, g.V, p * Vh + i, v, o);
     P::store_spinor(out, out_nrm, Vh, i, o);
 }
 
@@ -340,6 +352,9 @@ cudaError_t launch_eo(const wc_lattice_s *full, int parity, int mode, int dagger
                       const wc_field_s *vin, wc_field_s *out, double beta, cudaStream_t stream)
 {
     const wc_prec pr = out->prec;
+    if (pr == WC_F64 && full->fp64_arith == WC_ARITH_DF32)
+        return dagger ? launch_eo_p<PDF, 1>(full, parity, mode, hin, vin, out, beta, stream)
+                      : launch_eo_p<PDF, 0>(full, parity, mode, hin, vin, out, beta, stream);
     if (pr == WC_F64)
         return dagger ? launch_eo_p<P64, 1>(full, parity, mode, hin, vin, out, beta, stream)
                       : launch_eo_p<P64, 0>(full, parity, mode, hin, vin, out, beta, stream);
@@ -409,6 +424,8 @@ wc_status build_clover_inverse(wc_lattice lat)
     for (CloverStore *c : {&lat->cinv, &lat->ceo}) {
         if (c->c64) continue;
         st = check_cuda(lat, cudaMalloc(&c->c64, sizeof(double2) * 36 * (size_t)V), "cudaMalloc(clover inverse)");
+        if (st == WC_OK)
+            st = check_cuda(lat, cudaMalloc(&c->cdf, sizeof(float4) * 36 * (size_t)V), "cudaMalloc(clover inverse)");
         if (st == WC_OK)
             st = check_cuda(lat, cudaMalloc(&c->c32, sizeof(float4) * 18 * (size_t)V), "cudaMalloc(clover inverse)");
         if (st == WC_OK)

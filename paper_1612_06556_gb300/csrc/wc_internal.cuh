@@ -63,6 +63,7 @@ struct wc_lattice_s {
     bool gauge_loaded = false;
     bool clover_loaded = false;
     double csw = 0.0, kappa = 0.0;
+    int fp64_arith = WC_ARITH_F64;            // arithmetic of the FP64 operator kernels
     wc::GaugeStore gauge;
     wc::CloverStore clover;
     wc::SolverState st;                       // scratch of single-RHS calls

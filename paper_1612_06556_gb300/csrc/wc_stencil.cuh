@@ -17,6 +17,13 @@
 
 namespace wc {
 
+// S * a for S = +-1, without a multiplication (exact in every arithmetic)
+template <int S, class T>
+__device__ __forceinline__ T sgn(T a)
+{
+    return S > 0 ? a : -a;
+}
+
 // Two-spinor h of (1 + S gamma_mu) psi, reading the four spin components of
 // one colour at a time through ldc(c, u0, u1, d0, d1) (spins 0..3 of
 // colour c).
@@ -27,19 +34,18 @@ __device__ __forceinline__ void project_from(LoadColour ldc, cx<R> h[6])
     for (int c = 0; c < 3; ++c) {
         cx<R> u0, u1, d0, d1;
         ldc(c, u0, u1, d0, d1);
-        const R s = R(S);
         if (MU == 0) {
-            h[c] = u0 + s * times_i(d1);
-            h[3 + c] = u1 + s * times_i(d0);
+            h[c] = u0 + sgn<S>(times_i(d1));
+            h[3 + c] = u1 + sgn<S>(times_i(d0));
         } else if (MU == 1) {
-            h[c] = u0 + s * d1;
-            h[3 + c] = u1 - s * d0;
+            h[c] = u0 + sgn<S>(d1);
+            h[3 + c] = u1 - sgn<S>(d0);
         } else if (MU == 2) {
-            h[c] = u0 + s * times_i(d0);
-            h[3 + c] = u1 - s * times_i(d1);
+            h[c] = u0 + sgn<S>(times_i(d0));
+            h[3 + c] = u1 - sgn<S>(times_i(d1));
         } else {
-            h[c] = u0 + s * d0;
-            h[3 + c] = u1 + s * d1;
+            h[c] = u0 + sgn<S>(d0);
+            h[3 + c] = u1 + sgn<S>(d1);
         }
     }
 }
@@ -63,21 +69,20 @@ __device__ __forceinline__ void reconstruct_add(cx<R> acc[12], const cx<R> w[6])
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const cx<R> w0 = w[c], w1 = w[3 + c];
-        const R s = R(S);
         acc[c] = acc[c] + w0;
         acc[3 + c] = acc[3 + c] + w1;
         if (MU == 0) {
-            acc[6 + c] = acc[6 + c] - s * times_i(w1);
-            acc[9 + c] = acc[9 + c] - s * times_i(w0);
+            acc[6 + c] = acc[6 + c] - sgn<S>(times_i(w1));
+            acc[9 + c] = acc[9 + c] - sgn<S>(times_i(w0));
         } else if (MU == 1) {
-            acc[6 + c] = acc[6 + c] - s * w1;
-            acc[9 + c] = acc[9 + c] + s * w0;
+            acc[6 + c] = acc[6 + c] - sgn<S>(w1);
+            acc[9 + c] = acc[9 + c] + sgn<S>(w0);
         } else if (MU == 2) {
-            acc[6 + c] = acc[6 + c] - s * times_i(w0);
-            acc[9 + c] = acc[9 + c] + s * times_i(w1);
+            acc[6 + c] = acc[6 + c] - sgn<S>(times_i(w0));
+            acc[9 + c] = acc[9 + c] + sgn<S>(times_i(w1));
         } else {
-            acc[6 + c] = acc[6 + c] + s * w0;
-            acc[9 + c] = acc[9 + c] + s * w1;
+            acc[6 + c] = acc[6 + c] + sgn<S>(w0);
+            acc[9 + c] = acc[9 + c] + sgn<S>(w1);
         }
     }
 }
@@ -124,6 +129,145 @@ __device__ __forceinline__ void su3_adj_mul(const cx<R> u[6], const cx<R> r2[3],
         w[3 * s] = coef * y0;
         w[3 * s + 1] = coef * y1;
         w[3 * s + 2] = coef * y2;
+    }
+}
+
+}  // namespace wc
+
+namespace wc {
+
+// ---- compact forms for the double-FP32 operator ------------------------
+// A double-FP32 site costs ~20 k instructions; written out per direction
+// (as the FP32/FP16/FP64 kernels are) the code no longer fits the
+// instruction cache (ncu: half of the fetches miss, 65 % of the stalls are
+// "no instruction").  These forms run the eight hops and the clover rows as
+// loops with a runtime index, so that one copy of the SU(3) product and of
+// the clover row is in the code.
+
+template <class R>
+__device__ __forceinline__ void project_rt(int mu, int s, const cx<R> p[12], cx<R> h[6])
+{
+    switch (2 * mu + (s > 0)) {
+    case 0: project<0, -1>(p, h); break;
+    case 1: project<0, 1>(p, h); break;
+    case 2: project<1, -1>(p, h); break;
+    case 3: project<1, 1>(p, h); break;
+    case 4: project<2, -1>(p, h); break;
+    case 5: project<2, 1>(p, h); break;
+    case 6: project<3, -1>(p, h); break;
+    default: project<3, 1>(p, h);
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void reconstruct_add_rt(int mu, int s, cx<R> acc[12], const cx<R> w[6])
+{
+    switch (2 * mu + (s > 0)) {
+    case 0: reconstruct_add<0, -1>(acc, w); break;
+    case 1: reconstruct_add<0, 1>(acc, w); break;
+    case 2: reconstruct_add<1, -1>(acc, w); break;
+    case 3: reconstruct_add<1, 1>(acc, w); break;
+    case 4: reconstruct_add<2, -1>(acc, w); break;
+    case 5: reconstruct_add<2, 1>(acc, w); break;
+    case 6: reconstruct_add<3, -1>(acc, w); break;
+    default: reconstruct_add<3, 1>(acc, w);
+    }
+}
+
+// w = coef * W h with W = U (adj false) or U^+ (adj true), one spin per
+// iteration of a runtime loop
+template <class R>
+__device__ __forceinline__ void su3_mul_rt(bool adj, const cx<R> u[6], const cx<R> r2[3], const cx<R> h[6], R coef,
+                                           cx<R> w[6])
+{
+    cx<R> m[9];
+    const cx<R> rows[9] = {u[0], u[1], u[2], u[3], u[4], u[5], r2[0], r2[1], r2[2]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) m[3 * i + j] = adj ? conj(rows[3 * j + i]) : rows[3 * i + j];
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+        const cx<R> a = s ? h[3] : h[0], b = s ? h[4] : h[1], c = s ? h[5] : h[2];
+        cx<R> y[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            y[i] = m[3 * i] * a;
+            y[i] = cfma(m[3 * i + 1], b, y[i]);
+            y[i] = cfma(m[3 * i + 2], c, y[i]);
+            y[i] = coef * y[i];
+        }
+        if (s) {
+            w[3] = y[0];
+            w[4] = y[1];
+            w[5] = y[2];
+        } else {
+            w[0] = y[0];
+            w[1] = y[1];
+            w[2] = y[2];
+        }
+    }
+}
+
+// The eight hops of site x (coordinates c) added to acc: acc += k sum_mu
+// [W_fwd (1 + SF g_mu) in(x+mu) + W_bwd (1 - SF g_mu) in(x-mu)], the
+// neighbour spinor read at sidx(y) of a field of Vin sites.
+template <class P, int SF, class SiteIdx>
+__device__ __forceinline__ void hops_rt(const Geom &g, const GaugeStore &U, const void *in, const float *in_nrm,
+                                        int Vin, int x, const int c[4], typename P::real k,
+                                        cx<typename P::real> acc[12], SiteIdx sidx)
+{
+    using R = typename P::real;
+    unsigned wf = 0, wb = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (c[m] == g.L[m] - 1) wf |= 1u << m;
+        if (c[m] == 0) wb |= 1u << m;
+    }
+#pragma unroll 1
+    for (int hop = 0; hop < 8; ++hop) {
+        const int mu = hop >> 1;
+        const bool fwd = (hop & 1) == 0;
+        const int L = g.L[mu], st = g.stride[mu];
+        const bool wrap = ((fwd ? wf : wb) >> mu) & 1u;
+        const int y = fwd ? (wrap ? x - (L - 1) * st : x + st) : (wrap ? x + (L - 1) * st : x - st);
+        cx<R> p[12], h[6], u[6], r2[3], w[6];
+        const R scale = P::load_spinor_raw(in, in_nrm, Vin, sidx(y), p);
+        const R coef = ((mu == 3 && wrap) ? k * R(g.tbc) : k) * scale;
+        const int s = fwd ? SF : -SF;
+        project_rt(mu, s, p, h);
+        P::load_link(U, g.V, mu, fwd ? x : y, u, r2);
+        su3_mul_rt(!fwd, u, r2, h, coef, w);
+        reconstruct_add_rt(mu, s, acc, w);
+    }
+}
+
+// y = A v for clover block b of the packed store (rows in a runtime loop;
+// each row reads its six entries: diagonal, lower (i, j) and the conjugate
+// of lower (j, i))
+template <class P>
+__device__ __forceinline__ void clover_block_rt(const CloverStore &C, int V, int x, int b,
+                                                const cx<typename P::real> v[6], cx<typename P::real> y[6])
+{
+    using R = typename P::real;
+#pragma unroll 1
+    for (int i = 0; i < 6; ++i) {
+        cx<R> acc = mkc(R(0.0f, 0.0f), R(0.0f, 0.0f));
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            cx<R> e;
+            if (j == i) {
+                e = cx<R>{P::clover_real(C, V, x, b, i), R(0.0f, 0.0f)};
+            } else {
+                const int hi = i > j ? i : j, lo = i > j ? j : i;
+                const cx<R> l = P::clover_lower(C, V, x, b, hi * (hi - 1) / 2 + lo);
+                e = j < i ? l : conj(l);
+            }
+            acc = cfma(e, v[j], acc);
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+            if (r == i) y[r] = acc;
     }
 }
 
