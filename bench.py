@@ -52,8 +52,8 @@ NCU_TRAFFIC = {
     # the other lexicographic shapes run the same kernel body), from the
     # capture summarised in profiles/apply_fp32_24x24x24x32.md; valid while
     # the operator's device sources hash to sources_sha
-    "sources_sha": "5a93cb3e6d6f971d",
-    "bytes_per_launch": 293898496,
+    "sources_sha": "80b055bc73884d5c",
+    "bytes_per_launch": 294333184,
 }
 
 
@@ -264,22 +264,27 @@ def run_ours(args, world, rank, local):
         ms = e0.elapsed_time(e1)
         ms = max_over_ranks(ms)
         # end to end through the public API with host buffers: canonical
-        # complex128 in (pinned) -> import -> apply -> export -> host
-        host_in = torch.from_numpy(src).pin_memory()
-        host_out = torch.empty_like(host_in).pin_memory()
+        # complex64 in (pinned, the FP32 apply's own precision) -> import ->
+        # apply -> export -> host; the complex128 round trip beside it
         fin, fout = lat.field(wc.F32), lat.field(wc.F32)
-        for _ in range(2):
-            fin.load(host_in)
-            lat.apply_M(fout, fin)
-            fout.store(host_out)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            fin.load(host_in)
-            lat.apply_M(fout, fin)
-            fout.store(host_out)
-        torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(1000 * (time.perf_counter() - t0) / args.e2e_steps)
+
+        def e2e(host_in):
+            host_out = torch.empty_like(host_in).pin_memory()
+            for _ in range(2):
+                fin.load(host_in)
+                lat.apply_M(fout, fin)
+                fout.store(host_out)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                fin.load(host_in)
+                lat.apply_M(fout, fin)
+                fout.store(host_out)
+            torch.cuda.synchronize()
+            return max_over_ranks(1000 * (time.perf_counter() - t0) / args.e2e_steps)
+
+        e2e_ms = e2e(torch.from_numpy(src.astype(np.complex64)).pin_memory())
+        e2e128_ms = e2e(torch.from_numpy(src).pin_memory())
         solve = solve_comparison(wc, lat, src, args) if not args.skip_solves else None
     clk = clocks.summary()
     shape = lat.apply_shape(wc.F32, 0)
@@ -320,8 +325,9 @@ def run_ours(args, world, rank, local):
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_alg,
                      "same_size_copy_gbs": copy_gbs, "frac_of_same_size_copy": achieved / copy_gbs},
         "e2e": {"value": whole_job_rate(flops, world, e2e_ms) / 1e9, "unit": "GFlop/s",
-                "h2d_bytes_per_step": V * 12 * 16, "d2h_bytes_per_step": V * 12 * 16,
-                "ms_per_step": e2e_ms},
+                "h2d_bytes_per_step": V * 12 * 8, "d2h_bytes_per_step": V * 12 * 8,
+                "ms_per_step": e2e_ms, "host_data": "complex64",
+                "complex128_ms_per_step": e2e128_ms},
         "gpu_launches": args.steps,
         "clocks": clk,
     }
@@ -437,6 +443,13 @@ def batch_comparison(wc, args):
                              delta=0.01, krylov_prec=wc.F16, even_odd=True)
     run_batch(eo_h16)
     infos_eo_h16, t_eo_h16 = run_batch(eo_h16)
+    # the same with the FP64 operator steps in double-FP32 arithmetic
+    for lat in lats[::12]:
+        lat.set_fp64_arith(wc.ARITH_DF32)
+    run_batch(eo_h16)
+    infos_eo_h16_df, t_eo_h16_df = run_batch(eo_h16)
+    for lat in lats[::12]:
+        lat.set_fp64_arith(wc.ARITH_F64)
     eo_ras = wc.solve_params(tol=1e-10, max_iter=5000, precond=wc.PRECOND_RAS, inner_prec=wc.F32,
                              block=(4, 4, 4, 4), solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True)
     run_batch(eo_ras)
@@ -470,6 +483,8 @@ def batch_comparison(wc, args):
             "even_odd_sequential_seconds": t_seq_eo, "even_odd_sequential_all_ok": all(i.status == 0 for i in seq_eo),
             "even_odd_fp16_vectors_batch_seconds": t_eo_h16,
             "even_odd_fp16_vectors_all_ok": all(i.status == 0 for i in infos_eo_h16),
+            "even_odd_fp16_vectors_df32_batch_seconds": t_eo_h16_df,
+            "even_odd_fp16_vectors_df32_all_ok": all(i.status == 0 for i in infos_eo_h16_df),
             "even_odd_ras_batch_seconds": t_eo_ras, "even_odd_ras_all_ok": all(i.status == 0 for i in infos_eo_ras),
             "even_odd_ras_steps": [min(i.iters for i in infos_eo_ras), max(i.iters for i in infos_eo_ras)],
             "even_odd_steps": [min(i.iters for i in infos_eo), max(i.iters for i in infos_eo)],
@@ -681,7 +696,10 @@ def force_timing(wc, args):
             ("flexible_ras", dict(tol=1e-12, precond=wc.PRECOND_RAS, inner_prec=wc.F32),
              "FP64 flexible BiCGStab + FP32 RAS"),
             ("eo_reliable", dict(tol=1e-12, precond=wc.PRECOND_NONE, even_odd=True, solver=wc.SOLVER_RELIABLE),
-             "even-odd FP32 BiCGStab with FP64 reliable updates")):
+             "even-odd FP32 BiCGStab with FP64 reliable updates"),
+            ("eo_reliable_df32", dict(tol=1e-12, precond=wc.PRECOND_NONE, even_odd=True, solver=wc.SOLVER_RELIABLE),
+             "even-odd FP32 BiCGStab with reliable updates, FP64 operator steps in double-FP32")):
+        lat.set_fp64_arith(wc.ARITH_DF32 if name.endswith("_df32") else wc.ARITH_F64)
         lat.action_force(f_phi, F, **kw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -8,7 +8,10 @@
  * an FP32/FP16-storage overlapped Restricted Additive Schwarz (RAS)
  * preconditioner whose blocks are solved inside CTAs, as FP32/FP16
  * BiCGStab with FP64 reliable updates, or as the three-level nested solver,
- * each on the full lattice or on its even-odd Schur complement.  This is the
+ * each on the full lattice or on its even-odd Schur complement; the FP64
+ * operator steps may run in double-FP32 arithmetic on the FP32 pipes
+ * (wc_set_fp64_arith), since GB300 executes FP64 at 1/64 of its FP32 rate.
+ * This is the
  * solver stack of the paper's CCS-QCD benchmark (Sec. 2: double-precision
  * flexible BiCGStab, single-precision preconditioner, even-odd and
  * overlapped RAS preconditioning, SU(3) reconstruction; Sec. 3: the hopping
@@ -27,7 +30,8 @@
  *     anti-Hermitian part of the four-leaf clover sum divided by 8
  *
  * Canonical (caller-side) layouts, all complex128 = interleaved (re, im)
- * doubles in C order:
+ * doubles in C order (spinors may also be passed as complex64 through
+ * wc_field_import_f32 / wc_field_export_f32):
  *   gauge   U[Lt][Lz][Ly][Lx][mu][3][3]   (row, column)
  *   spinor  psi[Lt][Lz][Ly][Lx][spin 4][colour 3]
  *   force   F[Lt][Lz][Ly][Lx][mu][3][3]
@@ -197,6 +201,13 @@ wc_status wc_field_destroy(wc_field f);
 wc_status wc_field_import(wc_field f, const double *data);
 /* field -> canonical complex128 (device or host).  Same rules. */
 wc_status wc_field_export(wc_field f, double *data);
+/* The same with canonical complex64 data (float pairs, psi[V][4][3]), device
+ * or host: half the bytes of complex128 across the host link, for callers
+ * whose data is single precision.  Import widens (FP64 field) or rounds
+ * (FP16 field); export of an FP64 field rounds to nearest FP32.  Same
+ * synchronisation and error rules as the complex128 calls. */
+wc_status wc_field_import_f32(wc_field f, const float *data);
+wc_status wc_field_export_f32(wc_field f, float *data);
 /* dst = src converted to dst's precision, times scale (any precisions). */
 wc_status wc_field_copy(wc_field dst, wc_field src, double scale);
 

@@ -40,7 +40,7 @@ EXPORTED = [
     "wc_apply_M", "wc_apply_Mdag", "wc_apply_hop", "wc_dot", "wc_norm2", "wc_axpy_norm",
     "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
     "wc_dot_noalloc", "wc_ras_autotune", "wc_apply_shape", "wc_apply_schur", "wc_apply_multi",
-    "wc_force_times_links", "wc_set_fp64_arith",
+    "wc_force_times_links", "wc_set_fp64_arith", "wc_field_import_f32", "wc_field_export_f32",
 ]
 
 
@@ -78,6 +78,8 @@ _L.wc_field_create.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(_vp)]
 _L.wc_field_destroy.argtypes = [_vp]
 _L.wc_field_import.argtypes = [_vp, _vp]
 _L.wc_field_export.argtypes = [_vp, _vp]
+_L.wc_field_import_f32.argtypes = [_vp, _vp]
+_L.wc_field_export_f32.argtypes = [_vp, _vp]
 _L.wc_field_copy.argtypes = [_vp, _vp, ctypes.c_double]
 for _n in ("wc_apply_M", "wc_apply_Mdag", "wc_apply_hop"):
     getattr(_L, _n).argtypes = [_vp, _vp, _vp]
@@ -131,6 +133,26 @@ def _nbytes(a):
     return a.numel() * 16 if hasattr(a, "numel") else a.size * 16
 
 
+def _is_c64(a) -> bool:
+    """True for a complex64 torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        return a.dtype == torch.complex64
+    import numpy as np
+    return getattr(a, "dtype", None) == np.complex64
+
+
+def _ptr64(a):
+    """Data pointer of a C-contiguous complex64 torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("expected a contiguous complex64 tensor")
+        return a.data_ptr()
+    if not a.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous complex64 array")
+    return a.ctypes.data
+
+
 def ras_params(block=(4, 4, 4, 4), overlap=1, mr_iters=4) -> RasParams:
     return RasParams((ctypes.c_int * 4)(*block), int(overlap), int(mr_iters))
 
@@ -154,19 +176,26 @@ class Field:
         self.handle = h
 
     def _size_ok(self, a):
-        if _nbytes(a) != self.lattice.volume * 12 * 16:
-            raise ValueError(f"spinor buffer must hold {self.lattice.volume}*12 complex128")
+        n = a.numel() if hasattr(a, "numel") else a.size
+        if n != self.lattice.volume * 12:
+            raise ValueError(f"spinor buffer must hold {self.lattice.volume}*12 complex values")
 
     def load(self, psi):
-        """Import canonical complex128 psi[V,4,3] (device or host)."""
+        """Import canonical psi[V,4,3], complex128 or complex64 (device or host)."""
         self._size_ok(psi)
-        _check(_L.wc_field_import(self.handle, _vp(_ptr(psi))), self.lattice.handle)
+        if _is_c64(psi):
+            _check(_L.wc_field_import_f32(self.handle, _vp(_ptr64(psi))), self.lattice.handle)
+        else:
+            _check(_L.wc_field_import(self.handle, _vp(_ptr(psi))), self.lattice.handle)
         return self
 
     def store(self, out):
-        """Export into canonical complex128 out[V,4,3] (device or host)."""
+        """Export into canonical out[V,4,3], complex128 or complex64 (device or host)."""
         self._size_ok(out)
-        _check(_L.wc_field_export(self.handle, _vp(_ptr(out))), self.lattice.handle)
+        if _is_c64(out):
+            _check(_L.wc_field_export_f32(self.handle, _vp(_ptr64(out))), self.lattice.handle)
+        else:
+            _check(_L.wc_field_export(self.handle, _vp(_ptr(out))), self.lattice.handle)
         return out
 
     def copy_from(self, src: "Field", scale: float = 1.0):

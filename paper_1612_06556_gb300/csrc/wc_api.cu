@@ -60,8 +60,9 @@ bool is_device_pointer(const void *p)
 // canonical <-> internal
 // ------------------------------------------------------------------------
 
-template <class P>
-__global__ void k_import(int V, const double2 *src, void *dst, float *nrm)
+// T: double2 (canonical complex128) or float2 (canonical complex64)
+template <class P, class T>
+__global__ void k_import(int V, const T *src, void *dst, float *nrm)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= V) return;
@@ -69,21 +70,22 @@ __global__ void k_import(int V, const double2 *src, void *dst, float *nrm)
     cx<R> s[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        const double2 v = src[(size_t)x * 12 + k];
+        const T v = src[(size_t)x * 12 + k];
         s[k] = mkc((R)v.x, (R)v.y);
     }
     P::store_spinor(dst, nrm, V, x, s);
 }
 
-template <class P>
-__global__ void k_export(int V, const void *src, const float *nrm, double2 *dst)
+template <class P, class T>
+__global__ void k_export(int V, const void *src, const float *nrm, T *dst)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= V) return;
+    using E = decltype(T::x);
     cx<typename P::real> s[12];
     P::load_spinor(src, nrm, V, x, s);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) dst[(size_t)x * 12 + k] = make_double2((double)s[k].re, (double)s[k].im);
+    for (int k = 0; k < 12; ++k) dst[(size_t)x * 12 + k] = T{(E)s[k].re, (E)s[k].im};
 }
 
 // canonical U[V][4][3][3] -> two-row stores in three precisions
@@ -403,6 +405,73 @@ namespace {
 
 using namespace wc;
 
+namespace {
+
+template <class T>
+wc_status field_import(wc_field f, const T *data)
+{
+    if (!f) return set_error(nullptr, WC_ERR_ARG, "field is NULL");
+    wc_lattice lat = f->lat;
+    if (!data) return set_error(lat, WC_ERR_ARG, "data is NULL");
+    const int V = lat->g.V;
+    const size_t bytes = sizeof(T) * 12 * (size_t)V;
+    const T *src = data;
+    wc_status st = WC_OK;
+    const bool host = !is_device_pointer(data);
+    if (host) {
+        st = need_staging(lat, bytes);
+        if (st != WC_OK) return st;
+        st = check_cuda(lat, cudaMemcpyAsync(lat->staging, data, bytes, cudaMemcpyHostToDevice, lat->stream),
+                        "cudaMemcpyAsync(import)");
+        if (st != WC_OK) return st;
+        src = reinterpret_cast<const T *>(lat->staging);
+    }
+    dim3 grid((V + 255) / 256), block(256);
+    if (f->prec == WC_F64)
+        k_import<P64, T><<<grid, block, 0, lat->stream>>>(V, src, f->data, f->nrm);
+    else if (f->prec == WC_F32)
+        k_import<P32, T><<<grid, block, 0, lat->stream>>>(V, src, f->data, f->nrm);
+    else
+        k_import<P16, T><<<grid, block, 0, lat->stream>>>(V, src, f->data, f->nrm);
+    st = check_launch(lat, "import");
+    if (st == WC_OK && host) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync(import)");
+    return st;
+}
+
+template <class T>
+wc_status field_export(wc_field f, T *data)
+{
+    if (!f) return set_error(nullptr, WC_ERR_ARG, "field is NULL");
+    wc_lattice lat = f->lat;
+    if (!data) return set_error(lat, WC_ERR_ARG, "data is NULL");
+    const int V = lat->g.V;
+    const size_t bytes = sizeof(T) * 12 * (size_t)V;
+    const bool host = !is_device_pointer(data);
+    T *dst = data;
+    wc_status st = WC_OK;
+    if (host) {
+        st = need_staging(lat, bytes);
+        if (st != WC_OK) return st;
+        dst = reinterpret_cast<T *>(lat->staging);
+    }
+    dim3 grid((V + 255) / 256), block(256);
+    if (f->prec == WC_F64)
+        k_export<P64, T><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
+    else if (f->prec == WC_F32)
+        k_export<P32, T><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
+    else
+        k_export<P16, T><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
+    st = check_launch(lat, "export");
+    if (st == WC_OK && host) {
+        st = check_cuda(lat, cudaMemcpyAsync(data, lat->staging, bytes, cudaMemcpyDeviceToHost, lat->stream),
+                        "cudaMemcpyAsync(export)");
+        if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync(export)");
+    }
+    return st;
+}
+
+}  // namespace
+
 extern "C" {
 
 wc_status wc_create_lattice(const int dims[4], int t_bc, void *cuda_stream, wc_lattice *out)
@@ -570,63 +639,22 @@ wc_status wc_field_destroy(wc_field f)
 
 wc_status wc_field_import(wc_field f, const double *data)
 {
-    if (!f) return set_error(nullptr, WC_ERR_ARG, "field is NULL");
-    wc_lattice lat = f->lat;
-    if (!data) return set_error(lat, WC_ERR_ARG, "data is NULL");
-    const int V = lat->g.V;
-    const size_t bytes = sizeof(double2) * 12 * (size_t)V;
-    const double2 *src = reinterpret_cast<const double2 *>(data);
-    wc_status st = WC_OK;
-    const bool host = !is_device_pointer(data);
-    if (host) {
-        st = need_staging(lat, bytes);
-        if (st != WC_OK) return st;
-        st = check_cuda(lat, cudaMemcpyAsync(lat->staging, data, bytes, cudaMemcpyHostToDevice, lat->stream),
-                        "cudaMemcpyAsync(import)");
-        if (st != WC_OK) return st;
-        src = lat->staging;
-    }
-    dim3 grid((V + 255) / 256), block(256);
-    if (f->prec == WC_F64)
-        k_import<P64><<<grid, block, 0, lat->stream>>>(V, src, f->data, f->nrm);
-    else if (f->prec == WC_F32)
-        k_import<P32><<<grid, block, 0, lat->stream>>>(V, src, f->data, f->nrm);
-    else
-        k_import<P16><<<grid, block, 0, lat->stream>>>(V, src, f->data, f->nrm);
-    st = check_launch(lat, "import");
-    if (st == WC_OK && host) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync(import)");
-    return st;
+    return field_import(f, reinterpret_cast<const double2 *>(data));
 }
 
 wc_status wc_field_export(wc_field f, double *data)
 {
-    if (!f) return set_error(nullptr, WC_ERR_ARG, "field is NULL");
-    wc_lattice lat = f->lat;
-    if (!data) return set_error(lat, WC_ERR_ARG, "data is NULL");
-    const int V = lat->g.V;
-    const size_t bytes = sizeof(double2) * 12 * (size_t)V;
-    const bool host = !is_device_pointer(data);
-    double2 *dst = reinterpret_cast<double2 *>(data);
-    wc_status st = WC_OK;
-    if (host) {
-        st = need_staging(lat, bytes);
-        if (st != WC_OK) return st;
-        dst = lat->staging;
-    }
-    dim3 grid((V + 255) / 256), block(256);
-    if (f->prec == WC_F64)
-        k_export<P64><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
-    else if (f->prec == WC_F32)
-        k_export<P32><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
-    else
-        k_export<P16><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
-    st = check_launch(lat, "export");
-    if (st == WC_OK && host) {
-        st = check_cuda(lat, cudaMemcpyAsync(data, lat->staging, bytes, cudaMemcpyDeviceToHost, lat->stream),
-                        "cudaMemcpyAsync(export)");
-        if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync(export)");
-    }
-    return st;
+    return field_export(f, reinterpret_cast<double2 *>(data));
+}
+
+wc_status wc_field_import_f32(wc_field f, const float *data)
+{
+    return field_import(f, reinterpret_cast<const float2 *>(data));
+}
+
+wc_status wc_field_export_f32(wc_field f, float *data)
+{
+    return field_export(f, reinterpret_cast<float2 *>(data));
 }
 
 wc_status wc_field_copy(wc_field dst, wc_field src, double scale)

@@ -98,19 +98,38 @@ __device__ __forceinline__ void apply_site_at(const Geom &g, int x, const GaugeS
     int c[4];
     site_coords(g, x, c);
     cx<R> acc[12];
-    if constexpr (std::is_same<P, PDF>::value) {   // compact form (instruction cache)
-        if (KIND == 2) {
+    if constexpr (std::is_same<P, PDF>::value) {
+        // hops in double-FP32 on the FP32 pipes, in the compact form (the
+        // instruction cache); the clover term in FP64 on the FP64 pipe,
+        // which the hops of the other warps leave idle
 #pragma unroll
-            for (int k = 0; k < 12; ++k) acc[k] = mkc(R(0.0f, 0.0f), R(0.0f, 0.0f));
-        } else {
-            cx<R> p[12];
-            P::load_spinor(in, in_nrm, g.V, x, p);
-            clover_block_rt<P>(C, g.V, x, 0, p, acc);
-            clover_block_rt<P>(C, g.V, x, 1, p + 6, acc + 6);
-        }
+        for (int k = 0; k < 12; ++k) acc[k] = mkc(R(0.0f, 0.0f), R(0.0f, 0.0f));
         const R k = KIND == 2 ? R(1.0) : R(-kappa);
         hops_rt<P, KIND == 1 ? +1 : -1>(g, U, in, in_nrm, g.V, x, c, k, acc, [](int y) { return y; });
-        P::store_spinor(out, out_nrm, g.V, x, acc);
+        if (KIND == 2) {
+            P::store_spinor(out, out_nrm, g.V, x, acc);
+            return;
+        }
+        cx<double> ad[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) ad[q] = mkc(df_to_double(acc[q].re), df_to_double(acc[q].im));
+        cx<double> pd[12];
+        P64::load_spinor(in, nullptr, g.V, x, pd);
+#pragma unroll 1
+        for (int b = 0; b < 2; ++b) {
+            double r[36];
+            cx<double> v6[6], y6[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v6[q] = b ? pd[6 + q] : pd[q];
+            P64::load_clover(C, g.V, x, b, r);
+            clover_block_mul(r, v6, y6);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                if (b) ad[6 + q] = ad[6 + q] + y6[q];
+                else ad[q] = ad[q] + y6[q];
+            }
+        }
+        P64::store_spinor(out, out_nrm, g.V, x, ad);
         return;
     }
     if (KIND == 2) {

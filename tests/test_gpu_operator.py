@@ -106,6 +106,40 @@ def test_import_export_memory_kinds():
         assert np.array_equal(out_dev.cpu().numpy(), ref)
 
 
+def test_import_export_complex64():
+    """complex64 import/export (wc_field_import_f32 / _export_f32): exact
+    for FP32 fields, widening into FP64 and rounding out of it, the same
+    FP16 rounding as from complex128, on host and device buffers."""
+    import torch
+    dims = (4, 6, 4, 6)
+    lat = make_lattice(dims, synth.unit_links(dims), 1.0, 0.1, -1)
+    psi = synth.gaussian_source(dims, 5) * np.logspace(-8, 3, synth.volume(dims))[:, None, None]
+    p32 = psi.astype(np.complex64)
+    # FP32 field: bit-exact round trip of complex64 data
+    assert np.array_equal(lat.field(1).load(p32).store(np.zeros_like(p32)), p32)
+    # FP64 field: widened exactly; complex128 export returns the widened values
+    f64 = lat.field(0).load(p32)
+    assert np.array_equal(f64.store(np.zeros_like(psi)), p32.astype(np.complex128))
+    # complex64 export of FP64 data rounds to nearest
+    assert np.array_equal(lat.field(0).load(psi).store(np.zeros_like(p32)), p32)
+    # FP16 field: same stored values whichever width the import came in
+    a = lat.field(2).load(p32).store(np.zeros_like(psi))
+    b = lat.field(2).load(p32.astype(np.complex128)).store(np.zeros_like(psi))
+    assert np.array_equal(a, b)
+    # device and pinned buffers
+    dev = torch.from_numpy(p32).cuda()
+    out = torch.zeros_like(dev)
+    lat.field(1).load(dev).store(out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), p32)
+    pin = torch.from_numpy(p32).pin_memory()
+    outp = torch.zeros_like(pin).pin_memory()
+    lat.field(1).load(pin).store(outp)
+    assert np.array_equal(outp.numpy(), p32)
+    with pytest.raises(ValueError):
+        lat.field(1).load(p32[:-1])
+
+
 def test_gpu_gauge_covariance():
     dims, kappa, csw, tbc = (4, 6, 4, 6), 0.12, 1.5, -1
     U = synth.exp_links(dims, 0.5, 11)
