@@ -52,8 +52,8 @@ NCU_TRAFFIC = {
     # the other lexicographic shapes run the same kernel body), from the
     # capture summarised in profiles/apply_fp32_24x24x24x32.md; valid while
     # the operator's device sources hash to sources_sha
-    "sources_sha": "80b055bc73884d5c",
-    "bytes_per_launch": 294333184,
+    "sources_sha": "70b2bab09f81e2e1",
+    "bytes_per_launch": 294086912,
 }
 
 
@@ -750,6 +750,8 @@ def solve_comparison(wc, lat, src, args):
                                                    even_odd=True)),
                      ("eo_reliable_h16_df32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE,
                                                    delta=0.01, krylov_prec=wc.F16, even_odd=True)),
+                     ("eo_reliable_h16_delta1e-4_df32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE,
+                                                             delta=1e-4, krylov_prec=wc.F16, even_odd=True)),
                      ("eo_nested_h16_df32", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED,
                                                  inner_tol=0.01, inner_iters=100, krylov_prec=wc.F16,
                                                  even_odd=True))):

@@ -99,20 +99,23 @@ __device__ __forceinline__ void apply_site_at(const Geom &g, int x, const GaugeS
     site_coords(g, x, c);
     cx<R> acc[12];
     if constexpr (std::is_same<P, PDF>::value) {
-        // hops in double-FP32 on the FP32 pipes, in the compact form (the
-        // instruction cache); the clover term in FP64 on the FP64 pipe,
-        // which the hops of the other warps leave idle
+        // Six hops (directions y, z, t) in double-FP32 on the FP32 pipes, in
+        // the compact form (the instruction cache); the clover term and the
+        // two x hops in FP64 on the FP64 pipe, which the double-FP32 work of
+        // the other warps leaves idle.
+        constexpr int SF = KIND == 1 ? +1 : -1;
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = mkc(R(0.0f, 0.0f), R(0.0f, 0.0f));
         const R k = KIND == 2 ? R(1.0) : R(-kappa);
-        hops_rt<P, KIND == 1 ? +1 : -1>(g, U, in, in_nrm, g.V, x, c, k, acc, [](int y) { return y; });
-        if (KIND == 2) {
-            P::store_spinor(out, out_nrm, g.V, x, acc);
-            return;
-        }
+        hops_rt<P, SF>(g, U, in, in_nrm, g.V, x, c, k, acc, [](int y) { return y; }, 2);
         cx<double> ad[12];
 #pragma unroll
         for (int q = 0; q < 12; ++q) ad[q] = mkc(df_to_double(acc[q].re), df_to_double(acc[q].im));
+        hop_dir<P64, 0, SF, -SF>(g, U, in, in_nrm, x, c, KIND == 2 ? 1.0 : -kappa, ad);
+        if (KIND == 2) {
+            P64::store_spinor(out, out_nrm, g.V, x, ad);
+            return;
+        }
         cx<double> pd[12];
         P64::load_spinor(in, nullptr, g.V, x, pd);
 #pragma unroll 1
@@ -334,7 +337,7 @@ cudaError_t launch_shape(wc_lattice lat, wc_field out, wc_field in, int kind, co
 std::mutex g_shape_mutex;
 std::map<std::array<int, 6>, int> g_shape_choice;   // (L, prec, kind) -> shape index
 
-// Time every fitting shape (two rounds of 8 launches after one warm-up,
+// Time every fitting shape (three rounds of 16 launches after one warm-up,
 // best round kept, candidates interleaved so that clock drift affects all
 // alike) and keep the fastest.  Needs an uncaptured stream; out is
 // overwritten by the real launch that follows.
@@ -349,12 +352,12 @@ int tune_shape(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t
     }
     float best_ms[kNumShapes];
     for (int i = 0; i < kNumShapes; ++i) best_ms[i] = 1e30f;
-    for (int round = 0; round < 2; ++round) {
+    for (int round = 0; round < 3; ++round) {
         for (int i = 0; i < kNumShapes; ++i) {
             if (!shape_fits(lat->g, kShapes[i], P::kCaps)) continue;
             if (launch_shape<P>(lat, out, in, kind, kShapes[i], stream) != cudaSuccess) continue;
             cudaEventRecord(e0, stream);
-            for (int r = 0; r < 8; ++r) launch_shape<P>(lat, out, in, kind, kShapes[i], stream);
+            for (int r = 0; r < 16; ++r) launch_shape<P>(lat, out, in, kind, kShapes[i], stream);
             cudaEventRecord(e1, stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) continue;
             float ms = 0.f;

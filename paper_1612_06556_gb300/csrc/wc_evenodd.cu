@@ -279,9 +279,9 @@ __global__ void __launch_bounds__(128, P::kEoMinBlocks) k_eo(Geom g, int p, Gaug
     const int x = full_site(g, i, p, c);
     if constexpr (std::is_same<P, PDF>::value) {
         // compact form (instruction cache): hops and clover rows in runtime
-        // loops.  (Doing the site-local A / A^-1 products in FP64 instead,
-        // as the full-lattice kernel does with the clover term, measured
-        // 3 % slower here.)
+        // loops.  (Moving the site-local A / A^-1 products, or the two x
+        // hops, to FP64 as the full-lattice kernel does measured 3 % slower
+        // here: this kernel runs at a fixed 128-register cap.)
         cx<R> h[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) h[k] = mkc(R(0.0f, 0.0f), R(0.0f, 0.0f));

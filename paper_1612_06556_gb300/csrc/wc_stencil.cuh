@@ -209,13 +209,14 @@ __device__ __forceinline__ void su3_mul_rt(bool adj, const cx<R> u[6], const cx<
     }
 }
 
-// The eight hops of site x (coordinates c) added to acc: acc += k sum_mu
-// [W_fwd (1 + SF g_mu) in(x+mu) + W_bwd (1 - SF g_mu) in(x-mu)], the
-// neighbour spinor read at sidx(y) of a field of Vin sites.
+// Hops first..7 of site x (coordinates c; hop 2 mu is the forward, 2 mu + 1
+// the backward hop in direction mu) added to acc: acc += k sum [W_fwd (1 +
+// SF g_mu) in(x+mu) + W_bwd (1 - SF g_mu) in(x-mu)], the neighbour spinor
+// read at sidx(y) of a field of Vin sites.
 template <class P, int SF, class SiteIdx>
 __device__ __forceinline__ void hops_rt(const Geom &g, const GaugeStore &U, const void *in, const float *in_nrm,
                                         int Vin, int x, const int c[4], typename P::real k,
-                                        cx<typename P::real> acc[12], SiteIdx sidx)
+                                        cx<typename P::real> acc[12], SiteIdx sidx, int first = 0)
 {
     using R = typename P::real;
     unsigned wf = 0, wb = 0;
@@ -225,7 +226,7 @@ __device__ __forceinline__ void hops_rt(const Geom &g, const GaugeStore &U, cons
         if (c[m] == 0) wb |= 1u << m;
     }
 #pragma unroll 1
-    for (int hop = 0; hop < 8; ++hop) {
+    for (int hop = first; hop < 8; ++hop) {
         const int mu = hop >> 1;
         const bool fwd = (hop & 1) == 0;
         const int L = g.L[mu], st = g.stride[mu];
