@@ -283,7 +283,27 @@ def run_ours(args, world, rank, local):
             torch.cuda.synchronize()
             return max_over_ranks(1000 * (time.perf_counter() - t0) / args.e2e_steps)
 
-        e2e_ms = e2e(torch.from_numpy(src.astype(np.complex64)).pin_memory())
+        def e2e_pipelined(host_in):
+            # asynchronous calls: the next step's host-to-device copy overlaps
+            # this step's kernels and device-to-host copy
+            host_out = torch.empty_like(host_in).pin_memory()
+            for _ in range(2):
+                fin.load_async(host_in)
+                lat.apply_M(fout, fin)
+                fout.store_async(host_out)
+            lat.sync()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                fin.load_async(host_in)
+                lat.apply_M(fout, fin)
+                fout.store_async(host_out)
+            lat.sync()
+            return max_over_ranks(1000 * (time.perf_counter() - t0) / args.e2e_steps)
+
+        host64 = torch.from_numpy(src.astype(np.complex64)).pin_memory()
+        e2e_ms = e2e_pipelined(host64)
+        e2e_sync_ms = e2e(host64)
         e2e128_ms = e2e(torch.from_numpy(src).pin_memory())
         solve = solve_comparison(wc, lat, src, args) if not args.skip_solves else None
     clk = clocks.summary()
@@ -326,8 +346,9 @@ def run_ours(args, world, rank, local):
                      "same_size_copy_gbs": copy_gbs, "frac_of_same_size_copy": achieved / copy_gbs},
         "e2e": {"value": whole_job_rate(flops, world, e2e_ms) / 1e9, "unit": "GFlop/s",
                 "h2d_bytes_per_step": V * 12 * 8, "d2h_bytes_per_step": V * 12 * 8,
-                "ms_per_step": e2e_ms, "host_data": "complex64",
-                "complex128_ms_per_step": e2e128_ms},
+                "ms_per_step": e2e_ms, "host_data": "complex64, page-locked",
+                "calls": "wc_field_import_async -> wc_apply_M -> wc_field_export_async per step, wc_sync at the end",
+                "synchronous_calls_ms_per_step": e2e_sync_ms, "complex128_synchronous_ms_per_step": e2e128_ms},
         "gpu_launches": args.steps,
         "clocks": clk,
     }

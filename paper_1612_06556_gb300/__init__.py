@@ -41,6 +41,7 @@ EXPORTED = [
     "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
     "wc_dot_noalloc", "wc_ras_autotune", "wc_apply_shape", "wc_apply_schur", "wc_apply_multi",
     "wc_force_times_links", "wc_set_fp64_arith", "wc_field_import_f32", "wc_field_export_f32",
+    "wc_field_import_async", "wc_field_export_async", "wc_sync",
 ]
 
 
@@ -80,6 +81,9 @@ _L.wc_field_import.argtypes = [_vp, _vp]
 _L.wc_field_export.argtypes = [_vp, _vp]
 _L.wc_field_import_f32.argtypes = [_vp, _vp]
 _L.wc_field_export_f32.argtypes = [_vp, _vp]
+_L.wc_field_import_async.argtypes = [_vp, _vp, ctypes.c_int]
+_L.wc_field_export_async.argtypes = [_vp, _vp, ctypes.c_int]
+_L.wc_sync.argtypes = [_vp]
 _L.wc_field_copy.argtypes = [_vp, _vp, ctypes.c_double]
 for _n in ("wc_apply_M", "wc_apply_Mdag", "wc_apply_hop"):
     getattr(_L, _n).argtypes = [_vp, _vp, _vp]
@@ -198,6 +202,25 @@ class Field:
             _check(_L.wc_field_export(self.handle, _vp(_ptr(out))), self.lattice.handle)
         return out
 
+    def load_async(self, psi):
+        """Queue the import of psi[V,4,3] (complex128 or complex64; CUDA or
+        page-locked host memory) without waiting; keep psi unchanged until
+        Lattice.sync() (see wc_field_import_async)."""
+        self._size_ok(psi)
+        c64 = _is_c64(psi)
+        ptr = _ptr64(psi) if c64 else _ptr(psi)
+        _check(_L.wc_field_import_async(self.handle, _vp(ptr), int(c64)), self.lattice.handle)
+        return self
+
+    def store_async(self, out):
+        """Queue the export into out[V,4,3] (complex128 or complex64; CUDA or
+        page-locked host memory); out is valid after Lattice.sync()."""
+        self._size_ok(out)
+        c64 = _is_c64(out)
+        ptr = _ptr64(out) if c64 else _ptr(out)
+        _check(_L.wc_field_export_async(self.handle, _vp(ptr), int(c64)), self.lattice.handle)
+        return out
+
     def copy_from(self, src: "Field", scale: float = 1.0):
         _check(_L.wc_field_copy(self.handle, src.handle, float(scale)), self.lattice.handle)
         return self
@@ -229,6 +252,11 @@ class Lattice:
     def set_stream(self, stream):
         s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
         _check(_L.wc_set_stream(self.handle, _vp(s)), self.handle)
+
+    def sync(self):
+        """Wait for everything queued on this lattice (see wc_sync)."""
+        _check(_L.wc_sync(self.handle), self.handle)
+        return self
 
     def set_fp64_arith(self, arith: int):
         """ARITH_F64 (default) or ARITH_DF32: arithmetic of the FP64 operator

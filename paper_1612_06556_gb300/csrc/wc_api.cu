@@ -470,6 +470,102 @@ wc_status field_export(wc_field f, T *data)
     return st;
 }
 
+bool is_pinned_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// copy stream, events and the two staging buffers of the asynchronous path
+wc_status async_setup(wc_lattice lat)
+{
+    if (lat->copy_stream) return WC_OK;
+    const size_t bytes = sizeof(double2) * 12 * (size_t)lat->g.V;
+    wc_status st = check_cuda(lat, cudaStreamCreateWithFlags(&lat->copy_stream, cudaStreamNonBlocking),
+                              "cudaStreamCreate(copy)");
+    if (st == WC_OK)
+        st = check_cuda(lat, cudaEventCreateWithFlags(&lat->ev_in_ready, cudaEventDisableTiming), "cudaEventCreate");
+    if (st == WC_OK)
+        st = check_cuda(lat, cudaEventCreateWithFlags(&lat->ev_in_free, cudaEventDisableTiming), "cudaEventCreate");
+    if (st == WC_OK) st = check_cuda(lat, dalloc(&lat->astage_in, bytes), "cudaMalloc(staging)");
+    if (st == WC_OK) st = check_cuda(lat, dalloc(&lat->astage_out, bytes), "cudaMalloc(staging)");
+    // nothing to wait for before the first copy
+    if (st == WC_OK) st = check_cuda(lat, cudaEventRecord(lat->ev_in_free, lat->stream), "cudaEventRecord");
+    return st;
+}
+
+template <class T>
+wc_status field_import_async(wc_field f, const T *data)
+{
+    if (!f) return set_error(nullptr, WC_ERR_ARG, "field is NULL");
+    wc_lattice lat = f->lat;
+    if (!data) return set_error(lat, WC_ERR_ARG, "data is NULL");
+    const bool dev = is_device_pointer(data);
+    if (!dev && !is_pinned_host(data))
+        return set_error(lat, WC_ERR_ARG, "asynchronous import needs device or page-locked host memory");
+    const int V = lat->g.V;
+    const T *src = data;
+    wc_status st = WC_OK;
+    if (!dev) {
+        st = async_setup(lat);
+        if (st != WC_OK) return st;
+        // the previous import kernel must have read the staging buffer
+        st = check_cuda(lat, cudaStreamWaitEvent(lat->copy_stream, lat->ev_in_free, 0), "wait");
+        if (st == WC_OK)
+            st = check_cuda(lat, cudaMemcpyAsync(lat->astage_in, data, sizeof(T) * 12 * (size_t)V,
+                                                 cudaMemcpyHostToDevice, lat->copy_stream), "cudaMemcpyAsync(import)");
+        if (st == WC_OK) st = check_cuda(lat, cudaEventRecord(lat->ev_in_ready, lat->copy_stream), "record");
+        if (st == WC_OK) st = check_cuda(lat, cudaStreamWaitEvent(lat->stream, lat->ev_in_ready, 0), "wait");
+        if (st != WC_OK) return st;
+        src = reinterpret_cast<const T *>(lat->astage_in);
+    }
+    dim3 grid((V + 255) / 256), block(256);
+    if (f->prec == WC_F64)
+        k_import<P64, T><<<grid, block, 0, lat->stream>>>(V, src, f->data, f->nrm);
+    else if (f->prec == WC_F32)
+        k_import<P32, T><<<grid, block, 0, lat->stream>>>(V, src, f->data, f->nrm);
+    else
+        k_import<P16, T><<<grid, block, 0, lat->stream>>>(V, src, f->data, f->nrm);
+    st = check_launch(lat, "import");
+    if (st == WC_OK && !dev) st = check_cuda(lat, cudaEventRecord(lat->ev_in_free, lat->stream), "record");
+    return st;
+}
+
+template <class T>
+wc_status field_export_async(wc_field f, T *data)
+{
+    if (!f) return set_error(nullptr, WC_ERR_ARG, "field is NULL");
+    wc_lattice lat = f->lat;
+    if (!data) return set_error(lat, WC_ERR_ARG, "data is NULL");
+    const bool dev = is_device_pointer(data);
+    if (!dev && !is_pinned_host(data))
+        return set_error(lat, WC_ERR_ARG, "asynchronous export needs device or page-locked host memory");
+    const int V = lat->g.V;
+    T *dst = data;
+    wc_status st = WC_OK;
+    if (!dev) {
+        st = async_setup(lat);
+        if (st != WC_OK) return st;
+        dst = reinterpret_cast<T *>(lat->astage_out);   // the previous copy out is earlier in this stream
+    }
+    dim3 grid((V + 255) / 256), block(256);
+    if (f->prec == WC_F64)
+        k_export<P64, T><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
+    else if (f->prec == WC_F32)
+        k_export<P32, T><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
+    else
+        k_export<P16, T><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
+    st = check_launch(lat, "export");
+    if (st == WC_OK && !dev)
+        st = check_cuda(lat, cudaMemcpyAsync(data, lat->astage_out, sizeof(T) * 12 * (size_t)V,
+                                             cudaMemcpyDeviceToHost, lat->stream), "cudaMemcpyAsync(export)");
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -516,6 +612,14 @@ wc_status wc_destroy_lattice(wc_lattice lat)
     free_clover(lat->cinv);
     free_clover(lat->ceo);
     cudaFree(lat->staging);
+    if (lat->copy_stream) {
+        cudaStreamSynchronize(lat->copy_stream);
+        cudaStreamDestroy(lat->copy_stream);
+    }
+    if (lat->ev_in_ready) cudaEventDestroy(lat->ev_in_ready);
+    if (lat->ev_in_free) cudaEventDestroy(lat->ev_in_free);
+    cudaFree(lat->astage_in);
+    cudaFree(lat->astage_out);
     delete lat;
     return WC_OK;
 }
@@ -650,6 +754,26 @@ wc_status wc_field_export(wc_field f, double *data)
 wc_status wc_field_import_f32(wc_field f, const float *data)
 {
     return field_import(f, reinterpret_cast<const float2 *>(data));
+}
+
+wc_status wc_field_import_async(wc_field f, const void *data, int complex64)
+{
+    return complex64 ? field_import_async(f, static_cast<const float2 *>(data))
+                     : field_import_async(f, static_cast<const double2 *>(data));
+}
+
+wc_status wc_field_export_async(wc_field f, void *data, int complex64)
+{
+    return complex64 ? field_export_async(f, static_cast<float2 *>(data))
+                     : field_export_async(f, static_cast<double2 *>(data));
+}
+
+wc_status wc_sync(wc_lattice lat)
+{
+    if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
+    wc_status st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync");
+    if (st == WC_OK && lat->copy_stream) st = check_cuda(lat, cudaStreamSynchronize(lat->copy_stream), "sync");
+    return st;
 }
 
 wc_status wc_field_export_f32(wc_field f, float *data)

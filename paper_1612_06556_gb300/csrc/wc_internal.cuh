@@ -69,6 +69,13 @@ struct wc_lattice_s {
     wc::SolverState st;                       // scratch of single-RHS calls
     double2 *staging = nullptr;               // canonical-size device buffer
     size_t staging_bytes = 0;
+    // asynchronous import/export: host-to-device copies run on copy_stream
+    // into astage_in (ev_in_ready: copied; ev_in_free: consumed by the
+    // import kernel), device-to-host copies on the lattice stream from
+    // astage_out
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr;
+    double2 *astage_in = nullptr, *astage_out = nullptr;
     // even-odd: A^-1 (built on first use) and the half lattice whose
     // operator is the Schur complement M^ (V/2 sites, shares gauge/clover)
     wc::CloverStore cinv;                     // A^-1, parity-ordered planes (even-odd kernels)

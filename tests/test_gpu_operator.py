@@ -140,6 +140,48 @@ def test_import_export_complex64():
         lat.field(1).load(p32[:-1])
 
 
+def test_async_import_export_pipeline():
+    """wc_field_import_async / export_async: a pipelined loop over several
+    inputs (page-locked complex64 and complex128 host buffers, CUDA
+    tensors) gives exactly the outputs of the synchronous calls; pageable
+    host memory is refused before anything is queued."""
+    import torch
+    w = wc()
+    dims = (4, 6, 4, 6)
+    U = synth.exp_links(dims, 0.3, 2101)
+    lat = make_lattice(dims, U, 1.0, 0.12, -1)
+    srcs = [synth.gaussian_source(dims, 2102 + i) for i in range(4)]
+    fin, fout = lat.field(1), lat.field(1)
+    for dt in (np.complex64, np.complex128):
+        ref = []
+        for s in srcs:
+            fin.load(s.astype(dt))
+            lat.apply_M(fout, fin)
+            ref.append(fout.store(np.zeros(s.shape, dt)))
+        hins = [torch.from_numpy(s.astype(dt)).pin_memory() for s in srcs]
+        houts = [torch.zeros_like(h).pin_memory() for h in hins]
+        for hi, ho in zip(hins, houts):
+            fin.load_async(hi)
+            lat.apply_M(fout, fin)
+            fout.store_async(ho)
+        lat.sync()
+        for r, ho in zip(ref, houts):
+            assert np.array_equal(ho.numpy(), r)
+    dev = torch.from_numpy(srcs[1]).cuda()
+    out = torch.zeros_like(dev)
+    fin.load_async(dev)
+    lat.apply_M(fout, fin)
+    fout.store_async(out)
+    lat.sync()
+    fin.load(srcs[1])
+    lat.apply_M(fout, fin)
+    assert np.array_equal(out.cpu().numpy(), fout.store(np.zeros_like(srcs[1])))
+    for call in (lambda: fin.load_async(srcs[0]), lambda: fout.store_async(np.zeros_like(srcs[0]))):
+        with pytest.raises(w.WCError) as e:
+            call()
+        assert e.value.status == 1
+
+
 def test_gpu_gauge_covariance():
     dims, kappa, csw, tbc = (4, 6, 4, 6), 0.12, 1.5, -1
     U = synth.exp_links(dims, 0.5, 11)
