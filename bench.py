@@ -313,6 +313,7 @@ def run_ours(args, world, rank, local):
     copy_gbs = copy_rate(BYTES_PER_SITE["f32"] * V, stream)
     multi = multi_rhs_apply(wc, lat, dims, ms / args.steps, stream)
     ras = ras_timing(wc, lat, dims, src, stream)
+    point = point_source_solve(wc)
     large = large_lattice(wc, args) if not args.skip_large else None
     batch = batch_comparison(wc, args) if not args.skip_batch else None
     force = force_timing(wc, args) if not args.skip_force else None
@@ -365,11 +366,13 @@ def run_ours(args, world, rank, local):
         line["force"] = force
     line["apply_multi"] = multi
     line["ras"] = ras
+    line["point_source_8x8x8x8"] = point
     if world == 1 and not args.skip_cpu:
         smp = OracleSampler(dims, U, src, csw, kappa, tbc, args.ref_seconds)
         g, dt = smp.step()
         line["cpu_baseline"] = {"value": g, "unit": "GFlop/s", "cores": smp.cores, "kind": "oracle",
-                                "sample": smp.describe(dt)}
+                                "sample": smp.describe(dt),
+                                "point_source_solve_8x8x8x8": oracle_point_source_solve()}
     print(json.dumps(line), flush=True)
 
 
@@ -801,6 +804,37 @@ def solve_comparison(wc, lat, src, args):
     out["ras"] = "4^4 blocks, overlap 1, 4 MR iterations"
     out["df32"] = "suffix _df32: FP64 operator steps in double-FP32 arithmetic (wc_set_fp64_arith)"
     return out
+
+
+def point_source_solve(wc):
+    """The 8^3x8 point-source system (exp(0.3 iH) links, csw 1.0, kappa
+    0.12, antiperiodic t): plain FP64 BiCGStab to 1e-12 on the GPU, second of
+    two identical solves."""
+    import synth
+    dims, U, src, csw, kappa, tbc = synth.config_inputs(1)
+    lat = wc.Lattice(dims, tbc).load_gauge(U).load_clover(csw, kappa)
+    b = lat.field(wc.F64).load(src)
+    out = {"lattice": list(dims), "solver": "plain FP64 BiCGStab, tol 1e-12"}
+    for _ in range(2):
+        x = lat.field(wc.F64)
+        info = lat.solve(x, b, tol=1e-12, check=False)
+        x.close()
+    out.update({"seconds": info.seconds, "iters": info.iters, "true_rel_resid": info.true_rel_resid,
+                "status": wc.STATUS.get(info.status, info.status)})
+    lat.close()
+    return out
+
+
+def oracle_point_source_solve():
+    """The same system solved by the CPU oracle's FP64 BiCGStab (host
+    cores), for the reported CPU baseline."""
+    import oracle
+    import synth
+    dims, U, src, csw, kappa, tbc = synth.config_inputs(1)
+    op = oracle.Operator(dims, U, csw, kappa, tbc)
+    t0 = time.perf_counter()
+    res = oracle.bicgstab(op.M, src, tol=1e-12)
+    return {"seconds": time.perf_counter() - t0, "iters": int(res.iters)}
 
 
 def fp64_apply_timing(wc, lat, dims, src, stream, steps=60):

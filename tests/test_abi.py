@@ -55,3 +55,19 @@ def test_argument_errors_are_reported_without_a_gpu(lib):
     with pytest.raises(wc.WCError) as e:
         wc.Lattice((4, 4, 4, 4), t_bc=3)
     assert e.value.status == 1
+
+
+def test_null_handles_are_argument_errors_without_a_gpu(lib):
+    """Entry points reject NULL handles with WC_ERR_ARG before touching the
+    device (host-side checks of the double-FP32 switch, the complex64 and
+    asynchronous transfers and the lattice sync)."""
+    import paper_1612_06556_gb300 as wc
+    L = wc._L
+    buf = (ctypes.c_double * 24)()
+    assert L.wc_set_fp64_arith(None, wc.ARITH_DF32) == 1
+    assert L.wc_sync(None) == 1
+    assert L.wc_field_import_f32(None, buf) == 1
+    assert L.wc_field_export_f32(None, buf) == 1
+    assert L.wc_field_import_async(None, buf, 0) == 1
+    assert L.wc_field_export_async(None, buf, 1) == 1
+    assert L.wc_last_error(None)
