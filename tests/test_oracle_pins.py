@@ -17,6 +17,8 @@ index or a transposed operand in the oracle fails at least one of them:
   * RAS brute force          MR on a block matrix cut out of the dense M
   * force                    central finite differences, covariance, TA form
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -519,3 +521,31 @@ def test_schur_determinant_identity_and_adjoint():
     _, ld_s = np.linalg.slogdet(D)
     ld_a = sum(np.linalg.slogdet(eo.A[s])[1] for s in od)
     assert abs(ld_full - (ld_s + ld_a)) <= 1e-9 * abs(ld_full)
+
+
+def test_oracle_matches_stored_regression_values():
+    """The oracle reproduces tests/golden/oracle_regression_4x4x4x4.json
+    (written by tests/golden/make_golden.py from the oracle itself): a guard
+    against unnoticed changes of the oracle's arithmetic, which every pin
+    above and every GPU parity test relies on."""
+    import importlib.util
+    import json
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    stored = json.load(open(os.path.join(here, "oracle_regression_4x4x4x4.json")))
+    now = mg.compute()
+    assert stored["config"] == now["config"] and stored["sites"] == now["sites"]
+
+    def close(a, b, rtol=1e-10):
+        a, b = np.asarray(a, float), np.asarray(b, float)
+        return np.max(np.abs(a - b)) <= rtol * max(np.max(np.abs(b)), 1e-300)
+
+    for key in ("M_psi", "H_psi", "schur_psi"):
+        for s in stored["sites"]:
+            assert close(now[key][str(s)], stored[key][str(s)]), (key, s)
+    for key in ("clover_block_site0", "force_link_site0_mu0"):
+        assert close(now[key], stored[key]), key
+    for key in ("norm2_M_psi", "action_S"):
+        assert abs(now[key] - stored[key]) <= 1e-11 * abs(stored[key]), key
