@@ -1,4 +1,13 @@
 // C ABI entry points: lattices, fields, gauge/clover loading, applies.
+//
+// Field transfers convert between the caller's canonical layout (complex128
+// or complex64, site-major) and the plane-major device layouts in one kernel
+// per call.  The synchronous calls stage host data in a lattice-owned
+// buffer and return when the caller's memory may be reused; the
+// asynchronous calls take device or page-locked host memory, copy host data
+// in on a second stream of the lattice (so that the next input crosses the
+// host link while the current step computes and copies its result out) and
+// leave the caller to wc_sync.
 #include <math.h>
 #include <stdio.h>
 
