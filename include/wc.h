@@ -296,18 +296,81 @@ wc_status wc_axpy_norm(wc_lattice lat, const double *a, wc_field x, wc_field y,
  * The paper has no counterpart: this is wc_dot for callers that must not
  * allocate device memory (a framework that owns the memory pool, a
  * latency-critical path where cudaMalloc would synchronise the device).
- * a, b: device pointers to n interleaved (re, im) doubles; out: device
- * pointer to 2 doubles, written on the given CUDA stream (NULL = legacy
+ * a, b: device pointers to n interleaved (re, im) doubles, 16-byte aligned
+ * (as every complex128 array allocation is); out: device pointer to 2
+ * doubles, 8-byte aligned, written on the given CUDA stream (NULL = legacy
  * default stream); the call returns without waiting for the result.
+ * WC_ERR_ARG, before any CUDA call, for NULL or misaligned pointers (a and
+ * b may be NULL when n = 0: the result is then 0), n < 0 or n above the
+ * maximum.
  * It allocates nothing: its scratch is a fixed 32 KiB array in the
  * library's device memory, held by every GPU that loads the library until
  * the process exits.  n may be at most 8,388,608 (WC_ERR_ARG beyond).
- * The first call on a device looks up that array's device address (with
- * that device current) and must come before any stream capture that
- * includes this call.  Every call shares the one array, so calls whose
- * kernels overlap on the GPU (e.g. on two streams) race and give wrong
- * sums; calls ordered on one stream are safe.  Deterministic for fixed n. */
+ * When that array comes to exist: with CUDA's lazy module loading (the
+ * default since CUDA 12.2) the library code holding it is loaded into a
+ * context on first use, and the first call of this function on a device is
+ * such a use -- that first call may allocate device memory for the module
+ * and may synchronise.  A caller that must not allocate at all makes one
+ * call during its own set-up (or runs with CUDA_MODULE_LOADING=EAGER, where
+ * the array exists from context creation); every later call on that device
+ * and context allocates nothing.  The first call on a device also looks up
+ * the array's device address (with that device current) and must come
+ * before any stream capture that includes this call.  Every call shares the
+ * one array, so calls whose kernels overlap on the GPU (e.g. on two streams)
+ * race and give wrong sums; calls ordered on one stream are safe.
+ * Deterministic for fixed n. */
 wc_status wc_dot_noalloc(const double *a, const double *b, long long n, double *out, void *cuda_stream);
+
+/* ---- domain decomposition: the overlapped MULT ------------------------ */
+
+/* The paper's multi-node hopping multiplication overlaps the halo exchange
+ * with computation (Sec. 2.2, communication-computation overlapping): a
+ * pre-communication step prepares the face data, the interior sites are
+ * computed while the messages travel, and the surface sites once they have
+ * arrived.  These calls provide the three steps for one sub-domain; moving
+ * the buffers between sub-domains (NCCL, MPI, device copies) is the
+ * caller's.
+ *
+ * wc_create_subdomain: a lattice holding the sites [offset, offset +
+ * local_dims) of a lattice of extents global_dims (every extent >= 2,
+ * offset[mu] + local_dims[mu] <= global_dims[mu]).  Direction mu is cut when
+ * local_dims[mu] < global_dims[mu] (at least one must be); along uncut
+ * directions the sub-domain is periodic by itself.  Neighbouring
+ * sub-domains across a cut face must have the same extents in the other
+ * three directions.  t_bc applies to hops across the global time boundary.
+ * On a sub-domain, wc_load_gauge takes the gauge field (canonical layout)
+ * of the sites [offset - c, offset + local_dims + c) with c[mu] = 1 along
+ * cut directions and 0 otherwise (periodic in the global lattice): the
+ * clover leaves of a face site reach one site into the neighbour, so
+ * wc_load_clover builds the clover term of the sub-domain exactly; the
+ * extended field is kept for later clover rebuilds.  Fields, imports,
+ * exports, copies and the BLAS-1 calls work on sub-domains (inner products
+ * are then partial sums of the sub-domain's sites); the whole-lattice
+ * operator, RAS and the solvers return WC_ERR_ARG.
+ *
+ * Face buffers: one per cut direction and side, wc_halo_bytes(mu) bytes
+ * (12 FP32 reals per face site; 0 for uncut directions), 16-byte aligned
+ * device memory.  send[2 mu] goes to the lower neighbour along mu and
+ * arrives there as recv[2 mu + 1]; send[2 mu + 1] goes to the upper
+ * neighbour and arrives as its recv[2 mu].  Entries of uncut directions are
+ * ignored (may be NULL).  FP32 fields; dagger = 1 for M^+ (pack and surface
+ * must use the same dagger).
+ *
+ * wc_halo_pack: fills the send buffers from in (lower face:
+ * (1 -+ gamma_mu) in projected to two spinors; upper face: U_mu^+ times the
+ * other projection).  wc_apply_interior: out = M in (M^+ in) on every site
+ * that has no hop across a cut face; it needs no buffer and may run while
+ * the buffers travel.  wc_apply_surface: out on the remaining sites, from in
+ * and the received buffers.  The three calls queue kernels on the lattice
+ * stream (wc_set_stream may switch it between calls to overlap them); the
+ * two apply calls together give exactly the whole-lattice operator (bit for
+ * bit with wc_apply_M / wc_apply_Mdag of the undivided lattice in FP32). */
+wc_status wc_create_subdomain(const int local_dims[4], const int global_dims[4], const int offset[4], int t_bc,
+                              void *cuda_stream, wc_lattice *out);
+wc_status wc_halo_bytes(wc_lattice lat, int mu, long long *bytes);
+wc_status wc_halo_pack(wc_lattice lat, wc_field in, int dagger, void *const send[8]);
+wc_status wc_apply_interior(wc_lattice lat, wc_field out, wc_field in, int dagger);
+wc_status wc_apply_surface(wc_lattice lat, wc_field out, wc_field in, int dagger, const void *const recv[8]);
 
 /* ---- preconditioner and solvers --------------------------------------- */
 

@@ -42,6 +42,7 @@ EXPORTED = [
     "wc_dot_noalloc", "wc_ras_autotune", "wc_apply_shape", "wc_apply_schur", "wc_apply_multi",
     "wc_force_times_links", "wc_set_fp64_arith", "wc_field_import_f32", "wc_field_export_f32",
     "wc_field_import_async", "wc_field_export_async", "wc_sync",
+    "wc_create_subdomain", "wc_halo_bytes", "wc_halo_pack", "wc_apply_interior", "wc_apply_surface",
 ]
 
 
@@ -101,6 +102,11 @@ _L.wc_force_times_links.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp]
 _L.wc_apply_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
 _L.wc_ras_autotune.argtypes = [_vp, _vp, ctypes.POINTER(SolveParams), ctypes.POINTER(RasParams)]
 _L.wc_dot_noalloc.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
+_L.wc_create_subdomain.argtypes = [ctypes.POINTER(ctypes.c_int)] * 3 + [ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+_L.wc_halo_bytes.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
+_L.wc_halo_pack.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]
+_L.wc_apply_interior.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+_L.wc_apply_surface.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]
 _L.wc_last_error.argtypes = [_vp]
 _L.wc_last_error.restype = ctypes.c_char_p
 for _n in EXPORTED:
@@ -455,3 +461,64 @@ def pseudofermion_action(U, phi, lattice: Lattice, csw: float, kappa: float, par
     """Differentiable S = phi^+ (M^+ M)^-1 phi (see PseudofermionAction)."""
     p = params if params is not None else solve_params(**kw)
     return _torch_autograd_function().apply(U, phi, lattice, float(csw), float(kappa), p)
+
+
+def _buf_ptrs(bufs):
+    """Eight device buffer pointers (CUDA tensors or None) as a C array."""
+    if len(bufs) != 8:
+        raise ValueError("need 8 buffers: [2 mu] lower side, [2 mu + 1] upper side, None for uncut mu")
+    ptrs = []
+    for b in bufs:
+        if b is None:
+            ptrs.append(None)
+        else:
+            if not (b.is_cuda and b.is_contiguous()):
+                raise ValueError("halo buffers must be contiguous CUDA tensors")
+            ptrs.append(b.data_ptr())
+    return (_vp * 8)(*ptrs)
+
+
+class SubDomain(Lattice):
+    """One sub-domain of a decomposed lattice: the sites [offset, offset +
+    local_dims) of a lattice of extents global_dims, with the overlapped
+    operator steps halo_pack / apply_interior / apply_surface (see
+    wc_create_subdomain in wc.h)."""
+
+    def __init__(self, local_dims, global_dims, offset, t_bc: int = -1, stream=None):
+        self.dims = tuple(int(d) for d in local_dims)
+        self.global_dims = tuple(int(d) for d in global_dims)
+        self.offset = tuple(int(o) for o in offset)
+        self.volume = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
+        self.split = tuple(l < g for l, g in zip(self.dims, self.global_dims))
+        self.ext_dims = tuple(l + 2 * int(c) for l, c in zip(self.dims, self.split))
+        s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        h = _vp()
+        c4 = ctypes.c_int * 4
+        _check(_L.wc_create_subdomain(c4(*self.dims), c4(*self.global_dims), c4(*self.offset), int(t_bc), _vp(s),
+                                      ctypes.byref(h)))
+        self.handle = h
+        self.t_bc = t_bc
+
+    def load_gauge(self, U_ext):
+        """U_ext: the gauge field of the sub-domain extended by one site across
+        every cut face (extents ext_dims, canonical layout)."""
+        n = self.ext_dims[0] * self.ext_dims[1] * self.ext_dims[2] * self.ext_dims[3]
+        if _nbytes(U_ext) != n * 36 * 16:
+            raise ValueError(f"extended gauge buffer must hold {n}*4*3*3 complex128")
+        _check(_L.wc_load_gauge(self.handle, _vp(_ptr(U_ext))), self.handle)
+        return self
+
+    def halo_bytes(self, mu: int) -> int:
+        r = ctypes.c_longlong()
+        _check(_L.wc_halo_bytes(self.handle, int(mu), ctypes.byref(r)), self.handle)
+        return r.value
+
+    def halo_pack(self, inp: Field, send, dagger: bool = False):
+        _check(_L.wc_halo_pack(self.handle, inp.handle, int(bool(dagger)), _buf_ptrs(send)), self.handle)
+
+    def apply_interior(self, out: Field, inp: Field, dagger: bool = False):
+        _check(_L.wc_apply_interior(self.handle, out.handle, inp.handle, int(bool(dagger))), self.handle)
+
+    def apply_surface(self, out: Field, inp: Field, recv, dagger: bool = False):
+        _check(_L.wc_apply_surface(self.handle, out.handle, inp.handle, int(bool(dagger)), _buf_ptrs(recv)),
+               self.handle)

@@ -358,6 +358,17 @@ wc_status check_field(wc_lattice lat, wc_field f, const char *name)
 
 }  // namespace
 
+wc_status require_operator(wc_lattice lat, bool need_clover)
+{
+    if (lat->split_mask)
+        return set_error(lat, WC_ERR_ARG,
+                         "sub-domain lattice: its operator needs the neighbours' face data (wc_halo_pack, "
+                         "wc_apply_interior, wc_apply_surface)");
+    if (!lat->gauge_loaded) return set_error(lat, WC_ERR_STATE, "gauge field not loaded");
+    if (need_clover && !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "clover term not loaded");
+    return WC_OK;
+}
+
 wc_status state_init(wc_lattice lat, SolverState &s)
 {
     const int max_blocks = 8 * sm_count();
@@ -489,22 +500,39 @@ bool is_pinned_host(const void *p)
     return a.type == cudaMemoryTypeHost;
 }
 
-// copy stream, events and the two staging buffers of the asynchronous path
+// copy stream, events and the two staging buffers of the asynchronous path.
+// Everything is created into locals and handed to the lattice only when
+// every step succeeded (the copy stream is set last: it marks the set-up as
+// done); after a failure the partial resources are released and the next
+// asynchronous call tries again.
 wc_status async_setup(wc_lattice lat)
 {
     if (lat->copy_stream) return WC_OK;
     const size_t bytes = sizeof(double2) * 12 * (size_t)lat->g.V;
-    wc_status st = check_cuda(lat, cudaStreamCreateWithFlags(&lat->copy_stream, cudaStreamNonBlocking),
-                              "cudaStreamCreate(copy)");
-    if (st == WC_OK)
-        st = check_cuda(lat, cudaEventCreateWithFlags(&lat->ev_in_ready, cudaEventDisableTiming), "cudaEventCreate");
-    if (st == WC_OK)
-        st = check_cuda(lat, cudaEventCreateWithFlags(&lat->ev_in_free, cudaEventDisableTiming), "cudaEventCreate");
-    if (st == WC_OK) st = check_cuda(lat, dalloc(&lat->astage_in, bytes), "cudaMalloc(staging)");
-    if (st == WC_OK) st = check_cuda(lat, dalloc(&lat->astage_out, bytes), "cudaMalloc(staging)");
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ready = nullptr, freed = nullptr;
+    double2 *in = nullptr, *out = nullptr;
+    wc_status st = check_cuda(lat, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate(copy)");
+    if (st == WC_OK) st = check_cuda(lat, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "cudaEventCreate");
+    if (st == WC_OK) st = check_cuda(lat, cudaEventCreateWithFlags(&freed, cudaEventDisableTiming), "cudaEventCreate");
+    if (st == WC_OK) st = check_cuda(lat, dalloc(&in, bytes), "cudaMalloc(staging)");
+    if (st == WC_OK) st = check_cuda(lat, dalloc(&out, bytes), "cudaMalloc(staging)");
     // nothing to wait for before the first copy
-    if (st == WC_OK) st = check_cuda(lat, cudaEventRecord(lat->ev_in_free, lat->stream), "cudaEventRecord");
-    return st;
+    if (st == WC_OK) st = check_cuda(lat, cudaEventRecord(freed, lat->stream), "cudaEventRecord");
+    if (st != WC_OK) {
+        if (cs) cudaStreamDestroy(cs);
+        if (ready) cudaEventDestroy(ready);
+        if (freed) cudaEventDestroy(freed);
+        cudaFree(in);
+        cudaFree(out);
+        return st;
+    }
+    lat->ev_in_ready = ready;
+    lat->ev_in_free = freed;
+    lat->astage_in = in;
+    lat->astage_out = out;
+    lat->copy_stream = cs;
+    return WC_OK;
 }
 
 template <class T>
@@ -629,6 +657,7 @@ wc_status wc_destroy_lattice(wc_lattice lat)
     if (lat->ev_in_free) cudaEventDestroy(lat->ev_in_free);
     cudaFree(lat->astage_in);
     cudaFree(lat->astage_out);
+    wc_destroy_lattice(lat->ext);
     delete lat;
     return WC_OK;
 }
@@ -637,6 +666,7 @@ wc_status wc_set_stream(wc_lattice lat, void *cuda_stream)
 {
     if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
     lat->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (lat->ext) lat->ext->stream = lat->stream;
     return WC_OK;
 }
 
@@ -665,6 +695,19 @@ wc_status wc_load_gauge(wc_lattice lat, const double *data)
             free_gauge(g);
             return st;
         }
+    }
+    if (lat->split_mask) {
+        // a sub-domain: data is the gauge field extended by one site across
+        // every cut face; it is loaded on the extended lattice (where the
+        // clover term will be built) and its interior copied here
+        lat->ext->stream = lat->stream;
+        st = wc_load_gauge(lat->ext, data);
+        if (st != WC_OK) return set_error(lat, st, "extended gauge field: " + lat->ext->err);
+        st = check_cuda(lat, extract_gauge(lat, lat->stream), "extract gauge");
+        lat->gauge_loaded = (st == WC_OK);
+        lat->clover_loaded = false;
+        lat->cinv_loaded = false;
+        return st;
     }
     const size_t bytes = sizeof(double2) * 36 * (size_t)V;
     const double2 *src = reinterpret_cast<const double2 *>(data);
@@ -705,8 +748,17 @@ wc_status wc_load_clover(wc_lattice lat, double csw, double kappa)
             return st;
         }
     }
-    k_build_clover<<<(V + 63) / 64, 64, 0, lat->stream>>>(lat->g, lat->gauge, c, csw, kappa);
-    st = check_launch(lat, "build_clover");
+    if (lat->split_mask) {
+        // a sub-domain: built on the extended lattice, whose halo sites hold
+        // the neighbours' links the face sites' clover leaves reach
+        lat->ext->stream = lat->stream;
+        st = wc_load_clover(lat->ext, csw, kappa);
+        if (st != WC_OK) return set_error(lat, st, "extended lattice clover: " + lat->ext->err);
+        st = check_cuda(lat, extract_clover(lat, lat->stream), "extract clover");
+    } else {
+        k_build_clover<<<(V + 63) / 64, 64, 0, lat->stream>>>(lat->g, lat->gauge, c, csw, kappa);
+        st = check_launch(lat, "build_clover");
+    }
     if (st != WC_OK) return st;
     lat->csw = csw;
     lat->kappa = kappa;
@@ -807,8 +859,8 @@ static wc_status apply_common(wc_lattice lat, wc_field out, wc_field in, int kin
     if (st != WC_OK) return st;
     if (out == in || out->data == in->data) return set_error(lat, WC_ERR_ARG, "out and in must be distinct fields");
     if (out->prec != in->prec) return set_error(lat, WC_ERR_ARG, "out and in must have the same precision");
-    if (!lat->gauge_loaded) return set_error(lat, WC_ERR_STATE, "gauge field not loaded");
-    if (kind != 2 && !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "clover term not loaded");
+    st = require_operator(lat, kind != 2);
+    if (st != WC_OK) return st;
     return check_cuda(lat, launch_apply(lat, out, in, kind, lat->stream), "apply");
 }
 
@@ -829,7 +881,8 @@ wc_status wc_apply_multi(wc_lattice lat, int n, wc_field *outs, wc_field *ins, i
             if (outs[r] == ins[q] || (q < r && outs[r] == outs[q]))
                 return set_error(lat, WC_ERR_ARG, "out fields must be distinct from each other and from the inputs");
     }
-    if (!lat->gauge_loaded || !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "gauge/clover not loaded");
+    wc_status st = require_operator(lat);
+    if (st != WC_OK) return st;
     return check_cuda(lat, launch_apply_multi(lat, n, outs, ins, dagger ? 1 : 0, nullptr, lat->stream),
                       "apply_multi");
 }
@@ -842,7 +895,8 @@ wc_status wc_apply_schur(wc_lattice lat, wc_field out, wc_field in, int dagger)
     if (st != WC_OK) return st;
     if (out == in || out->prec != in->prec)
         return set_error(lat, WC_ERR_ARG, "out and in must be distinct fields of one precision");
-    if (!lat->gauge_loaded || !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "gauge/clover not loaded");
+    st = require_operator(lat);
+    if (st != WC_OK) return st;
     wc_lattice h = nullptr;
     st = half_lattice(lat, &h);
     if (st != WC_OK) return st;

@@ -624,7 +624,8 @@ extern "C" wc_status wc_ras_autotune(wc_lattice lat, wc_field b, const wc_solve_
     if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
     if (!b || !p || !out) return set_error(lat, WC_ERR_ARG, "NULL argument");
     if (b->lat != lat || b->prec != WC_F64) return set_error(lat, WC_ERR_ARG, "b must be an FP64 field of lat");
-    if (!lat->gauge_loaded || !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "gauge/clover not loaded");
+    wc_status st0 = require_operator(lat);
+    if (st0 != WC_OK) return st0;
     if (p->inner_prec != WC_F32 && p->inner_prec != WC_F16) return set_error(lat, WC_ERR_ARG, "bad inner precision");
     if (p->ras.overlap < 0 || p->ras.mr_iters < 0) return set_error(lat, WC_ERR_ARG, "bad RAS overlap / mr_iters");
     wc_solve_params q = *p;

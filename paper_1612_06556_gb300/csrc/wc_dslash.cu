@@ -57,107 +57,6 @@ __device__ __forceinline__ int site_of_thread(const Geom &g, const TileMap &m, i
     return cx + g.stride[1] * cy + g.stride[2] * cz + g.stride[3] * ct;
 }
 
-template <class P, int MU, int SF, int SB>
-__device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, const void *in, const float *in_nrm,
-                                        int x, const int c[4], typename P::real k, cx<typename P::real> acc[12])
-{
-    using R = typename P::real;
-    const int L = g.L[MU], st = g.stride[MU];
-    {
-        const bool wrap = c[MU] == L - 1;
-        const int xf = wrap ? x - (L - 1) * st : x + st;
-        cx<R> p[12], h[6], u[6], r2[3], w[6];
-        const R scale = P::load_spinor_raw(in, in_nrm, g.V, xf, p);
-        const R coef = ((MU == 3 && wrap) ? k * R(g.tbc) : k) * scale;
-        project<MU, SF>(p, h);
-        P::load_link(U, g.V, MU, x, u, r2);
-        su3_mul(u, r2, h, coef, w);
-        reconstruct_add<MU, SF>(acc, w);
-    }
-    {
-        const bool wrap = c[MU] == 0;
-        const int xb = wrap ? x + (L - 1) * st : x - st;
-        cx<R> p[12], h[6], u[6], r2[3], w[6];
-        const R scale = P::load_spinor_raw(in, in_nrm, g.V, xb, p);
-        const R coef = ((MU == 3 && wrap) ? k * R(g.tbc) : k) * scale;
-        project<MU, SB>(p, h);
-        P::load_link(U, g.V, MU, xb, u, r2);
-        su3_adj_mul(u, r2, h, coef, w);
-        reconstruct_add<MU, SB>(acc, w);
-    }
-}
-
-// One site: out(x) = M in, M^+ in or H in (KIND 0, 1, 2) for the site of
-// this thread in logical block blk.
-template <class P, int KIND>
-__device__ __forceinline__ void apply_site_at(const Geom &g, int x, const GaugeStore &U, const CloverStore &C,
-                                              const void *in, const float *in_nrm, void *out, float *out_nrm,
-                                              double kappa)
-{
-    using R = typename P::real;
-    int c[4];
-    site_coords(g, x, c);
-    cx<R> acc[12];
-    if constexpr (std::is_same<P, PDF>::value) {
-        // Six hops (directions y, z, t) in double-FP32 on the FP32 pipes, in
-        // the compact form (the instruction cache); the clover term and the
-        // two x hops in FP64 on the FP64 pipe, which the double-FP32 work of
-        // the other warps leaves idle.
-        constexpr int SF = KIND == 1 ? +1 : -1;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k] = mkc(R(0.0f, 0.0f), R(0.0f, 0.0f));
-        const R k = KIND == 2 ? R(1.0) : R(-kappa);
-        hops_rt<P, SF>(g, U, in, in_nrm, g.V, x, c, k, acc, [](int y) { return y; }, 2);
-        cx<double> ad[12];
-#pragma unroll
-        for (int q = 0; q < 12; ++q) ad[q] = mkc(df_to_double(acc[q].re), df_to_double(acc[q].im));
-        hop_dir<P64, 0, SF, -SF>(g, U, in, in_nrm, x, c, KIND == 2 ? 1.0 : -kappa, ad);
-        if (KIND == 2) {
-            P64::store_spinor(out, out_nrm, g.V, x, ad);
-            return;
-        }
-        cx<double> pd[12];
-        P64::load_spinor(in, nullptr, g.V, x, pd);
-#pragma unroll 1
-        for (int b = 0; b < 2; ++b) {
-            double r[36];
-            cx<double> v6[6], y6[6];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) v6[q] = b ? pd[6 + q] : pd[q];
-            P64::load_clover(C, g.V, x, b, r);
-            clover_block_mul(r, v6, y6);
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                if (b) ad[6 + q] = ad[6 + q] + y6[q];
-                else ad[q] = ad[q] + y6[q];
-            }
-        }
-        P64::store_spinor(out, out_nrm, g.V, x, ad);
-        return;
-    }
-    if (KIND == 2) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k] = mkc(R(0), R(0));
-    } else {
-        cx<R> p[12];
-        P::load_spinor(in, in_nrm, g.V, x, p);
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            R r[36];
-            P::load_clover(C, g.V, x, b, r);
-            clover_block_mul(r, p + 6 * b, acc + 6 * b);
-        }
-    }
-    const R k = KIND == 2 ? R(1) : R(-kappa);
-    constexpr int SF = KIND == 1 ? +1 : -1;
-    constexpr int SB = -SF;
-    hop_dir<P, 0, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
-    hop_dir<P, 1, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
-    hop_dir<P, 2, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
-    hop_dir<P, 3, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
-    P::store_spinor(out, out_nrm, g.V, x, acc);
-}
-
 template <class P, int KIND>
 __device__ __forceinline__ void apply_site(const Geom &g, const TileMap &tm, int blk, const GaugeStore &U,
                                            const CloverStore &C, const void *in, const float *in_nrm, void *out,

@@ -84,6 +84,15 @@ struct wc_lattice_s {
     wc_lattice_s *half = nullptr;
     wc_lattice_s *schur_parent = nullptr;     // set on a half lattice
     wc_field_s *schur_tmp[3] = {};            // half lattice: odd-site temporaries
+    // sub-domain of a decomposed lattice (wc_create_subdomain): extents of
+    // the whole lattice, global coordinate of local site 0, bit mu of
+    // split_mask: direction mu is cut (its faces border other sub-domains),
+    // and the lattice extended by one site across every cut face, on which
+    // the gauge field is loaded and the clover term built
+    int global_L[4] = {0, 0, 0, 0};
+    int offset[4] = {0, 0, 0, 0};
+    int split_mask = 0;
+    wc_lattice_s *ext = nullptr;
     std::string err;
 };
 
@@ -116,6 +125,17 @@ cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_p
                        cudaStream_t stream);
 
 bool apply_shape(wc_lattice lat, wc_prec prec, int kind, int force, int out[6]);
+
+// WC_OK when the whole-lattice operator of lat can be applied: gauge field
+// (and, with need_clover, the clover term) loaded, and lat not a sub-domain,
+// whose operator needs its neighbours' face data (wc_halo_pack /
+// wc_apply_interior / wc_apply_surface)
+wc_status require_operator(wc_lattice lat, bool need_clover = true);
+
+// sub-domains (wc_halo.cu): copy the interior of the extended lattice's
+// gauge field / clover term into the sub-domain's stores
+cudaError_t extract_gauge(wc_lattice sub, cudaStream_t stream);
+cudaError_t extract_clover(wc_lattice sub, cudaStream_t stream);
 
 // multi-right-hand-side FP32 operator (wc_mrhs.cu): outs[r] = M ins[r]
 // (kind 0) or M^+ ins[r] (kind 1) for r < n <= kMrhsMax, links and clover

@@ -11,6 +11,9 @@
 // reduction -- in one file-scope __device__ array of fixed size, so it
 // allocates nothing.  Every GPU that loads the library holds that array
 // (32 KiB + 256 B) until the process exits.
+#include <cuda.h>
+#include <stdint.h>
+
 #include <mutex>
 
 #include "wc_internal.cuh"
@@ -96,11 +99,39 @@ __global__ void __launch_bounds__(kNaThreads) k_dot_noalloc(const double2 *a, co
     }
 }
 
-std::mutex g_setup_mutex;
-NoAllocScratch *g_scratch_addr[kMaxDevices] = {};
+// cuCtxGetId of the driver, looked up through the runtime (no link against
+// libcuda); null when the driver does not offer it
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+CtxGetIdFn ctx_get_id()
+{
+    static CtxGetIdFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return static_cast<CtxGetIdFn>(nullptr);
+        }
+        return reinterpret_cast<CtxGetIdFn>(p);
+    }();
+    return fn;
+}
 
-// Device address of the scratch array on the current device (set up once
-// per device: the name g_noalloc_scratch is only a host-side stand-in).
+struct ScratchEntry {
+    unsigned long long ctx = 0;   // id of the context the address belongs to
+    NoAllocScratch *addr = nullptr;
+};
+
+std::mutex g_setup_mutex;
+ScratchEntry g_scratch[kMaxDevices];
+
+// Device address of the scratch array for the current device and context.
+// The name g_noalloc_scratch is only a host-side stand-in; the address is
+// looked up with cudaGetSymbolAddress once per device (with that device
+// current) and cached together with the context's id, so that a context
+// destroyed and created again (cudaDeviceReset) gets a fresh lookup instead
+// of a stale address.  Without cuCtxGetId the lookup is repeated every call
+// (cheap once the library's module is loaded).
 cudaError_t scratch_address(NoAllocScratch **p)
 {
     int dev = 0;
@@ -108,13 +139,23 @@ cudaError_t scratch_address(NoAllocScratch **p)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *addr = nullptr;
-        e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<NoAllocScratch *>(addr);
+    CtxGetIdFn get_id = ctx_get_id();
+    unsigned long long id = 0;
+    bool have_id = get_id && get_id(nullptr, &id) == CUDA_SUCCESS;
+    ScratchEntry &ent = g_scratch[dev];
+    if (have_id && ent.addr && ent.ctx == id) {
+        *p = ent.addr;
+        return cudaSuccess;
     }
-    *p = g_scratch_addr[dev];
+    void *addr = nullptr;
+    e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    // the lookup made the device's primary context current if it was not yet
+    if (!have_id) have_id = get_id && get_id(nullptr, &id) == CUDA_SUCCESS;
+    ent.addr = static_cast<NoAllocScratch *>(addr);
+    ent.ctx = have_id ? id : 0;
+    if (!have_id) ent.addr = nullptr;   // no id to validate a cached address against
+    *p = static_cast<NoAllocScratch *>(addr);
     return cudaSuccess;
 }
 
@@ -125,8 +166,12 @@ using namespace wc;
 extern "C" wc_status wc_dot_noalloc(const double *a, const double *b, long long n, double *out,
                                     void *cuda_stream)
 {
-    if (!a || !b || !out) return set_error(nullptr, WC_ERR_ARG, "wc_dot_noalloc: a, b and out must not be NULL");
+    if (!out) return set_error(nullptr, WC_ERR_ARG, "wc_dot_noalloc: out must not be NULL");
     if (n < 0) return set_error(nullptr, WC_ERR_ARG, "wc_dot_noalloc: n must be >= 0");
+    if (n > 0 && (!a || !b)) return set_error(nullptr, WC_ERR_ARG, "wc_dot_noalloc: a and b must not be NULL");
+    if (((uintptr_t)a | (uintptr_t)b) & 15u)
+        return set_error(nullptr, WC_ERR_ARG, "wc_dot_noalloc: a and b must be 16-byte aligned (complex128 arrays)");
+    if ((uintptr_t)out & 7u) return set_error(nullptr, WC_ERR_ARG, "wc_dot_noalloc: out must be 8-byte aligned");
     if (n > kNaMaxN)
         return set_error(nullptr, WC_ERR_ARG,
                          "wc_dot_noalloc: n = " + std::to_string(n) +

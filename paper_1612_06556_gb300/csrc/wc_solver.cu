@@ -699,8 +699,7 @@ wc_status check_solve_args(wc_lattice lat, wc_field x, wc_field b, const wc_solv
         wc_status st = check_ras_params(lat, &p->ras);
         if (st != WC_OK) return st;
     }
-    if (!lat->gauge_loaded || !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "gauge/clover not loaded");
-    return WC_OK;
+    return require_operator(lat);
 }
 
 }  // namespace wc
@@ -741,7 +740,8 @@ wc_status wc_ras_precond(wc_lattice lat, wc_field out, wc_field in, const wc_ras
         return set_error(lat, WC_ERR_ARG, "RAS works on FP32 or FP16 fields of one precision");
     wc_status st = check_ras_params(lat, p);
     if (st != WC_OK) return st;
-    if (!lat->gauge_loaded || !lat->clover_loaded) return set_error(lat, WC_ERR_STATE, "gauge/clover not loaded");
+    st = require_operator(lat);
+    if (st != WC_OK) return st;
     return check_cuda(lat, launch_ras(lat, out, in, *p, 0, lat->stream), "ras");
 }
 

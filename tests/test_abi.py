@@ -71,3 +71,34 @@ def test_null_handles_are_argument_errors_without_a_gpu(lib):
     assert L.wc_field_import_async(None, buf, 0) == 1
     assert L.wc_field_export_async(None, buf, 1) == 1
     assert L.wc_last_error(None)
+
+
+def test_dot_noalloc_argument_errors_without_a_gpu(lib):
+    """The allocation-free inner product rejects NULL or misaligned pointers
+    and negative sizes with WC_ERR_ARG before any CUDA call (the pointer
+    values below are never dereferenced)."""
+    import paper_1612_06556_gb300 as wc
+    L = wc._L
+    p16, p8 = wc._vp(0x10000), wc._vp(0x20008)
+    assert L.wc_dot_noalloc(None, p16, 4, p16, None) == 1
+    assert L.wc_dot_noalloc(p16, None, 4, p16, None) == 1
+    assert L.wc_dot_noalloc(p16, p16, 4, None, None) == 1
+    assert L.wc_dot_noalloc(p16, p16, -1, p16, None) == 1
+    assert L.wc_dot_noalloc(p8, p16, 4, p16, None) == 1
+    assert "aligned" in L.wc_last_error(None).decode()
+    assert L.wc_dot_noalloc(p16, p8, 4, p16, None) == 1
+    assert L.wc_dot_noalloc(p16, p16, 4, wc._vp(0x10004), None) == 1
+    assert "aligned" in L.wc_last_error(None).decode()
+
+
+def test_subdomain_argument_errors_without_a_gpu(lib):
+    """wc_create_subdomain checks its extents and offsets before any CUDA
+    call."""
+    import paper_1612_06556_gb300 as wc
+    for local, glob, off in [((4, 4, 4, 4), (4, 4, 4, 4), (0, 0, 0, 0)),    # nothing cut
+                             ((4, 4, 4, 8), (4, 4, 4, 4), (0, 0, 0, 0)),    # local > global
+                             ((4, 4, 4, 4), (4, 4, 4, 8), (0, 0, 0, 5)),    # outside the lattice
+                             ((4, 4, 4, 1), (4, 4, 4, 8), (0, 0, 0, 0))]:   # extent < 2
+        with __import__("pytest").raises(wc.WCError) as e:
+            wc.SubDomain(local, glob, off)
+        assert e.value.status == 1

@@ -27,14 +27,44 @@ def test_dot_noalloc_matches_dot_twice_in_a_row():
     ta = torch.from_numpy(a).cuda()
     tb = torch.from_numpy(b).cuda()
     stream = torch.cuda.current_stream()
+    outs = [torch.full((2,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(2)]
+    tol = 1e-12 * np.linalg.norm(a) * np.linalg.norm(b)
+    free_after_first = None
     for trial in range(2):
         ref = lat.dot(fa, fb)
-        out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
-        wc.dot_noalloc(ta, tb, out, stream)
-        got = complex(*out.cpu().numpy())
-        tol = 1e-12 * np.linalg.norm(a) * np.linalg.norm(b)
+        torch.cuda.synchronize()
+        wc.dot_noalloc(ta, tb, outs[trial], stream)
+        torch.cuda.synchronize()
+        # the first call on the device may load the library's module (lazy
+        # loading); the second must not change the device's free memory
+        free = torch.cuda.mem_get_info()[0]
+        if trial == 0:
+            free_after_first = free
+        else:
+            assert free == free_after_first
+        got = complex(*outs[trial].cpu().numpy())
         assert abs(got - ref) <= tol, (trial, got, ref)
         assert abs(got - np.vdot(a, b)) <= tol
+
+
+@pytest.mark.parametrize("n", [0, 1, 4097, 8388608])
+def test_dot_noalloc_sizes_against_numpy(n):
+    """Empty input (one block, zero result), a ragged last chunk, and the
+    largest size the fixed scratch holds (2048 blocks)."""
+    import torch
+
+    import paper_1612_06556_gb300 as wc
+
+    rng = np.random.default_rng(n + 5)
+    a = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        wc.dot_noalloc(ta, tb, out, torch.cuda.current_stream())
+        got = complex(*out.cpu().numpy())
+        ref = np.vdot(a, b)
+        assert abs(got - ref) <= 1e-12 * max(1.0, np.linalg.norm(a) * np.linalg.norm(b)), (n, got, ref)
 
 
 def test_dot_noalloc_rejects_sizes_beyond_its_maximum():
