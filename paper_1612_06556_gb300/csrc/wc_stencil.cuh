@@ -309,6 +309,157 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, cons
     }
 }
 
+// ---- FP16 storage: products and sums formed from the stored halves ------
+// With FP16 storage the clover entries, the centre spinor and the
+// neighbour spinors are binary16 values: fma.f32.f16 forms a product of
+// two of them exactly (11 x 11 significand bits fit in FP32) and adds it in
+// FP32 with one rounding -- the result of converting both to FP32 and using
+// an FP32 fma, without the conversion instructions (the FP16 operator is
+// bound by instruction issue).
+
+__device__ __forceinline__ float fma_h(unsigned short a, unsigned short b, float c)
+{
+    float d;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned short lo16(unsigned w) { return (unsigned short)(w & 0xffffu); }
+__device__ __forceinline__ unsigned short hi16(unsigned w) { return (unsigned short)(w >> 16); }
+
+// y = B v for clover block b (FP16 store, site x) and the unscaled FP16
+// centre spinor components v (half2 words (re, im), spins 2b, 2b + 1)
+__device__ __forceinline__ void clover_block_h(const CloverStore &C, int V, int x, int b, const unsigned v[6],
+                                               cx<float> y[6])
+{
+    unsigned short vr[6], vi[6], nvr[6], nvi[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        vr[i] = lo16(v[i]);
+        vi[i] = hi16(v[i]);
+        nvr[i] = vr[i] ^ 0x8000u;
+        nvi[i] = vi[i] ^ 0x8000u;
+    }
+    const uint4 *p = C.c16 + x;
+    auto entry = [&](int q) {   // half2 word q (0..17) of block b
+        const int gq = 18 * b + q;
+        const uint4 w = __ldg(p + (size_t)(gq >> 2) * V);
+        return (gq & 3) == 0 ? w.x : ((gq & 3) == 1 ? w.y : ((gq & 3) == 2 ? w.z : w.w));
+    };
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {   // diagonal reals 2q, 2q + 1
+        const unsigned d = entry(q);
+        y[2 * q] = mkc(fma_h(lo16(d), vr[2 * q], 0.f), fma_h(lo16(d), vi[2 * q], 0.f));
+        y[2 * q + 1] = mkc(fma_h(hi16(d), vr[2 * q + 1], 0.f), fma_h(hi16(d), vi[2 * q + 1], 0.f));
+    }
+    int k = 3;
+#pragma unroll
+    for (int a = 1; a < 6; ++a) {
+#pragma unroll
+        for (int c = 0; c < a; ++c) {
+            const unsigned l = entry(k++);
+            const unsigned short lr = lo16(l), li = hi16(l);
+            // y[a] += l v[c]; y[c] += conj(l) v[a]
+            y[a].re = fma_h(lr, vr[c], fma_h(li, nvi[c], y[a].re));
+            y[a].im = fma_h(lr, vi[c], fma_h(li, vr[c], y[a].im));
+            y[c].re = fma_h(lr, vr[a], fma_h(li, vi[a], y[c].re));
+            y[c].im = fma_h(lr, vi[a], fma_h(li, nvr[a], y[c].im));
+        }
+    }
+}
+
+// a + S b for binary16 a, b, exactly rounded to FP32 (the FP32 sum of the
+// two converted values); S = +-1
+template <int S>
+__device__ __forceinline__ float add_hh(unsigned short a, unsigned short b)
+{
+    const unsigned short one = 0x3c00u, s_one = S > 0 ? 0x3c00u : 0xbc00u;
+    return fma_h(a, one, fma_h(b, s_one, 0.f));
+}
+
+// two-spinor of (1 + S gamma_MU) psi from the packed FP16 spinor words
+// w[k] (component k = 3 spin + colour as half2 (re, im)), unscaled
+template <int MU, int S>
+__device__ __forceinline__ void project_h16(const unsigned w[12], cx<float> h[6])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const unsigned u0 = w[c], u1 = w[3 + c], d0 = w[6 + c], d1 = w[9 + c];
+        if (MU == 0) {   // h0 = u0 + S i d1, h1 = u1 + S i d0
+            h[c] = mkc(add_hh<-S>(lo16(u0), hi16(d1)), add_hh<S>(hi16(u0), lo16(d1)));
+            h[3 + c] = mkc(add_hh<-S>(lo16(u1), hi16(d0)), add_hh<S>(hi16(u1), lo16(d0)));
+        } else if (MU == 1) {   // h0 = u0 + S d1, h1 = u1 - S d0
+            h[c] = mkc(add_hh<S>(lo16(u0), lo16(d1)), add_hh<S>(hi16(u0), hi16(d1)));
+            h[3 + c] = mkc(add_hh<-S>(lo16(u1), lo16(d0)), add_hh<-S>(hi16(u1), hi16(d0)));
+        } else if (MU == 2) {   // h0 = u0 + S i d0, h1 = u1 - S i d1
+            h[c] = mkc(add_hh<-S>(lo16(u0), hi16(d0)), add_hh<S>(hi16(u0), lo16(d0)));
+            h[3 + c] = mkc(add_hh<S>(lo16(u1), hi16(d1)), add_hh<-S>(hi16(u1), lo16(d1)));
+        } else {   // h0 = u0 + S d0, h1 = u1 + S d1
+            h[c] = mkc(add_hh<S>(lo16(u0), lo16(d0)), add_hh<S>(hi16(u0), hi16(d0)));
+            h[3 + c] = mkc(add_hh<S>(lo16(u1), lo16(d1)), add_hh<S>(hi16(u1), hi16(d1)));
+        }
+    }
+}
+
+// acc += coef * (reconstruction of the two-spinor w), the coefficient
+// folded into the accumulation (reconstruct_add of coef w without forming
+// coef w)
+template <int MU, int S>
+__device__ __forceinline__ void reconstruct_fma(cx<float> acc[12], const cx<float> w[6], float coef)
+{
+    const float sc = S > 0 ? coef : -coef;   // S coef
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cx<float> w0 = w[c], w1 = w[3 + c];
+        acc[c] = mkc(fmaf(coef, w0.re, acc[c].re), fmaf(coef, w0.im, acc[c].im));
+        acc[3 + c] = mkc(fmaf(coef, w1.re, acc[3 + c].re), fmaf(coef, w1.im, acc[3 + c].im));
+        if (MU == 0) {   // acc[6+c] -= S i w1, acc[9+c] -= S i w0
+            acc[6 + c] = mkc(fmaf(sc, w1.im, acc[6 + c].re), fmaf(-sc, w1.re, acc[6 + c].im));
+            acc[9 + c] = mkc(fmaf(sc, w0.im, acc[9 + c].re), fmaf(-sc, w0.re, acc[9 + c].im));
+        } else if (MU == 1) {   // acc[6+c] -= S w1, acc[9+c] += S w0
+            acc[6 + c] = mkc(fmaf(-sc, w1.re, acc[6 + c].re), fmaf(-sc, w1.im, acc[6 + c].im));
+            acc[9 + c] = mkc(fmaf(sc, w0.re, acc[9 + c].re), fmaf(sc, w0.im, acc[9 + c].im));
+        } else if (MU == 2) {   // acc[6+c] -= S i w0, acc[9+c] += S i w1
+            acc[6 + c] = mkc(fmaf(sc, w0.im, acc[6 + c].re), fmaf(-sc, w0.re, acc[6 + c].im));
+            acc[9 + c] = mkc(fmaf(-sc, w1.im, acc[9 + c].re), fmaf(sc, w1.re, acc[9 + c].im));
+        } else {   // acc[6+c] += S w0, acc[9+c] += S w1
+            acc[6 + c] = mkc(fmaf(sc, w0.re, acc[6 + c].re), fmaf(sc, w0.im, acc[6 + c].im));
+            acc[9 + c] = mkc(fmaf(sc, w1.re, acc[9 + c].re), fmaf(sc, w1.im, acc[9 + c].im));
+        }
+    }
+}
+
+// the forward and backward hop of direction MU for FP16 storage (hop_dir
+// with the projection formed from the stored halves and the coefficient
+// folded into the accumulation)
+template <int MU, int SF, int SB>
+__device__ __forceinline__ void hop_dir_h16(const Geom &g, const GaugeStore &U, const void *in, const float *in_nrm,
+                                            int x, const int c[4], float k, cx<float> acc[12])
+{
+    const int L = g.L[MU], st = g.stride[MU];
+    const uint4 *ps = static_cast<const uint4 *>(in);
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+        const bool wrap = dir == 0 ? c[MU] == L - 1 : c[MU] == 0;
+        const int y = dir == 0 ? (wrap ? x - (L - 1) * st : x + st) : (wrap ? x + (L - 1) * st : x - st);
+        const uint4 s0 = __ldg(ps + y), s1 = __ldg(ps + (size_t)g.V + y), s2 = __ldg(ps + 2 * (size_t)g.V + y);
+        const unsigned w[12] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w, s2.x, s2.y, s2.z, s2.w};
+        const float coef = ((MU == 3 && wrap) ? k * (float)g.tbc : k) * __ldg(in_nrm + y);
+        cx<float> h[6], u[6], r2[3], wv[6];
+        if (dir == 0) {
+            project_h16<MU, SF>(w, h);
+            P16::load_link(U, g.V, MU, x, u, r2);
+            su3_mul(u, r2, h, 1.0f, wv);
+            reconstruct_fma<MU, SF>(acc, wv, coef);
+        } else {
+            project_h16<MU, SB>(w, h);
+            P16::load_link(U, g.V, MU, y, u, r2);
+            su3_adj_mul(u, r2, h, 1.0f, wv);
+            reconstruct_fma<MU, SB>(acc, wv, coef);
+        }
+    }
+}
+
 // One site: out(x) = M in, M^+ in or H in (KIND 0, 1, 2) for the site of
 // this thread in logical block blk.
 template <class P, int KIND>
@@ -360,6 +511,18 @@ __device__ __forceinline__ void apply_site_at(const Geom &g, int x, const GaugeS
     if (KIND == 2) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = mkc(R(0), R(0));
+    } else if constexpr (std::is_same<P, P16>::value) {
+        // clover products from the stored halves, the centre scale applied
+        // once to the result
+        const uint4 *ps = static_cast<const uint4 *>(in);
+        const uint4 s0 = __ldg(ps + x), s1 = __ldg(ps + (size_t)g.V + x), s2 = __ldg(ps + 2 * (size_t)g.V + x);
+        const float sc = __ldg(in_nrm + x);
+        const unsigned v0[6] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y};
+        const unsigned v1[6] = {s1.z, s1.w, s2.x, s2.y, s2.z, s2.w};
+        clover_block_h(C, g.V, x, 0, v0, acc);
+        clover_block_h(C, g.V, x, 1, v1, acc + 6);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) acc[q] = sc * acc[q];
     } else {
         cx<R> p[12];
         P::load_spinor(in, in_nrm, g.V, x, p);
@@ -373,10 +536,17 @@ __device__ __forceinline__ void apply_site_at(const Geom &g, int x, const GaugeS
     const R k = KIND == 2 ? R(1) : R(-kappa);
     constexpr int SF = KIND == 1 ? +1 : -1;
     constexpr int SB = -SF;
-    hop_dir<P, 0, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
-    hop_dir<P, 1, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
-    hop_dir<P, 2, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
-    hop_dir<P, 3, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
+    if constexpr (std::is_same<P, P16>::value) {
+        hop_dir_h16<0, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
+        hop_dir_h16<1, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
+        hop_dir_h16<2, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
+        hop_dir_h16<3, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
+    } else {
+        hop_dir<P, 0, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
+        hop_dir<P, 1, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
+        hop_dir<P, 2, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
+        hop_dir<P, 3, SF, SB>(g, U, in, in_nrm, x, c, k, acc);
+    }
     P::store_spinor(out, out_nrm, g.V, x, acc);
 }
 
