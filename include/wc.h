@@ -69,7 +69,8 @@ typedef enum {
     WC_ERR_NOT_CONVERGED = 4, /* solver hit max_iter before tol */
     WC_ERR_BREAKDOWN = 5,     /* BiCGStab breakdown: <rhat,r>, <rhat,v> or <t,t> = 0 */
     WC_ERR_NAN = 6,           /* a non-finite norm was met inside a reduction */
-    WC_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up */
+    WC_ERR_TIMEOUT = 7        /* reserved: no call returns it (no device-side wait is bounded by a
+                                 timeout; batched solves loop inside a CUDA graph) */
 } wc_status;
 
 typedef enum { WC_F64 = 0, WC_F32 = 1, WC_F16 = 2 } wc_prec;
@@ -423,6 +424,17 @@ wc_status wc_action_force(wc_lattice lat, wc_field phi, double *S_out, double *f
  * force into the autograd gradient of the binding.  Asynchronous on the
  * lattice stream. */
 wc_status wc_force_times_links(wc_lattice lat, const double *force, const double *U, double scale, double *out);
+
+/* Diagnostics of the checked build (the library compiled with -DWC_CHECKED,
+ * build.py --checked): every site, neighbour, block-local and shared-memory
+ * index the operator, even-odd, RAS and multi-RHS kernels compute is tested
+ * against its array's extent; an index out of range is counted and replaced
+ * by 0 (no fault: the result is wrong and the count says so), and the RAS
+ * kernels fill their shared memory with NaN before staging it.  *count =
+ * the number of out-of-range indices since the library was loaded (waits
+ * for the device first).  WC_ERR_STATE in the normal build.  The paper has
+ * no counterpart: this stands in for a memory checker. */
+wc_status wc_checked_violations(unsigned long long *count);
 
 const char *wc_last_error(wc_lattice lat);
 

@@ -18,7 +18,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libwc.so")
+# WC_LIBRARY selects another build of the library (the checked build,
+# libwc_checked.so, in the tests); default: the in-tree libwc.so
+LIB_PATH = os.environ.get("WC_LIBRARY") or os.path.join(_HERE, "libwc.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -43,6 +45,7 @@ EXPORTED = [
     "wc_force_times_links", "wc_set_fp64_arith", "wc_field_import_f32", "wc_field_export_f32",
     "wc_field_import_async", "wc_field_export_async", "wc_sync",
     "wc_create_subdomain", "wc_halo_bytes", "wc_halo_pack", "wc_apply_interior", "wc_apply_surface",
+    "wc_checked_violations",
 ]
 
 
@@ -107,6 +110,7 @@ _L.wc_halo_bytes.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong
 _L.wc_halo_pack.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]
 _L.wc_apply_interior.argtypes = [_vp, _vp, _vp, ctypes.c_int]
 _L.wc_apply_surface.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]
+_L.wc_checked_violations.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
 _L.wc_last_error.argtypes = [_vp]
 _L.wc_last_error.restype = ctypes.c_char_p
 for _n in EXPORTED:
@@ -522,3 +526,11 @@ class SubDomain(Lattice):
     def apply_surface(self, out: Field, inp: Field, recv, dagger: bool = False):
         _check(_L.wc_apply_surface(self.handle, out.handle, inp.handle, int(bool(dagger)), _buf_ptrs(recv)),
                self.handle)
+
+
+def checked_violations() -> int:
+    """Out-of-range indices counted by the checked build since it was loaded
+    (see wc_checked_violations); raises WCError in the normal build."""
+    n = ctypes.c_ulonglong()
+    _check(_L.wc_checked_violations(ctypes.byref(n)))
+    return n.value

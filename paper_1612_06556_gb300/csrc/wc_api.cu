@@ -14,6 +14,8 @@
 #include <mutex>
 #include <new>
 
+#include <vector>
+
 #include "wc_internal.cuh"
 
 namespace wc {
@@ -358,6 +360,15 @@ wc_status check_field(wc_lattice lat, wc_field f, const char *name)
 
 }  // namespace
 
+// readers of the per-translation-unit violation counters (checked build)
+std::vector<cudaError_t (*)(unsigned *)> &check_readers()
+{
+    static std::vector<cudaError_t (*)(unsigned *)> r;
+    return r;
+}
+
+void register_check_counter(cudaError_t (*read)(unsigned *)) { check_readers().push_back(read); }
+
 wc_status require_operator(wc_lattice lat, bool need_clover)
 {
     if (lat->split_mask)
@@ -627,6 +638,7 @@ wc_status wc_create_lattice(const int dims[4], int t_bc, void *cuda_stream, wc_l
     lat->g.stride[3] = dims[0] * dims[1] * dims[2];
     lat->g.V = (int)V;
     lat->g.tbc = t_bc;
+    geom_set_div(lat->g);
     lat->stream = static_cast<cudaStream_t>(cuda_stream);
     wc_status st = state_init(lat, lat->st);
     if (st != WC_OK) {
@@ -926,6 +938,21 @@ wc_status wc_apply_shape(wc_lattice lat, wc_prec prec, int kind, int force_index
     if (!apply_shape(lat, prec, kind, force_index, shape_out))
         return set_error(lat, WC_ERR_ARG, "launch shape does not fit this lattice / precision");
     return WC_OK;
+}
+
+wc_status wc_checked_violations(unsigned long long *count)
+{
+    if (!count) return set_error(nullptr, WC_ERR_ARG, "count is NULL");
+    *count = 0;
+    if (!kChecked) return set_error(nullptr, WC_ERR_STATE, "not a checked build (compile with -DWC_CHECKED)");
+    wc_status st = check_cuda(nullptr, cudaDeviceSynchronize(), "sync");
+    for (auto read : check_readers()) {
+        if (st != WC_OK) break;
+        unsigned v = 0;
+        st = check_cuda(nullptr, read(&v), "read violation counter");
+        *count += v;
+    }
+    return st;
 }
 
 const char *wc_last_error(wc_lattice lat)

@@ -169,7 +169,7 @@ __device__ __forceinline__ int full_site(const Geom &g, int i, int p, int c[4])
     c[2] = rest % g.L[2];
     c[3] = rest / g.L[2];
     c[0] = 2 * xh + ((p + c[1] + c[2] + c[3]) & 1);
-    return c[0] + g.stride[1] * c[1] + g.stride[2] * c[2] + g.stride[3] * c[3];
+    return wc_idx(c[0] + g.stride[1] * c[1] + g.stride[2] * c[2] + g.stride[3] * c[3], g.V);
 }
 
 // hops of the opposite-parity half field `in` into site x (full index x,
@@ -184,7 +184,7 @@ __device__ __forceinline__ void eo_hop_dir(const Geom &g, const GaugeStore &U, c
     const int L = g.L[MU], st = g.stride[MU];
     {
         const bool wrap = c[MU] == L - 1;
-        const int xf = wrap ? x - (L - 1) * st : x + st;
+        const int xf = wc_idx(wrap ? x - (L - 1) * st : x + st, g.V);
         cx<R> p[12], h[6], u[6], r2[3], w[6];
         const R scale = P::load_spinor_raw(in, in_nrm, Vh, xf >> 1, p);
         const R coef = ((MU == 3 && wrap) ? k * R(g.tbc) : k) * scale;
@@ -195,7 +195,7 @@ __device__ __forceinline__ void eo_hop_dir(const Geom &g, const GaugeStore &U, c
     }
     {
         const bool wrap = c[MU] == 0;
-        const int xb = wrap ? x + (L - 1) * st : x - st;
+        const int xb = wc_idx(wrap ? x + (L - 1) * st : x - st, g.V);
         cx<R> p[12], h[6], u[6], r2[3], w[6];
         const R scale = P::load_spinor_raw(in, in_nrm, Vh, xb >> 1, p);
         const R coef = ((MU == 3 && wrap) ? k * R(g.tbc) : k) * scale;
@@ -248,7 +248,7 @@ __device__ __forceinline__ void eo_tail(const Geom &g, int p, const CloverStore 
     } else {
         P::load_spinor(vin, vin_nrm, Vh, i, v);
         if (MODE == 1) {
-            clover_eo<P>(C, g.V, p * Vh + i, v, o);
+            clover_eo<P>(C, g.V, wc_idx(p * Vh + i, g.V), v, o);
 #pragma unroll
             for (int k = 0; k < 12; ++k) o[k] = o[k] + bt * h[k];
             P::store_spinor(out, out_nrm, Vh, i, o);
@@ -262,7 +262,7 @@ __device__ __forceinline__ void eo_tail(const Geom &g, int p, const CloverStore 
             return;
         }
     }
-    clover_eo<P>(Ci, g.V, p * Vh + i, v, o);
+    clover_eo<P>(Ci, g.V, wc_idx(p * Vh + i, g.V), v, o);
     P::store_spinor(out, out_nrm, Vh, i, o);
 }
 

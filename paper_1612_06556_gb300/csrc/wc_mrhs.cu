@@ -49,7 +49,7 @@ __device__ __forceinline__ void hop_mrhs(const Geom &g, const float4 (*st)[kMrhs
     const int L = g.L[MU], stl = g.stride[MU];
     {
         const bool wrap = c[MU] == L - 1;
-        const int xf = wrap ? x - (L - 1) * stl : x + stl;
+        const int xf = wc_idx(wrap ? x - (L - 1) * stl : x + stl, g.V);
         cx<float> p[12], h[6], u[6], r2[3], w[6];
         P32::load_spinor(in, nullptr, g.V, xf, p);
         const float coef = (MU == 3 && wrap) ? k * (float)g.tbc : k;
@@ -60,7 +60,7 @@ __device__ __forceinline__ void hop_mrhs(const Geom &g, const float4 (*st)[kMrhs
     }
     {
         const bool wrap = c[MU] == 0;
-        const int xb = wrap ? x + (L - 1) * stl : x - stl;
+        const int xb = wc_idx(wrap ? x + (L - 1) * stl : x - stl, g.V);
         cx<float> p[12], h[6], u[6], r2[3], w[6];
         P32::load_spinor(in, nullptr, g.V, xb, p);
         const float coef = (MU == 3 && wrap) ? k * (float)g.tbc : k;
@@ -91,7 +91,7 @@ __global__ void __maxnreg__(80)
             const int mu = (item - 12) / 3, j = (item - 12) % 3;
             int c[4];
             site_coords(g, x, c);
-            const int xb = c[mu] == 0 ? x + (g.L[mu] - 1) * g.stride[mu] : x - g.stride[mu];
+            const int xb = wc_idx(c[mu] == 0 ? x + (g.L[mu] - 1) * g.stride[mu] : x - g.stride[mu], g.V);
             v = __ldg(U.u32 + ((size_t)mu * 3 + j) * g.V + xb);
         } else {                                           // clover plane item - 24 of [18][V]
             v = __ldg(C.c32 + (size_t)(item - 24) * g.V + x);

@@ -156,16 +156,16 @@ __device__ __forceinline__ void ras_hops(const Geom &g, const RasGeom &rg, const
     if (lm + 1 < rg.e[MU]) {
         const float coef = (MU == 3 && (wbits & (16u << 3))) ? mk * (float)g.tbc : mk;
         cx<float> h[6], u[6], r2[3], w[6];
-        project_sm<MU, SF>(r, rg.ne, l + stl, h);
+        project_sm<MU, SF>(r, rg.ne, wc_idx(l + stl, rg.ne), h);
         P::load_link(U, g.V, MU, site, u, r2);
         su3_mul(u, r2, h, coef, w);
         reconstruct_add<MU, SF>(q, w);
     }
     if (lm >= 1) {
-        const int sb = (wbits & (1u << MU)) ? site + (g.L[MU] - 1) * g.stride[MU] : site - g.stride[MU];
+        const int sb = wc_idx((wbits & (1u << MU)) ? site + (g.L[MU] - 1) * g.stride[MU] : site - g.stride[MU], g.V);
         const float coef = (MU == 3 && (wbits & (1u << 3))) ? mk * (float)g.tbc : mk;
         cx<float> h[6], u[6], r2[3], w[6];
-        project_sm<MU, -SF>(r, rg.ne, l - stl, h);
+        project_sm<MU, -SF>(r, rg.ne, wc_idx(l - stl, rg.ne), h);
         P::load_link(U, g.V, MU, sb, u, r2);
         su3_adj_mul(u, r2, h, coef, w);
         reconstruct_add<MU, -SF>(q, w);
@@ -182,6 +182,12 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
     float4 *qs = r + 6 * rg.ne;                                      // [6][blockDim.x]
     float4 *xc = qs + 6 * blockDim.x;                                // [6][ncore]
     __shared__ float red[32 * 3];
+    if (kChecked) {   // every slot read before it is written shows up as NaN
+        const float nan = __int_as_float(0x7fc00000);
+        for (int q = threadIdx.x; q < 6 * (rg.ne + (int)blockDim.x + rg.ncore); q += blockDim.x)
+            r[q] = make_float4(nan, nan, nan, nan);
+        __syncthreads();
+    }
 
     // block origin
     int bc[4];
@@ -226,8 +232,8 @@ __global__ void __launch_bounds__(kRasMaxThreads, 1)
                 ci += cm * cs;
                 cs *= rg.b[m];
             }
-            gs[j] = site;
-            if (in_core) core[j] = ci;
+            gs[j] = wc_idx(site, g.V);
+            if (in_core) core[j] = wc_idx(ci, rg.ncore);
             // r = R v, x = 0
             cx<float> sp[12];
             P::load_spinor(vin, vin_nrm, V, site, sp);
@@ -482,6 +488,12 @@ __global__ void __cluster_dims__(kRasNC, 1, 1) __launch_bounds__(kRasCThreads, 1
     void *lk = r + 6 * np;                                                 // links
     float4 *xc = reinterpret_cast<float4 *>(static_cast<char *>(lk) + (size_t)RasLinks<P>::kBytes * np);   // [6][ncmax]
     __shared__ float red[32 * 3];
+    if (kChecked) {   // every slot read before it is written shows up as NaN
+        const float nan = __int_as_float(0x7fc00000);
+        const int nf4 = 6 * np + RasLinks<P>::kBytes / 16 * np + 6 * hg.ncmax;
+        for (int q = threadIdx.x; q < nf4; q += blockDim.x) r[q] = make_float4(nan, nan, nan, nan);
+        __syncthreads();
+    }
 
     // the neighbouring CTAs' images (distributed shared memory)
     constexpr int NC = kRasNC;
@@ -534,7 +546,8 @@ __global__ void __cluster_dims__(kRasNC, 1, 1) __launch_bounds__(kRasCThreads, 1
         }
         // core t slices of this CTA start at max(delta, rank h)
         const int t0 = max(rg.delta, rank * hg.h);
-        if (in_core) core = ci + (lc[3] - t0) * cs;
+        if (in_core) core = wc_idx(ci + (lc[3] - t0) * cs, hg.ncmax);
+        site = wc_idx(site, V);
         cx<float> sp[12];
         P::load_spinor(vin, vin_nrm, V, site, sp);
         sm_store(r, np, i, sp);
@@ -567,14 +580,14 @@ __global__ void __cluster_dims__(kRasNC, 1, 1) __launch_bounds__(kRasCThreads, 1
                 const int mu = hop >> 1;
                 const int st = mu == 0 ? 1 : (mu == 1 ? es1 : es2);
                 if (hop & 1) {
-                    const int j = i - st;
+                    const int j = wc_idx(i - st, hg.n);
                     switch (mu) {
                     case 0: ras_hop_c<P, 0, -SF, false>(r, lk, np, j, j, 1.f, q); break;
                     case 1: ras_hop_c<P, 1, -SF, false>(r, lk, np, j, j, 1.f, q); break;
                     default: ras_hop_c<P, 2, -SF, false>(r, lk, np, j, j, 1.f, q); break;
                     }
                 } else {
-                    const int j = i + st;
+                    const int j = wc_idx(i + st, hg.n);
                     switch (mu) {
                     case 0: ras_hop_c<P, 0, SF, true>(r, lk, np, j, i, 1.f, q); break;
                     case 1: ras_hop_c<P, 1, SF, true>(r, lk, np, j, i, 1.f, q); break;
@@ -584,15 +597,16 @@ __global__ void __cluster_dims__(kRasNC, 1, 1) __launch_bounds__(kRasCThreads, 1
             }
             if (hopmask & 64u) {
                 if (lt + 1 < hg.h)
-                    ras_hop_c<P, 3, SF, true, true>(r, lk, np, i + st3, i, ph_t_fwd, q);
+                    ras_hop_c<P, 3, SF, true, true>(r, lk, np, wc_idx(i + st3, hg.n), i, ph_t_fwd, q);
                 else   // last slice: neighbour in the next CTA's first slice
-                    ras_hop_c<P, 3, SF, true, true>(r_up, lk, np, i - lt * st3, i, ph_t_fwd, q);
+                    ras_hop_c<P, 3, SF, true, true>(r_up, lk, np, wc_idx(i - lt * st3, hg.n), i, ph_t_fwd, q);
             }
             if (hopmask & 128u) {
-                if (lt >= 1)
-                    ras_hop_c<P, 3, -SF, false, true>(r, lk, np, i - st3, i - st3, ph_t_bwd, q);
-                else {   // first slice: neighbour (and its link) in the previous CTA's last slice
-                    const int j = i + (hg.h - 1) * st3;
+                if (lt >= 1) {
+                    const int j = wc_idx(i - st3, hg.n);
+                    ras_hop_c<P, 3, -SF, false, true>(r, lk, np, j, j, ph_t_bwd, q);
+                } else {   // first slice: neighbour (and its link) in the previous CTA's last slice
+                    const int j = wc_idx(i + (hg.h - 1) * st3, hg.n);
                     ras_hop_c<P, 3, -SF, false, true>(r_dn, lk_dn, np, j, j, ph_t_bwd, q);
                 }
             }

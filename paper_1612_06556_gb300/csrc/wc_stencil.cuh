@@ -233,7 +233,7 @@ __device__ __forceinline__ void hops_rt(const Geom &g, const GaugeStore &U, cons
         const bool fwd = (hop & 1) == 0;
         const int L = g.L[mu], st = g.stride[mu];
         const bool wrap = ((fwd ? wf : wb) >> mu) & 1u;
-        const int y = fwd ? (wrap ? x - (L - 1) * st : x + st) : (wrap ? x + (L - 1) * st : x - st);
+        const int y = wc_idx(fwd ? (wrap ? x - (L - 1) * st : x + st) : (wrap ? x + (L - 1) * st : x - st), g.V);
         cx<R> p[12], h[6], u[6], r2[3], w[6];
         const R scale = P::load_spinor_raw(in, in_nrm, Vin, sidx(y), p);
         const R coef = ((mu == 3 && wrap) ? k * R(g.tbc) : k) * scale;
@@ -287,7 +287,7 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, cons
     const int L = g.L[MU], st = g.stride[MU];
     {
         const bool wrap = c[MU] == L - 1;
-        const int xf = wrap ? x - (L - 1) * st : x + st;
+        const int xf = wc_idx(wrap ? x - (L - 1) * st : x + st, g.V);
         cx<R> p[12], h[6], u[6], r2[3], w[6];
         const R scale = P::load_spinor_raw(in, in_nrm, g.V, xf, p);
         const R coef = ((MU == 3 && wrap) ? k * R(g.tbc) : k) * scale;
@@ -298,7 +298,7 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugeStore &U, cons
     }
     {
         const bool wrap = c[MU] == 0;
-        const int xb = wrap ? x + (L - 1) * st : x - st;
+        const int xb = wc_idx(wrap ? x + (L - 1) * st : x - st, g.V);
         cx<R> p[12], h[6], u[6], r2[3], w[6];
         const R scale = P::load_spinor_raw(in, in_nrm, g.V, xb, p);
         const R coef = ((MU == 3 && wrap) ? k * R(g.tbc) : k) * scale;
@@ -441,7 +441,7 @@ __device__ __forceinline__ void hop_dir_h16(const Geom &g, const GaugeStore &U, 
 #pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
         const bool wrap = dir == 0 ? c[MU] == L - 1 : c[MU] == 0;
-        const int y = dir == 0 ? (wrap ? x - (L - 1) * st : x + st) : (wrap ? x + (L - 1) * st : x - st);
+        const int y = wc_idx(dir == 0 ? (wrap ? x - (L - 1) * st : x + st) : (wrap ? x + (L - 1) * st : x - st), g.V);
         const uint4 s0 = __ldg(ps + y), s1 = __ldg(ps + (size_t)g.V + y), s2 = __ldg(ps + 2 * (size_t)g.V + y);
         const unsigned w[12] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w, s2.x, s2.y, s2.z, s2.w};
         const float coef = ((MU == 3 && wrap) ? k * (float)g.tbc : k) * __ldg(in_nrm + y);
@@ -468,8 +468,12 @@ __device__ __forceinline__ void apply_site_at(const Geom &g, int x, const GaugeS
                                               double kappa)
 {
     using R = typename P::real;
+    x = wc_idx(x, g.V);
     int c[4];
-    site_coords(g, x, c);
+    if constexpr (std::is_same<P, P16>::value)
+        site_coords_fast(g, x, c);
+    else
+        site_coords(g, x, c);
     cx<R> acc[12];
     if constexpr (std::is_same<P, PDF>::value) {
         // Six hops (directions y, z, t) in double-FP32 on the FP32 pipes, in

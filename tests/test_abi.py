@@ -102,3 +102,11 @@ def test_subdomain_argument_errors_without_a_gpu(lib):
         with __import__("pytest").raises(wc.WCError) as e:
             wc.SubDomain(local, glob, off)
         assert e.value.status == 1
+
+
+def test_checked_violations_needs_the_checked_build(lib):
+    """The normal build answers WC_ERR_STATE before touching the device."""
+    import paper_1612_06556_gb300 as wc
+    n = ctypes.c_ulonglong(7)
+    assert wc._L.wc_checked_violations(ctypes.byref(n)) == 3 and n.value == 0
+    assert wc._L.wc_checked_violations(None) == 1

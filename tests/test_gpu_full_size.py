@@ -68,7 +68,7 @@ def test_36_rhs_batch_on_three_lattices():
         assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
 
 
-@pytest.mark.parametrize("prec,tol", [(1, 2e-5), (2, 1e-2)])
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (2, 1.2e-3)])   # measured: 1.1e-7 / 3.3e-4 (L2), 2.3e-7 / 5.7e-4 (max)
 def test_ras_24x24x24x32_matches_oracle(prec, tol):
     """The RAS application of the 24^3x32 solve workload (4^4 blocks,
     overlap 1, 4 MR steps; 1728 blocks, the launch the bench times) on FP32

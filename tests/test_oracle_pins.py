@@ -193,6 +193,18 @@ def test_gauge_covariance_of_M_and_clover():
 # clover term closed forms
 # --------------------------------------------------------------------------
 
+def test_free_field_zero_mode_at_kappa_one_eighth():
+    """Unit links, fully periodic: H psi = 8 psi for a constant spinor (the
+    eight hops each return psi and (1 - g) + (1 + g) = 2), so M = 1 - H/8 at
+    kappa = 1/8 annihilates it -- the singular point the solvers' failure
+    tests use.  With the time boundary antiperiodic it is not a zero mode."""
+    dims = (4, 4, 4, 4)
+    U = synth.unit_links(dims)
+    const = np.tile(synth.gaussian_source((1, 1, 1, 1), 5), (synth.volume(dims), 1, 1))
+    assert np.max(np.abs(oracle.apply_M(dims, 1, 0.125, 1.7, U, const))) <= 1e-14
+    assert np.max(np.abs(oracle.apply_M(dims, -1, 0.125, 1.7, U, const))) > 0.1
+
+
 def test_clover_vanishes_on_unit_links():
     dims = (3, 4, 2, 5)
     T = oracle.clover_field(dims, 2.3, 0.13, synth.unit_links(dims))
