@@ -52,15 +52,15 @@ NCU_TRAFFIC = {
     # the other lexicographic shapes run the same kernel body), from the
     # capture summarised in profiles/apply_fp32_24x24x24x32.md; valid while
     # the operator's device sources hash to sources_sha
-    "sources_sha": "70b2bab09f81e2e1",
-    "bytes_per_launch": 294086912,
+    "sources_sha": "f83e0c25945f286f",
+    "bytes_per_launch": 293464320,
 }
 
 
 def kernel_sources_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1612_06556_gb300", "csrc")
-    for f in ("wc_dslash.cu", "wc_stencil.cuh", "wc_device.cuh", "wc_df.cuh"):
+    for f in ("wc_dslash.cu", "wc_stencil.cuh", "wc_device.cuh", "wc_df.cuh", "wc_check.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -313,6 +313,7 @@ def run_ours(args, world, rank, local):
     copy_gbs = copy_rate(BYTES_PER_SITE["f32"] * V, stream)
     multi = multi_rhs_apply(wc, lat, dims, ms / args.steps, stream)
     ras = ras_timing(wc, lat, dims, src, stream)
+    split = split_mult_timing(wc, dims, U, src, csw, kappa, tbc, stream, ms / args.steps)
     point = point_source_solve(wc)
     large = large_lattice(wc, args) if not args.skip_large else None
     batch = batch_comparison(wc, args) if not args.skip_batch else None
@@ -366,6 +367,7 @@ def run_ours(args, world, rank, local):
         line["force"] = force
     line["apply_multi"] = multi
     line["ras"] = ras
+    line["split_mult"] = split
     line["point_source_8x8x8x8"] = point
     if world == 1 and not args.skip_cpu:
         smp = OracleSampler(dims, U, src, csw, kappa, tbc, args.ref_seconds)
@@ -598,6 +600,79 @@ def ras_timing(wc, lat, dims, src, stream, reps=50):
         out[name] = {"ms": ms, "effective_tflops": tf, "frac_of_fp32_fma_peak": tf / peak}
         a.close()
         z.close()
+    return out
+
+
+def periodic_box(dims, a, start, extents):
+    """The box [start, start + extents) of a canonical [V, ...] array,
+    coordinates periodic (input slicing for the sub-domains)."""
+    lx, ly, lz, lt = dims
+    g = a.reshape((lt, lz, ly, lx) + a.shape[1:])
+    for m in range(4):
+        idx = np.arange(start[m], start[m] + extents[m]) % dims[m]
+        g = np.take(g, idx, axis=3 - m)
+    return np.ascontiguousarray(g).reshape((-1,) + a.shape[1:])
+
+
+def split_mult_timing(wc, dims, U, src, csw, kappa, tbc, stream, whole_ms, reps=100):
+    """The overlapped MULT (paper Sec. 2.2) on one GPU: the lattice cut in two
+    along t into sub-domains of half the time extent, each step timed by
+    itself on the stream -- halo pack of both sub-domains, the device copies
+    standing in for the exchange, interior and surface launches -- against
+    the whole-lattice FP32 apply.  On a multi-GPU machine the interior launch
+    would run while the buffers travel."""
+    import torch
+    lt = dims[3] // 2
+    local = (dims[0], dims[1], dims[2], lt)
+    subs, fin, fout, send, recv = [], [], [], [], []
+    for r in range(2):
+        off = (0, 0, 0, r * lt)
+        s = wc.SubDomain(local, dims, off, tbc, stream=stream)
+        s.load_gauge(periodic_box(dims, U, (0, 0, 0, off[3] - 1), (dims[0], dims[1], dims[2], lt + 2)))
+        s.load_clover(csw, kappa)
+        subs.append(s)
+        fin.append(s.field(wc.F32).load(periodic_box(dims, src, off, local)))
+        fout.append(s.field(wc.F32))
+        nb = s.halo_bytes(3)
+        send.append([None] * 6 + [torch.empty(nb // 4, dtype=torch.float32, device="cuda") for _ in range(2)])
+        recv.append([None] * 6 + [torch.empty(nb // 4, dtype=torch.float32, device="cuda") for _ in range(2)])
+
+    def pack():
+        for r in range(2):
+            subs[r].halo_pack(fin[r], send[r])
+
+    def exchange():
+        for r in range(2):
+            recv[r][7].copy_(send[1 - r][6])   # from the upper neighbour: its lower-face data
+            recv[r][6].copy_(send[1 - r][7])   # from the lower neighbour: its upper-face data
+
+    def interior():
+        for r in range(2):
+            subs[r].apply_interior(fout[r], fin[r])
+
+    def surface():
+        for r in range(2):
+            subs[r].apply_surface(fout[r], fin[r], recv[r])
+
+    out = {"cut": "t in two", "sub_domain": list(local), "face_bytes_per_direction": subs[0].halo_bytes(3)}
+    for name, fn in (("pack", pack), ("exchange_copies", exchange), ("interior", interior), ("surface", surface)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_us"] = 1000 * e0.elapsed_time(e1) / reps
+    out["split_total_us"] = out["pack_us"] + out["exchange_copies_us"] + out["interior_us"] + out["surface_us"]
+    out["whole_lattice_apply_us"] = 1000 * whole_ms
+    out["interior_share"] = out["interior_us"] / (out["pack_us"] + out["interior_us"] + out["surface_us"])
+    for f in fin + fout:
+        f.close()
+    for s in subs:
+        s.close()
     return out
 
 
@@ -864,6 +939,33 @@ def fp64_apply_timing(wc, lat, dims, src, stream, steps=60):
     return res
 
 
+def profile_run(args):
+    """A small, self-contained workload for ncu captures: the config-2 input
+    recipe on --profile-dims, warm-ups, then --steps launches of one kernel
+    (applies through the autotuned or pinned shape, or RAS with 4^4 blocks,
+    overlap 1, 4 MR steps)."""
+    import torch
+    import paper_1612_06556_gb300 as wc
+    import synth
+    dims = tuple(int(d) for d in args.profile_dims.split(","))
+    U = synth.haar_links(dims, 1002)
+    src = synth.z2_source(dims, 2002)
+    lat = wc.Lattice(dims, -1).load_gauge(U).load_clover(1.0, 0.125)
+    prec = {"f32": wc.F32, "f16": wc.F16, "f64": wc.F64}[args.profile_apply or args.profile_ras]
+    if args.profile_apply and args.apply_shape >= 0:
+        lat.apply_shape(prec, 0, args.apply_shape)
+    a, b = lat.field(prec).load(src), lat.field(prec)
+    step = (lambda: lat.apply_M(b, a)) if args.profile_apply else (lambda: lat.ras(b, a))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile_apply and "apply" or "ras", "prec": args.profile_apply or args.profile_ras,
+                      "dims": list(dims), "steps": args.steps}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -883,9 +985,17 @@ def main():
                     help="pin launch shape #N (0..21) of the timed applies instead of autotuning it")
     ap.add_argument("--large-solve", type=int, default=0,
                     help="also run the even-odd reliable-update solve of the 32^3x64 system (max steps)")
+    ap.add_argument("--profile-apply", choices=["f32", "f16", "f64"], default=None,
+                    help="run only --steps M applies of this precision on --profile-dims (for ncu captures)")
+    ap.add_argument("--profile-ras", choices=["f32", "f16"], default=None,
+                    help="run only --steps RAS applications on --profile-dims (for ncu captures)")
+    ap.add_argument("--profile-dims", default="24,24,24,32")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.profile_apply or args.profile_ras:
+        profile_run(args)
+        return
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
