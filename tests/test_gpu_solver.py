@@ -24,6 +24,7 @@ pytestmark = pytest.mark.gpu
     ((12, 8, 8, 8), (3, 2, 2, 2), 1, 3),
     ((8, 8, 8, 6), (4, 4, 4, 3), 1, 4),   # odd extended t extent: the one-CTA kernel
     ((8, 8, 8, 8), (2, 2, 2, 2), 2, 2),   # overlap 2: one core t slice per CTA of the pair
+    ((8, 8, 9, 8), (4, 4, 3, 4), 1, 4),   # odd extended z: the one-site-per-thread cluster kernel
 ])
 @pytest.mark.parametrize("prec", [1, 2])
 def test_ras_matches_oracle(dims, block, delta, k, prec):
