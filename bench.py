@@ -428,8 +428,9 @@ def batch_comparison(wc, args):
     24^3x48, 16^3x32 and 32^3x32, each lattice with its own exp(0.3 iH)
     gauge field) to 1e-10 with FP32 RAS (block shapes from the autotuner):
     one graph-launched batch (reliable-update solver; also the flexible FP64
-    outer solver, and the even-odd reliable-update solver without RAS) vs 36
-    sequential solves on the same GPU."""
+    outer solver, and the even-odd reliable-update solver without RAS, whose
+    12 sources per lattice step in lockstep groups, timed also with one
+    branch per right-hand side) vs 36 sequential solves on the same GPU."""
     import synth
     cfg = synth.CONFIGS[4]
     lats, bs, srcs = [], [], []
@@ -465,10 +466,22 @@ def batch_comparison(wc, args):
                          delta=0.01, even_odd=True)
     run_batch(eo)                           # warm-up: clover inverses, half-lattice fields
     infos_eo, t_eo = run_batch(eo)
+    # the same batch with one graph branch per right-hand side instead of
+    # lockstep groups (one multi-RHS Schur launch per group and step)
+    os.environ["WC_BATCH_LOCKSTEP"] = "0"
+    try:
+        infos_eo_br, t_eo_br = run_batch(eo)
+    finally:
+        del os.environ["WC_BATCH_LOCKSTEP"]
     eo_h16 = wc.solve_params(tol=1e-10, max_iter=5000, precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE,
                              delta=0.01, krylov_prec=wc.F16, even_odd=True)
     run_batch(eo_h16)
     infos_eo_h16, t_eo_h16 = run_batch(eo_h16)
+    os.environ["WC_BATCH_LOCKSTEP"] = "0"
+    try:
+        infos_eo_h16_br, t_eo_h16_br = run_batch(eo_h16)
+    finally:
+        del os.environ["WC_BATCH_LOCKSTEP"]
     # the same with the FP64 operator steps in double-FP32 arithmetic
     for lat in lats[::12]:
         lat.set_fp64_arith(wc.ARITH_DF32)
@@ -506,6 +519,10 @@ def batch_comparison(wc, args):
             "flexible_batch_seconds": t_flex, "flexible_all_ok": all(i.status == 0 for i in infos_flex),
             "flexible_steps": [min(i.iters for i in infos_flex), max(i.iters for i in infos_flex)],
             "even_odd_batch_seconds": t_eo, "even_odd_all_ok": all(i.status == 0 for i in infos_eo),
+            "even_odd_branch_per_rhs_batch_seconds": t_eo_br,
+            "even_odd_branch_per_rhs_all_ok": all(i.status == 0 for i in infos_eo_br),
+            "even_odd_fp16_vectors_branch_per_rhs_batch_seconds": t_eo_h16_br,
+            "even_odd_fp16_vectors_branch_per_rhs_all_ok": all(i.status == 0 for i in infos_eo_h16_br),
             "even_odd_sequential_seconds": t_seq_eo, "even_odd_sequential_all_ok": all(i.status == 0 for i in seq_eo),
             "even_odd_fp16_vectors_batch_seconds": t_eo_h16,
             "even_odd_fp16_vectors_all_ok": all(i.status == 0 for i in infos_eo_h16),
@@ -951,18 +968,27 @@ def profile_run(args):
     U = synth.haar_links(dims, 1002)
     src = synth.z2_source(dims, 2002)
     lat = wc.Lattice(dims, -1).load_gauge(U).load_clover(1.0, 0.125)
-    prec = {"f32": wc.F32, "f16": wc.F16, "f64": wc.F64}[args.profile_apply or args.profile_ras]
+    prec = {"f32": wc.F32, "f16": wc.F16, "f64": wc.F64}[args.profile_apply or args.profile_ras or
+                                                         args.profile_schur_multi]
     if args.profile_apply and args.apply_shape >= 0:
         lat.apply_shape(prec, 0, args.apply_shape)
     a, b = lat.field(prec).load(src), lat.field(prec)
-    step = (lambda: lat.apply_M(b, a)) if args.profile_apply else (lambda: lat.ras(b, a))
+    if args.profile_schur_multi:
+        ins = [lat.field(prec).load(synth.point_source(dims, spin=k % 4, colour=k // 4)) for k in range(12)]
+        outs = [lat.field(prec) for _ in range(12)]
+        step = lambda: lat.apply_schur_multi(outs, ins)   # noqa: E731
+    elif args.profile_apply:
+        step = lambda: lat.apply_M(b, a)   # noqa: E731
+    else:
+        step = lambda: lat.ras(b, a)   # noqa: E731
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     for _ in range(args.steps):
         step()
     torch.cuda.synchronize()
-    print(json.dumps({"profile": args.profile_apply and "apply" or "ras", "prec": args.profile_apply or args.profile_ras,
+    print(json.dumps({"profile": "apply" if args.profile_apply else ("ras" if args.profile_ras else "schur_multi"),
+                      "prec": args.profile_apply or args.profile_ras or args.profile_schur_multi,
                       "dims": list(dims), "steps": args.steps}))
 
 
@@ -989,11 +1015,13 @@ def main():
                     help="run only --steps M applies of this precision on --profile-dims (for ncu captures)")
     ap.add_argument("--profile-ras", choices=["f32", "f16"], default=None,
                     help="run only --steps RAS applications on --profile-dims (for ncu captures)")
+    ap.add_argument("--profile-schur-multi", choices=["f32", "f16"], default=None,
+                    help="run only --steps multi-RHS Schur applications (12 fields) on --profile-dims")
     ap.add_argument("--profile-dims", default="24,24,24,32")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.profile_apply or args.profile_ras:
+    if args.profile_apply or args.profile_ras or args.profile_schur_multi:
         profile_run(args)
         return
     world, rank, local = dist_setup()

@@ -282,6 +282,16 @@ wc_status wc_apply_schur(wc_lattice lat, wc_field out, wc_field in, int dagger);
  * operator's shape, which is chosen separately from the FP64 one. */
 wc_status wc_apply_shape(wc_lattice lat, wc_prec prec, int kind, int force_index, int shape_out[6]);
 
+/* outs[r] (even sites) = M^ ins[r] (even sites), M^ = A_ee - kappa^2 H_eo
+ * A_oo^-1 H_oe (M^+ with dagger = 1), odd sites of outs[r] set to zero, for
+ * 1 <= n <= 16 full-lattice FP32 or FP16 fields of one precision (all
+ * extents even).  One odd-site and one even-site pass serve all n fields:
+ * the links, A and A^-1 of a site are read once for every field (the
+ * right-hand sides of a propagator share them; paper Sec. 2: the solvers
+ * act on the even-odd preconditioned matrix).  outs must be distinct from
+ * each other and from ins.  Blocking. */
+wc_status wc_apply_schur_multi(wc_lattice lat, int n, wc_field *outs, wc_field *ins, int dagger);
+
 /* ---- fused BLAS-1 (FP64 accumulation; blocking) ---------------------- */
 
 /* re_im[0] + i re_im[1] = <a, b> = sum conj(a) b over all sites */

@@ -21,6 +21,15 @@
 //                            rho, beta recomputed }            for every i
 //       check 2: converged (true residual) or max_iter -> inactive
 //
+// Lockstep groups (reliable update without a preconditioner on the half
+// lattices of an even-odd batch): the right-hand sides of one lattice -- the
+// sources of a propagator -- step together in one IF branch per group, and
+// each step's two Schur applications are one multi-right-hand-side launch
+// for the whole group (links, A and A^-1 read once per site for all of
+// them), each of its five vector updates one launch over all members.  A member that has stopped keeps its place: the check kernels set
+// the skip word of its solver scalars, and its step kernels (and its part
+// of the multi-RHS launch) return at once.
+//
 // Each branch is captured from the same enqueue code the single-RHS solves
 // use, on that RHS's own solver state (scalars, reduction scratch, work
 // vectors), so branches share nothing but the read-only gauge field and
@@ -33,6 +42,7 @@
 // lattice extent and inner precision by a small autotuner (candidate shapes
 // timed on a short trial solve, result cached for the process).
 #include <math.h>
+#include <stdlib.h>
 
 #include <chrono>
 #include <map>
@@ -51,7 +61,7 @@ bool ras_fits(const wc_ras_params &p);
 namespace {
 
 struct BatchItem {
-    const SolverScalars *scal;
+    SolverScalars *scal;
     double tol2;    // tol^2 |b|^2
     double d2;      // delta^2 (reliable update)
     int max_iter;
@@ -65,9 +75,14 @@ struct BatchDev {
     int *active;
     int *refresh;
     double *rmax2;
-    const cudaGraphConditionalHandle *h_iter;
+    const cudaGraphConditionalHandle *h_iter;   // per RHS outside lockstep groups
     const cudaGraphConditionalHandle *h_ref;
+    const int *group;                           // per RHS: lockstep group, -1 if none
+    const cudaGraphConditionalHandle *h_group;  // per group
+    int ngroups;
 };
+
+constexpr int kMaxGroups = 64;
 
 // After the BiCGStab steps.  Flexible: decide which RHS continue and set
 // the WHILE condition.  Reliable: decide which RHS refresh now.
@@ -87,6 +102,7 @@ __global__ void k_batch_check_iter(BatchDev d, int n, int reliable, cudaGraphCon
                 if (!(s.rr > it.tol2) || s.flags != 0 || k >= it.max_iter) a = 0;
             } else if (s.flags != 0) {
                 a = 0;   // breakdown / NaN: the host takes over
+                if (d.group[i] >= 0) it.scal->skip = 1;
             } else {
                 if (s.rr > d.rmax2[i]) d.rmax2[i] = s.rr;
                 ref = (s.rr <= it.d2 * d.rmax2[i] || s.rr <= it.tol2 || k >= it.max_iter) ? 1 : 0;
@@ -106,11 +122,14 @@ __global__ void k_batch_check_iter(BatchDev d, int n, int reliable, cudaGraphCon
 }
 
 // Reliable update only, after the refreshes: stop converged RHS (FP64 true
-// residual) and RHS at max_iter; set the IF and WHILE conditions.
+// residual) and RHS at max_iter; set the IF conditions (per RHS, or per
+// lockstep group with the members' skip words) and the WHILE condition.
 __global__ void k_batch_check_refresh(BatchDev d, int n, cudaGraphConditionalHandle wh)
 {
     __shared__ int any;
+    __shared__ int gany[kMaxGroups];
     if (threadIdx.x == 0) any = 0;
+    for (int g = threadIdx.x; g < d.ngroups; g += blockDim.x) gany[g] = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const BatchItem &it = d.items[i];
@@ -121,10 +140,17 @@ __global__ void k_batch_check_refresh(BatchDev d, int n, cudaGraphConditionalHan
             d.rmax2[i] = rr;
             d.active[i] = a;
         }
-        cudaGraphSetConditional(d.h_iter[i], a ? 1u : 0u);
+        const int g = d.group[i];
+        if (g >= 0) {
+            it.scal->skip = a ? 0 : 1;
+            if (a) atomicOr(&gany[g], 1);
+        } else {
+            cudaGraphSetConditional(d.h_iter[i], a ? 1u : 0u);
+        }
         if (a) atomicOr(&any, 1);
     }
     __syncthreads();
+    for (int g = threadIdx.x; g < d.ngroups; g += blockDim.x) cudaGraphSetConditional(d.h_group[g], gany[g] ? 1u : 0u);
     if (threadIdx.x == 0) cudaGraphSetConditional(wh, any ? 1u : 0u);
 }
 
@@ -134,9 +160,10 @@ struct Resources {
     std::vector<LoVecs> LW;
     std::vector<cudaStream_t> streams;
     BatchItem *d_items = nullptr;
-    int *d_iters = nullptr, *d_active = nullptr, *d_refresh = nullptr;
+    int *d_iters = nullptr, *d_active = nullptr, *d_refresh = nullptr, *d_group = nullptr;
     double *d_rmax2 = nullptr;
-    cudaGraphConditionalHandle *d_hiter = nullptr, *d_href = nullptr;
+    cudaGraphConditionalHandle *d_hiter = nullptr, *d_href = nullptr, *d_hgroup = nullptr;
+    std::vector<LoMember *> d_members;   // per lockstep group
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 
@@ -153,6 +180,9 @@ struct Resources {
         cudaFree(d_rmax2);
         cudaFree(d_hiter);
         cudaFree(d_href);
+        cudaFree(d_group);
+        cudaFree(d_hgroup);
+        for (auto m : d_members) cudaFree(m);
         for (auto &s : S) state_free(s);
         for (auto s : streams)
             if (s) cudaStreamDestroy(s);
@@ -183,17 +213,17 @@ wc_status create_handles(cudaGraph_t parent, int n, const std::vector<int> &init
 }
 
 // One IF node per handle, each depending on deps, whose body holds the
-// launches `enqueue(i)` queues on stream i while that stream is captured.
+// launches `enqueue(k)` queues on the stream of right-hand side idx[k]
+// while that stream is captured.
 template <class Enqueue>
 wc_status add_if_nodes(cudaGraph_t parent, const std::vector<cudaGraphNode_t> &deps,
-                       const std::vector<cudaGraphConditionalHandle> &handles, Resources &R, Enqueue enqueue,
-                       std::vector<cudaGraphNode_t> *nodes)
+                       const std::vector<cudaGraphConditionalHandle> &handles, const std::vector<int> &idx,
+                       Resources &R, Enqueue enqueue, std::vector<cudaGraphNode_t> *nodes)
 {
-    nodes->clear();
-    for (size_t i = 0; i < handles.size(); ++i) {
+    for (size_t k = 0; k < handles.size(); ++k) {
         cudaGraphNodeParams ip = {};
         ip.type = cudaGraphNodeTypeConditional;
-        ip.conditional.handle = handles[i];
+        ip.conditional.handle = handles[k];
         ip.conditional.type = cudaGraphCondTypeIf;
         ip.conditional.size = 1;
         cudaGraphNode_t node;
@@ -201,12 +231,12 @@ wc_status add_if_nodes(cudaGraph_t parent, const std::vector<cudaGraphNode_t> &d
                                                             nullptr, deps.size(), &ip), "add IF node");
         if (st != WC_OK) return st;
         nodes->push_back(node);
-        cudaStream_t s = R.streams[i];
+        cudaStream_t s = R.streams[idx[k]];
         st = check_cuda(nullptr, cudaStreamBeginCaptureToGraph(s, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                                cudaStreamCaptureModeRelaxed),
                         "cudaStreamBeginCaptureToGraph");
         if (st != WC_OK) return st;
-        const wc_status est = enqueue((int)i);
+        const wc_status est = enqueue((int)k);
         cudaGraph_t captured = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(s, &captured);
         if (est != WC_OK) return est;
@@ -214,6 +244,52 @@ wc_status add_if_nodes(cudaGraph_t parent, const std::vector<cudaGraphNode_t> &d
         if (st != WC_OK) return st;
     }
     return WC_OK;
+}
+
+// Lockstep groups are on unless WC_BATCH_LOCKSTEP=0 (which keeps one branch
+// per right-hand side, e.g. to compare the two schedules).
+bool lockstep_enabled()
+{
+    const char *e = getenv("WC_BATCH_LOCKSTEP");
+    return !(e && e[0] == '0');
+}
+
+// One lockstep step of the reliable update for the right-hand sides idx of
+// one half lattice, queued on stream s: each of the five vector updates is
+// one launch for all members (member table dm on the device), each of the
+// two Schur applications one multi-right-hand-side launch; the kernels of a
+// stopped member return at once (its skip word).
+wc_status enqueue_group_step(wc_lattice half, const std::vector<int> &idx, Resources &R, const LoMember *dm,
+                             cudaStream_t s)
+{
+    const int m = (int)idx.size();
+    std::vector<wc_field> p(m), v(m), sv(m), t(m), tmp(m);
+    std::vector<const int *> skip(m);
+    for (int k = 0; k < m; ++k) {
+        const int i = idx[k];
+        const LoVecs &w = R.LW[i];
+        p[k] = w.phat;
+        v[k] = w.v;
+        sv[k] = w.shat;
+        t[k] = w.t;
+        tmp[k] = R.S[i].work[kSchurSlot + w.v->prec];
+        skip[k] = &R.S[i].scal->skip;
+        if (!tmp[k]) return set_error(half, WC_ERR_STATE, "lockstep: no odd-site intermediate");
+    }
+    const bool hv = R.LW[idx[0]].v->prec == WC_F16;
+    const int mb = R.S[idx[0]].red.max_blocks;
+    wc_status st = check_cuda(half, lo_group(LO_STEP_P, half, m, dm, hv, mb, s), "lo_p");
+    if (st == WC_OK)
+        st = check_cuda(half, launch_schur_multi(half, m, v.data(), p.data(), tmp.data(), 0, skip.data(), s),
+                        "schur_multi");
+    if (st == WC_OK) st = check_cuda(half, lo_group(LO_STEP_ALPHA, half, m, dm, hv, mb, s), "lo_alpha");
+    if (st == WC_OK) st = check_cuda(half, lo_group(LO_STEP_S, half, m, dm, hv, mb, s), "lo_s");
+    if (st == WC_OK)
+        st = check_cuda(half, launch_schur_multi(half, m, t.data(), sv.data(), tmp.data(), 0, skip.data(), s),
+                        "schur_multi");
+    if (st == WC_OK) st = check_cuda(half, lo_group(LO_STEP_OMEGA, half, m, dm, hv, mb, s), "lo_omega");
+    if (st == WC_OK) st = check_cuda(half, lo_group(LO_STEP_XR, half, m, dm, hv, mb, s), "lo_xr");
+    return st;
 }
 
 wc_status add_kernel_node(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, void *func, void **args,
@@ -431,6 +507,43 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
         }
     }
 
+    // lockstep groups: reliable update without a preconditioner on a half
+    // lattice, right-hand sides of the same lattice, up to kMrhsMax a group
+    std::vector<int> group(n, -1);
+    std::vector<std::vector<int>> members;
+    if (reliable && lockstep_enabled()) {
+        std::map<std::pair<wc_lattice, int>, int> open;   // (lattice, precision) -> group being filled
+        for (int i = 0; i < n; ++i) {
+            if (P[i].precond != WC_PRECOND_NONE || !lats[i]->schur_parent) continue;
+            const int pr = (int)R.LW[i].v->prec;
+            if (pr != WC_F32 && pr != WC_F16) continue;
+            const auto key = std::make_pair(lats[i], pr);
+            auto it = open.find(key);
+            if (it == open.end() || (int)members[it->second].size() == kMrhsMax) {
+                if ((int)members.size() == kMaxGroups) continue;
+                open[key] = (int)members.size();
+                members.emplace_back();
+                it = open.find(key);
+            }
+            group[i] = it->second;
+            members[it->second].push_back(i);
+        }
+        // a group of one gains nothing: back to its own branch
+        for (auto &m : members)
+            if (m.size() == 1) {
+                group[m[0]] = -1;
+                m.clear();
+            }
+        std::vector<std::vector<int>> kept;
+        for (auto &m : members)
+            if (!m.empty()) {
+                for (int i : m) group[i] = (int)kept.size();
+                kept.push_back(m);
+            }
+        members.swap(kept);
+    }
+    const int ngroups = (int)members.size();
+
     if (any) {
         std::vector<BatchItem> items(n);
         for (int i = 0; i < n; ++i) {
@@ -442,6 +555,22 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
         if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_active, active), "copy");
         if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_refresh, zeros), "copy");
         if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_rmax2, rmax2), "copy");
+        if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_group, group), "copy");
+        R.d_members.assign(ngroups, nullptr);
+        for (int g = 0; g < ngroups && st == WC_OK; ++g) {
+            std::vector<LoMember> tab;
+            for (int i : members[g]) {
+                const LoVecs &w = R.LW[i];
+                tab.push_back(lo_member(R.S[i], w.r, w.rhat, w.p, w.v, w.s, w.t, w.phat, w.shat, w.xlo));
+            }
+            st = check_cuda(nullptr, to_device(&R.d_members[g], tab), "copy");
+        }
+        // a member that starts inactive skips from the first step
+        const int one = 1;
+        for (int i = 0; i < n && st == WC_OK; ++i)
+            if (group[i] >= 0 && !active[i])
+                st = check_cuda(nullptr, cudaMemcpy(&R.S[i].scal->skip, &one, sizeof(int), cudaMemcpyHostToDevice),
+                                "copy");
         // top level: one WHILE node
         if (st == WC_OK) st = check_cuda(nullptr, cudaGraphCreate(&R.graph, 0), "cudaGraphCreate");
         cudaGraphConditionalHandle wh = 0;
@@ -460,26 +589,48 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
             if (st == WC_OK) body = wp.conditional.phGraph_out[0];
         }
         // body: IF(active_i){step_i} -> check_iter [-> IF(refresh_i){refresh_i} -> check_refresh]
-        std::vector<cudaGraphConditionalHandle> h_iter, h_ref;
+        //       IF(group g any active){lockstep step of group g}
+        std::vector<cudaGraphConditionalHandle> h_iter(n, 0), h_ref, h_grp, h_own;
+        std::vector<int> own, own_active, grp_lead, grp_active(ngroups, 0), all(n);
+        for (int i = 0; i < n; ++i) {
+            all[i] = i;
+            if (group[i] < 0) {
+                own.push_back(i);
+                own_active.push_back(active[i]);
+            } else if (active[i]) {
+                grp_active[group[i]] = 1;
+            }
+        }
+        for (const auto &m : members) grp_lead.push_back(m[0]);
         std::vector<cudaGraphNode_t> iter_nodes, ref_nodes;
-        if (st == WC_OK) st = create_handles(body, n, active, &h_iter);
+        if (st == WC_OK) st = create_handles(body, (int)own.size(), own_active, &h_own);
+        if (st == WC_OK) st = create_handles(body, ngroups, grp_active, &h_grp);
+        for (size_t k = 0; k < own.size() && st == WC_OK; ++k) h_iter[own[k]] = h_own[k];
         if (st == WC_OK && reliable) st = create_handles(body, n, zeros, &h_ref);
         if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_hiter, h_iter), "copy");
         if (st == WC_OK && reliable) st = check_cuda(nullptr, to_device(&R.d_href, h_ref), "copy");
-        BatchDev dev{R.d_items, R.d_iters, R.d_active, R.d_refresh, R.d_rmax2, R.d_hiter, R.d_href};
+        if (st == WC_OK && ngroups > 0) st = check_cuda(nullptr, to_device(&R.d_hgroup, h_grp), "copy");
+        BatchDev dev{R.d_items, R.d_iters, R.d_active, R.d_refresh, R.d_rmax2, R.d_hiter, R.d_href,
+                     R.d_group, R.d_hgroup, ngroups};
         int reliable_i = reliable ? 1 : 0;
         void *args1[] = {&dev, &n, &reliable_i, &wh};
         void *args2[] = {&dev, &n, &wh};
         if (st == WC_OK)
-            st = add_if_nodes(body, {}, h_iter, R, [&](int i) {
+            st = add_if_nodes(body, {}, h_own, own, R, [&](int k) {
+                const int i = own[k];
                 return reliable ? enqueue_lo_iteration(lats[i], R.S[i], P[i], 0, R.LW[i])
                                 : enqueue_iteration(lats[i], R.S[i], P[i], 0, xs[i], R.W[i]);
+            }, &iter_nodes);
+        if (st == WC_OK)
+            st = add_if_nodes(body, {}, h_grp, grp_lead, R, [&](int g) {
+                return enqueue_group_step(lats[members[g][0]], members[g], R, R.d_members[g],
+                                          R.streams[members[g][0]]);
             }, &iter_nodes);
         cudaGraphNode_t check1 = nullptr, check2 = nullptr;
         if (st == WC_OK)
             st = add_kernel_node(body, iter_nodes, reinterpret_cast<void *>(k_batch_check_iter), args1, &check1);
         if (st == WC_OK && reliable) {
-            st = add_if_nodes(body, {check1}, h_ref, R, [&](int i) {
+            st = add_if_nodes(body, {check1}, h_ref, all, R, [&](int i) {
                 return enqueue_refresh_full(lats[i], R.S[i], 0, xs[i], bs[i], R.W[i].r, R.LW[i]);
             }, &ref_nodes);
             if (st == WC_OK)
@@ -492,6 +643,10 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
         if (st == WC_OK)
             st = check_cuda(nullptr, cudaMemcpy(iters.data(), R.d_iters, sizeof(int) * n, cudaMemcpyDeviceToHost),
                             "copy");
+        // the host-driven continuation below runs the same step kernels
+        for (int i = 0; i < n && st == WC_OK; ++i)
+            if (group[i] >= 0)
+                st = check_cuda(nullptr, cudaMemset(&R.S[i].scal->skip, 0, sizeof(int)), "memset");
         if (st != WC_OK) return st;
     }
 

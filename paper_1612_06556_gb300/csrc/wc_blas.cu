@@ -8,6 +8,8 @@
 // ticket resets itself, so no memset is needed between launches.
 #include <math.h>
 
+#include <algorithm>
+
 #include "wc_internal.cuh"
 #include "wc_solver_kernels.cuh"
 
@@ -590,9 +592,10 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_init(long long n, const float4
 }
 
 // p = r + beta (p - omega v)
-__global__ void __launch_bounds__(kRedBlock) k_lo_p(long long n, const float4 *r, const float4 *v, float4 *p,
+__device__ __forceinline__ void body_lo_p(long long n, const float4 *r, const float4 *v, float4 *p,
                                                     const SolverScalars *sc)
 {
+    if (sc->skip) return;   // a stopped right-hand side of a lockstep batch
     const cx<float> beta = mkc((float)sc->beta.x, (float)sc->beta.y);
     const cx<float> omega = mkc((float)sc->omega.x, (float)sc->omega.y);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -606,11 +609,17 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_p(long long n, const float4 *r
         st4(p, i, p0, p1);
     }
 }
+__global__ void __launch_bounds__(kRedBlock) k_lo_p(long long n, const float4 *r, const float4 *v, float4 *p,
+                                                    const SolverScalars *sc)
+{
+    body_lo_p(n, r, v, p, sc);
+}
 
 // alpha = rho / <rhat, v>
-__global__ void __launch_bounds__(kRedBlock) k_lo_alpha(long long n, const float4 *rhat, const float4 *v,
+__device__ __forceinline__ void body_lo_alpha(long long n, const float4 *rhat, const float4 *v,
                                                         ReduceScratch rs, SolverScalars *sc)
 {
+    if (sc->skip) return;   // a stopped right-hand side of a lockstep batch
     float acc[2] = {0.f, 0.f};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -620,11 +629,17 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_alpha(long long n, const float
     }
     if (grid_reduce_f<2>(acc, rs, rs.result)) lo_alpha_update(rs.result, sc);
 }
+__global__ void __launch_bounds__(kRedBlock) k_lo_alpha(long long n, const float4 *rhat, const float4 *v,
+                                                        ReduceScratch rs, SolverScalars *sc)
+{
+    body_lo_alpha(n, rhat, v, rs, sc);
+}
 
 // s = r - alpha v
-__global__ void __launch_bounds__(kRedBlock) k_lo_s(long long n, const float4 *r, const float4 *v, float4 *s,
+__device__ __forceinline__ void body_lo_s(long long n, const float4 *r, const float4 *v, float4 *s,
                                                     const SolverScalars *sc)
 {
+    if (sc->skip) return;   // a stopped right-hand side of a lockstep batch
     const cx<float> alpha = mkc((float)sc->alpha.x, (float)sc->alpha.y);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -634,11 +649,17 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_s(long long n, const float4 *r
         st4(s, i, r0 - alpha * v0, r1 - alpha * v1);
     }
 }
+__global__ void __launch_bounds__(kRedBlock) k_lo_s(long long n, const float4 *r, const float4 *v, float4 *s,
+                                                    const SolverScalars *sc)
+{
+    body_lo_s(n, r, v, s, sc);
+}
 
 // omega = <t, s> / <t, t>
-__global__ void __launch_bounds__(kRedBlock) k_lo_omega(long long n, const float4 *t, const float4 *s,
+__device__ __forceinline__ void body_lo_omega(long long n, const float4 *t, const float4 *s,
                                                         ReduceScratch rs, SolverScalars *sc)
 {
+    if (sc->skip) return;   // a stopped right-hand side of a lockstep batch
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -650,13 +671,19 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_omega(long long n, const float
     }
     if (grid_reduce_f<4>(acc, rs, rs.result)) lo_omega_update(rs.result, sc);
 }
+__global__ void __launch_bounds__(kRedBlock) k_lo_omega(long long n, const float4 *t, const float4 *s,
+                                                        ReduceScratch rs, SolverScalars *sc)
+{
+    body_lo_omega(n, t, s, rs, sc);
+}
 
 // xlo += alpha phat + omega shat; r = s - omega t; rho' = <rhat, r>, rr = |r|^2
-__global__ void __launch_bounds__(kRedBlock) k_lo_xr(long long n, float4 *xlo, const float4 *phat,
+__device__ __forceinline__ void body_lo_xr(long long n, float4 *xlo, const float4 *phat,
                                                      const float4 *shat, const float4 *s, const float4 *t,
                                                      float4 *r, const float4 *rhat, ReduceScratch rs,
                                                      SolverScalars *sc)
 {
+    if (sc->skip) return;   // a stopped right-hand side of a lockstep batch
     const cx<float> alpha = mkc((float)sc->alpha.x, (float)sc->alpha.y);
     const cx<float> omega = mkc((float)sc->omega.x, (float)sc->omega.y);
     float acc[3] = {0.f, 0.f, 0.f};
@@ -679,6 +706,13 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_xr(long long n, float4 *xlo, c
         acc[2] += r0.re * r0.re + r0.im * r0.im + r1.re * r1.re + r1.im * r1.im;
     }
     if (grid_reduce_f<3>(acc, rs, rs.result)) lo_xr_update(rs.result, sc);
+}
+__global__ void __launch_bounds__(kRedBlock) k_lo_xr(long long n, float4 *xlo, const float4 *phat,
+                                                     const float4 *shat, const float4 *s, const float4 *t,
+                                                     float4 *r, const float4 *rhat, ReduceScratch rs,
+                                                     SolverScalars *sc)
+{
+    body_lo_xr(n, xlo, phat, shat, s, t, r, rhat, rs, sc);
 }
 
 // r was replaced by the true residual: rho = <rhat, r>,
@@ -734,8 +768,9 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_init_h(int V, HF r, HF rhat, H
     if (grid_reduce_f<1>(acc, rs, rs.result)) lo_init_update(rs.result, sc);
 }
 
-__global__ void __launch_bounds__(kRedBlock) k_lo_p_h(int V, HF r, HF v, HF p, const SolverScalars *sc)
+__device__ __forceinline__ void body_lo_p_h(int V, HF r, HF v, HF p, const SolverScalars *sc)
 {
+    if (sc->skip) return;   // a stopped right-hand side of a lockstep batch
     const cx<float> beta = mkc((float)sc->beta.x, (float)sc->beta.y);
     const cx<float> omega = mkc((float)sc->omega.x, (float)sc->omega.y);
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
@@ -748,6 +783,10 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_p_h(int V, HF r, HF v, HF p, c
         hst(p, V, x, c);
     }
 }
+__global__ void __launch_bounds__(kRedBlock) k_lo_p_h(int V, HF r, HF v, HF p, const SolverScalars *sc)
+{
+    body_lo_p_h(V, r, v, p, sc);
+}
 
 // acc[0] + i acc[1] += <a, b> over 12 components
 __device__ __forceinline__ void cdot_acc(const cx<float> a[12], const cx<float> b[12], float acc[2])
@@ -759,9 +798,10 @@ __device__ __forceinline__ void cdot_acc(const cx<float> a[12], const cx<float> 
     }
 }
 
-__global__ void __launch_bounds__(kRedBlock) k_lo_alpha_h(int V, HF rhat, HF v, ReduceScratch rs,
+__device__ __forceinline__ void body_lo_alpha_h(int V, HF rhat, HF v, ReduceScratch rs,
                                                           SolverScalars *sc)
 {
+    if (sc->skip) return;   // a stopped right-hand side of a lockstep batch
     float acc[2] = {0.f, 0.f};
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
         cx<float> a[12], b[12];
@@ -771,9 +811,15 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_alpha_h(int V, HF rhat, HF v, 
     }
     if (grid_reduce_f<2>(acc, rs, rs.result)) lo_alpha_update(rs.result, sc);
 }
-
-__global__ void __launch_bounds__(kRedBlock) k_lo_s_h(int V, HF r, HF v, HF s, const SolverScalars *sc)
+__global__ void __launch_bounds__(kRedBlock) k_lo_alpha_h(int V, HF rhat, HF v, ReduceScratch rs,
+                                                          SolverScalars *sc)
 {
+    body_lo_alpha_h(V, rhat, v, rs, sc);
+}
+
+__device__ __forceinline__ void body_lo_s_h(int V, HF r, HF v, HF s, const SolverScalars *sc)
+{
+    if (sc->skip) return;   // a stopped right-hand side of a lockstep batch
     const cx<float> alpha = mkc((float)sc->alpha.x, (float)sc->alpha.y);
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
         cx<float> a[12], b[12];
@@ -784,9 +830,14 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_s_h(int V, HF r, HF v, HF s, c
         hst(s, V, x, a);
     }
 }
-
-__global__ void __launch_bounds__(kRedBlock) k_lo_omega_h(int V, HF t, HF s, ReduceScratch rs, SolverScalars *sc)
+__global__ void __launch_bounds__(kRedBlock) k_lo_s_h(int V, HF r, HF v, HF s, const SolverScalars *sc)
 {
+    body_lo_s_h(V, r, v, s, sc);
+}
+
+__device__ __forceinline__ void body_lo_omega_h(int V, HF t, HF s, ReduceScratch rs, SolverScalars *sc)
+{
+    if (sc->skip) return;   // a stopped right-hand side of a lockstep batch
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
         cx<float> a[12], b[12];
@@ -801,10 +852,15 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_omega_h(int V, HF t, HF s, Red
     }
     if (grid_reduce_f<4>(acc, rs, rs.result)) lo_omega_update(rs.result, sc);
 }
+__global__ void __launch_bounds__(kRedBlock) k_lo_omega_h(int V, HF t, HF s, ReduceScratch rs, SolverScalars *sc)
+{
+    body_lo_omega_h(V, t, s, rs, sc);
+}
 
-__global__ void __launch_bounds__(kRedBlock) k_lo_xr_h(int V, float4 *xlo, HF phat, HF shat, HF s, HF t, HF r,
+__device__ __forceinline__ void body_lo_xr_h(int V, float4 *xlo, HF phat, HF shat, HF s, HF t, HF r,
                                                        HF rhat, ReduceScratch rs, SolverScalars *sc)
 {
+    if (sc->skip) return;   // a stopped right-hand side of a lockstep batch
     const cx<float> alpha = mkc((float)sc->alpha.x, (float)sc->alpha.y);
     const cx<float> omega = mkc((float)sc->omega.x, (float)sc->omega.y);
     float acc[3] = {0.f, 0.f, 0.f};
@@ -829,6 +885,11 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_xr_h(int V, float4 *xlo, HF ph
     }
     if (grid_reduce_f<3>(acc, rs, rs.result)) lo_xr_update(rs.result, sc);
 }
+__global__ void __launch_bounds__(kRedBlock) k_lo_xr_h(int V, float4 *xlo, HF phat, HF shat, HF s, HF t, HF r,
+                                                       HF rhat, ReduceScratch rs, SolverScalars *sc)
+{
+    body_lo_xr_h(V, xlo, phat, shat, s, t, r, rhat, rs, sc);
+}
 
 __global__ void __launch_bounds__(kRedBlock) k_lo_rho_h(int V, HF rhat, HF r, ReduceScratch rs, SolverScalars *sc)
 {
@@ -840,6 +901,44 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_rho_h(int V, HF rhat, HF r, Re
         cdot_acc(a, b, acc);
     }
     if (grid_reduce_f<2>(acc, rs, rs.result)) lo_rho_update(rs.result, sc);
+}
+
+// The step kernels for all members of a lockstep group: member blockIdx.y,
+// its part of the grid blockIdx.x (grid-stride loops and the block-partial
+// reductions use only the x extent).
+template <bool HALF, int STEP>
+__global__ void __launch_bounds__(kRedBlock) k_lo_group(int V, const LoMember *members)
+{
+    const LoMember &a = members[blockIdx.y];
+    const long long n = 6LL * V;
+    auto h = [](void *d, float *nrm) { return HF{d, nrm}; };
+    auto c4 = [](void *d) { return static_cast<const float4 *>(d); };
+    auto m4 = [](void *d) { return static_cast<float4 *>(d); };
+    switch (STEP) {
+    case LO_STEP_P:
+        if (HALF) body_lo_p_h(V, h(a.r, a.rn), h(a.v, a.vn), h(a.p, a.pn), a.sc);
+        else body_lo_p(n, c4(a.r), c4(a.v), m4(a.p), a.sc);
+        break;
+    case LO_STEP_ALPHA:
+        if (HALF) body_lo_alpha_h(V, h(a.rhat, a.rhatn), h(a.v, a.vn), a.rs, a.sc);
+        else body_lo_alpha(n, c4(a.rhat), c4(a.v), a.rs, a.sc);
+        break;
+    case LO_STEP_S:
+        if (HALF) body_lo_s_h(V, h(a.r, a.rn), h(a.v, a.vn), h(a.s, a.sn), a.sc);
+        else body_lo_s(n, c4(a.r), c4(a.v), m4(a.s), a.sc);
+        break;
+    case LO_STEP_OMEGA:
+        if (HALF) body_lo_omega_h(V, h(a.t, a.tn), h(a.s, a.sn), a.rs, a.sc);
+        else body_lo_omega(n, c4(a.t), c4(a.s), a.rs, a.sc);
+        break;
+    default:
+        if (HALF)
+            body_lo_xr_h(V, a.xlo, h(a.phat, a.phatn), h(a.shat, a.shatn), h(a.s, a.sn), h(a.t, a.tn),
+                         h(a.r, a.rn), h(a.rhat, a.rhatn), a.rs, a.sc);
+        else
+            body_lo_xr(n, a.xlo, c4(a.phat), c4(a.shat), c4(a.s), c4(a.t), m4(a.r), c4(a.rhat), a.rs, a.sc);
+        break;
+    }
 }
 
 // x (FP64) += xlo (FP32); xlo = 0.  FP32 plane j holds components 2j and
@@ -987,6 +1086,49 @@ cudaError_t lo_rho(wc_lattice lat, SolverState &S, wc_field rhat, wc_field r)
         k_lo_rho<<<WC_GRID(n)>>>(n, f4(rhat), f4(r), S.red, S.scal);
     return cudaGetLastError();
 }
+LoMember lo_member(SolverState &S, wc_field r, wc_field rhat, wc_field p, wc_field v, wc_field s, wc_field t,
+                   wc_field phat, wc_field shat, wc_field xlo)
+{
+    LoMember m{};
+    m.r = r->data, m.rhat = rhat->data, m.p = p->data, m.v = v->data;
+    m.s = s->data, m.t = t->data, m.phat = phat->data, m.shat = shat->data;
+    m.rn = r->nrm, m.rhatn = rhat->nrm, m.pn = p->nrm, m.vn = v->nrm;
+    m.sn = s->nrm, m.tn = t->nrm, m.phatn = phat->nrm, m.shatn = shat->nrm;
+    m.xlo = f4(xlo);
+    m.rs = S.red;
+    m.sc = S.scal;
+    return m;
+}
+
+cudaError_t lo_group(LoStep step, wc_lattice lat, int m, const LoMember *members, bool half, int max_blocks,
+                     cudaStream_t stream)
+{
+    if (m < 1 || m > 65535) return cudaErrorInvalidValue;
+    const int V = lat->g.V;
+    // about max_blocks blocks in all (each member reduces over its own
+    // gridDim.x partials, at most max_blocks of them)
+    const long long work = half ? (long long)V : 6LL * V;
+    long long gx = (work + kRedBlock - 1) / kRedBlock;
+    const long long share = std::max<long long>(1, (max_blocks + m - 1) / m);
+    const long long floor_blocks = std::max(1, max_blocks / 8);   // one per SM
+    gx = std::max<long long>(1, std::min<long long>(std::min<long long>(gx, max_blocks),
+                                                    std::max<long long>(share, floor_blocks)));
+    const dim3 grid((unsigned)gx, (unsigned)m);
+#define WC_GROUP_LAUNCH(S)                                                     \
+    if (half) k_lo_group<true, S><<<grid, kRedBlock, 0, stream>>>(V, members); \
+    else k_lo_group<false, S><<<grid, kRedBlock, 0, stream>>>(V, members)
+    switch (step) {
+    case LO_STEP_P: WC_GROUP_LAUNCH(LO_STEP_P); break;
+    case LO_STEP_ALPHA: WC_GROUP_LAUNCH(LO_STEP_ALPHA); break;
+    case LO_STEP_S: WC_GROUP_LAUNCH(LO_STEP_S); break;
+    case LO_STEP_OMEGA: WC_GROUP_LAUNCH(LO_STEP_OMEGA); break;
+    case LO_STEP_XR: WC_GROUP_LAUNCH(LO_STEP_XR); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef WC_GROUP_LAUNCH
+    return cudaGetLastError();
+}
+
 cudaError_t hp_add_lo(wc_lattice lat, SolverState &S, double2 *x, wc_field xlo_f)
 {
     float4 *xlo = f4(xlo_f);

@@ -185,7 +185,8 @@ struct SolverScalars {
     double pp, ss;   // |p|^2, |s|^2 (scales of the defect correction)
     double tt;
     int flags;       // bit 0: breakdown, bit 1: non-finite value
-    int pad;
+    int skip;        // lockstep batch: 1 = this right-hand side has stopped, and
+                     // the low-precision step kernels return at once (0 otherwise)
 };
 
 enum { FLAG_BREAKDOWN = 1, FLAG_NAN = 2 };

@@ -144,6 +144,13 @@ constexpr int kMrhsMax = 16;
 cudaError_t launch_apply_multi(wc_lattice lat, int n, const wc_field *outs, const wc_field *ins, int kind,
                                const int *active, cudaStream_t stream);
 
+// multi-right-hand-side Schur operator (wc_eomulti.cu): outs[r] = M^ ins[r]
+// (M^+ with dagger) for FP32 or FP16 half-lattice fields of the half lattice
+// `half`, tmps[r] its odd-site intermediates; skip (nullable) holds per field
+// a device flag (nullable) whose nonzero value skips it
+cudaError_t launch_schur_multi(wc_lattice half, int n, wc_field const *outs, wc_field const *ins,
+                               wc_field const *tmps, int dagger, const int *const *skip, cudaStream_t stream);
+
 // even-odd preconditioning (wc_evenodd.cu)
 // tmp: a half-lattice field of out's precision for the odd-site
 // intermediate (nullptr: the half lattice's own, shared by its callers)

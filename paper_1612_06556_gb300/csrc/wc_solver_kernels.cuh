@@ -46,4 +46,26 @@ cudaError_t lo_rho(wc_lattice lat, SolverState &S, wc_field rhat, wc_field r);
 // x (FP64) += xlo (FP32); xlo = 0
 cudaError_t hp_add_lo(wc_lattice lat, SolverState &S, double2 *x, wc_field xlo);
 
+// One member of a lockstep group: its vectors (values; per-site scales for
+// FP16 storage, else null), accumulated correction, reduction scratch and
+// scalars.
+struct LoMember {
+    void *r, *rhat, *p, *v, *s, *t, *phat, *shat;
+    float *rn, *rhatn, *pn, *vn, *sn, *tn, *phatn, *shatn;
+    float4 *xlo;
+    ReduceScratch rs;
+    SolverScalars *sc;
+};
+enum LoStep { LO_STEP_P, LO_STEP_ALPHA, LO_STEP_S, LO_STEP_OMEGA, LO_STEP_XR };
+// Fill a LoMember from a member's state and vectors (host side).
+LoMember lo_member(SolverState &S, wc_field r, wc_field rhat, wc_field p, wc_field v, wc_field s, wc_field t,
+                   wc_field phat, wc_field shat, wc_field xlo);
+// One step kernel (lo_p, lo_alpha, lo_s, lo_omega or lo_xr) for the m
+// members of a lockstep group in one launch, blockIdx.y = member; members:
+// device array of m entries, all on lat with one storage precision (half:
+// FP16).  Each member reduces into its own scratch and updates its own
+// scalars; a member whose skip word is set does nothing.
+cudaError_t lo_group(LoStep step, wc_lattice lat, int m, const LoMember *members, bool half, int max_blocks,
+                     cudaStream_t stream);
+
 }  // namespace wc

@@ -47,6 +47,38 @@ def test_schur_matches_oracle(dims, tbc, prec, dagger):
     assert_elementwise(out, eo.schur(psi, dagger), TOL[prec])
 
 
+@pytest.mark.parametrize("n", [1, 5, 12])
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_schur_multi_matches_oracle(n, prec, dagger):
+    """The multi-RHS Schur operator (one odd and one even pass for all n
+    fields, links, A and A^-1 shared) on a volume whose last CTA is ragged
+    (432 sites per parity, CTAs of 32), every field against the oracle and
+    against the single-field operator."""
+    dims, tbc = (6, 4, 6, 6), -1
+    U, lat, op, eo = _setup(dims, tbc, 720 + n)
+    srcs = [synth.gaussian_source(dims, 730 + r) for r in range(n)]
+    ins = [lat.field(prec).load(s) for s in srcs]
+    outs = [lat.field(prec) for _ in srcs]
+    lat.apply_schur_multi(outs, ins, dagger)
+    for s, o in zip(srcs, outs):
+        got = o.store(np.zeros_like(s))
+        assert np.abs(got[eo.odd]).max() == 0.0
+        assert_elementwise(got, eo.schur(s, dagger), TOL[prec])
+        assert_elementwise(got, _gpu_schur(lat, s, prec, dagger), 1e-6 if prec == 1 else 2e-3)
+
+
+def test_schur_multi_argument_errors():
+    w = wc()
+    dims = (4, 4, 4, 4)
+    U, lat, op, eo = _setup(dims, -1, 11)
+    a, b = lat.field(1), lat.field(1)
+    for outs, ins in [([a], [a]), ([a, a], [b, b]), ([lat.field(0)], [lat.field(0)]), ([a] * 17, [b] * 17)]:
+        with pytest.raises(w.WCError) as e:
+            lat.apply_schur_multi(outs, ins)
+        assert e.value.status == 1
+
+
 def test_schur_full_size_sampled():
     """24^3x32 (a half lattice of 221,184 sites per parity) in FP32: every
     odd site zero, sampled even sites against the oracle composition."""
@@ -165,6 +197,44 @@ def test_even_odd_batch(solver):
         w.solve_batch([lat], [lat.field(0)], [lat.field(0).load(synth.z2_source(dims, 3))], tol=1e-10,
                       even_odd=True)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("krylov", [1, 2])
+def test_lockstep_batch(krylov, monkeypatch):
+    """Reliable-update even-odd batch of 19 right-hand sides on one lattice:
+    the lockstep schedule (groups of up to 16 stepping together, both Schur
+    applications of a step in one multi-RHS launch) holds 16 + 3 of them; a
+    zero source starts inactive, sources of different structure stop after
+    different step counts.  Every solution is checked with the oracle's full
+    M, and the step counts against one branch per right-hand side."""
+    w = wc()
+    dims = (6, 6, 6, 8)
+    U = synth.exp_links(dims, 0.3, 1401)
+    lat = make_lattice(dims, U, 1.0, 0.124, -1)
+    srcs = [synth.point_source(dims, spin=k % 4, colour=k % 3, site=7 * k) for k in range(12)]
+    srcs += [synth.gaussian_source(dims, 40 + k) for k in range(5)]
+    srcs += [np.zeros_like(srcs[0]), synth.z2_source(dims, 7)]
+    bs = [lat.field(0).load(s) for s in srcs]
+
+    def run():
+        xs = [lat.field(0) for _ in srcs]
+        infos = w.solve_batch([lat] * len(srcs), xs, bs, tol=1e-10, solver=w.SOLVER_RELIABLE, even_odd=True,
+                              krylov_prec=krylov, max_iter=3000)
+        return infos, [x.store(np.zeros_like(s)) for x, s in zip(xs, srcs)]
+
+    infos, sols = run()
+    for info, sol, src in zip(infos, sols, srcs):
+        assert info.status == 0 and info.true_rel_resid <= 1e-10
+        r = src - oracle.apply_M(dims, -1, 0.124, 1.0, U, sol)
+        assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+    assert np.abs(sols[17]).max() == 0.0
+    steps = [i.iters for i in infos]
+    assert len(set(steps)) > 1   # the members stop at different steps
+    monkeypatch.setenv("WC_BATCH_LOCKSTEP", "0")
+    infos0, _ = run()
+    for a, b in zip(infos, infos0):
+        assert b.status == 0
+        assert abs(a.iters - b.iters) <= max(3, 0.1 * b.iters)
 
 
 @pytest.mark.parametrize("krylov", [1, 2])
