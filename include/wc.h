@@ -404,7 +404,16 @@ wc_status wc_solve_bicgstab(wc_lattice lat, wc_field x, wc_field b, const wc_sol
  * RELIABLE; NESTED is WC_ERR_ARG here).  With even_odd every right-hand side
  * is first reduced to its even-site Schur system (all extents even), the
  * Schur systems are solved in the graph, and each solution is completed on
- * the odd sites and checked on the full system.  With
+ * the odd sites and checked on the full system.  Reliable update without a
+ * preconditioner on even-odd systems runs the right-hand sides of one
+ * lattice in lockstep groups of up to 16 (each step's Schur applications are
+ * one multi-right-hand-side launch for the group; a stopped member skips its
+ * kernels); the environment variable WC_BATCH_LOCKSTEP=0 gives every
+ * right-hand side its own branch instead.  A zero initial guess skips the
+ * start's operator application.  Each lattice keeps the solver states and
+ * work fields of its largest batch (and, with even_odd, five FP64
+ * half-lattice fields per right-hand side) for the next batch, until
+ * wc_destroy_lattice; calls on one lattice must not overlap.  With
  * p->precond = WC_PRECOND_RAS and p->ras.block = {0,0,0,0} the RAS block
  * shape of each lattice is chosen by wc_ras_autotune.  Blocking; fills
  * infos[0..n-1] (seconds: wall time of the whole batch); returns the first

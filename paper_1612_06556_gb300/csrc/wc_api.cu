@@ -654,6 +654,7 @@ wc_status wc_destroy_lattice(wc_lattice lat)
 {
     if (!lat) return WC_OK;
     cudaStreamSynchronize(lat->stream);
+    free_batch_pool(lat);
     free_half(lat);
     state_free(lat->st);
     free_gauge(lat->gauge);

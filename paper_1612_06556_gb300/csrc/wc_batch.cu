@@ -77,6 +77,7 @@ struct BatchDev {
     double *rmax2;
     const cudaGraphConditionalHandle *h_iter;   // per RHS outside lockstep groups
     const cudaGraphConditionalHandle *h_ref;
+    int *fresh;                                 // per RHS: stopped right after a refresh
     const int *group;                           // per RHS: lockstep group, -1 if none
     const cudaGraphConditionalHandle *h_group;  // per group
     int ngroups;
@@ -102,6 +103,7 @@ __global__ void k_batch_check_iter(BatchDev d, int n, int reliable, cudaGraphCon
                 if (!(s.rr > it.tol2) || s.flags != 0 || k >= it.max_iter) a = 0;
             } else if (s.flags != 0) {
                 a = 0;   // breakdown / NaN: the host takes over
+                d.fresh[i] = 0;
                 if (d.group[i] >= 0) it.scal->skip = 1;
             } else {
                 if (s.rr > d.rmax2[i]) d.rmax2[i] = s.rr;
@@ -136,7 +138,10 @@ __global__ void k_batch_check_refresh(BatchDev d, int n, cudaGraphConditionalHan
         int a = d.active[i];
         if (a && d.refresh[i]) {
             const double rr = it.scal->rr;   // FP64 true residual of the refresh
-            if (!(rr > it.tol2) || d.iters[i] >= it.max_iter) a = 0;
+            if (!(rr > it.tol2) || d.iters[i] >= it.max_iter) {
+                a = 0;
+                d.fresh[i] = 1;   // x and the FP64 residual rr are current
+            }
             d.rmax2[i] = rr;
             d.active[i] = a;
         }
@@ -160,7 +165,8 @@ struct Resources {
     std::vector<LoVecs> LW;
     std::vector<cudaStream_t> streams;
     BatchItem *d_items = nullptr;
-    int *d_iters = nullptr, *d_active = nullptr, *d_refresh = nullptr, *d_group = nullptr;
+    int *d_iters = nullptr, *d_active = nullptr, *d_refresh = nullptr, *d_group = nullptr, *d_fresh = nullptr;
+    std::vector<std::pair<wc_lattice, int>> home;   // pool slot each state came from
     double *d_rmax2 = nullptr;
     cudaGraphConditionalHandle *d_hiter = nullptr, *d_href = nullptr, *d_hgroup = nullptr;
     std::vector<LoMember *> d_members;   // per lockstep group
@@ -182,8 +188,17 @@ struct Resources {
         cudaFree(d_href);
         cudaFree(d_group);
         cudaFree(d_hgroup);
+        cudaFree(d_fresh);
         for (auto m : d_members) cudaFree(m);
-        for (auto &s : S) state_free(s);
+        // states go back to their lattice's pool, with the work fields
+        // this batch added
+        for (size_t i = 0; i < S.size(); ++i) {
+            S[i].stream = nullptr;
+            if (i < home.size() && home[i].first)
+                home[i].first->batch_states[home[i].second] = S[i];
+            else
+                state_free(S[i]);
+        }
         for (auto s : streams)
             if (s) cudaStreamDestroy(s);
     }
@@ -459,41 +474,72 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
         if (st == WC_OK && P[i].precond == WC_PRECOND_RAS) st = check_ras_params(lats[i], &P[i].ras);
         if (st != WC_OK) return set_error(nullptr, st, std::string("wc_solve_batch: ") + lats[i]->err);
     }
+    // solver states from the lattices' pools (created on first use; their
+    // work fields persist from batch to batch)
+    R.home.assign(n, std::make_pair(wc_lattice(nullptr), 0));
+    {
+        std::map<wc_lattice, int> used;
+        for (int i = 0; i < n && st == WC_OK; ++i) {
+            const int k = used[lats[i]]++;
+            auto &pool = lats[i]->batch_states;
+            if (k == (int)pool.size()) {
+                SolverState fresh;
+                st = state_init(lats[i], fresh);
+                if (st != WC_OK) break;
+                pool.push_back(fresh);
+            }
+            R.S[i] = pool[k];
+            pool[k] = SolverState{};   // held by this batch until it returns
+            R.home[i] = std::make_pair(lats[i], k);
+        }
+    }
     for (int i = 0; i < n && st == WC_OK; ++i) {
-        st = state_init(lats[i], R.S[i]);
-        if (st == WC_OK)
-            st = check_cuda(lats[i], cudaStreamCreateWithFlags(&R.streams[i], cudaStreamNonBlocking), "stream");
+        st = check_cuda(lats[i], cudaStreamCreateWithFlags(&R.streams[i], cudaStreamNonBlocking), "stream");
         if (st == WC_OK) {
             R.S[i].stream = R.streams[i];
-            st = solver_vectors(lats[i], R.S[i], P[i], &R.W[i]);
+            st = check_cuda(lats[i], cudaMemsetAsync(R.S[i].scal, 0, sizeof(SolverScalars), R.streams[i]), "memset");
         }
+        if (st == WC_OK)
+            st = check_cuda(lats[i], cudaMemsetAsync(R.S[i].red.ticket, 0, sizeof(unsigned), R.streams[i]), "memset");
+        if (st == WC_OK) st = solver_vectors(lats[i], R.S[i], P[i], &R.W[i]);
         if (st == WC_OK && reliable) st = lo_vectors(lats[i], R.S[i], P[i], &R.LW[i]);
     }
     if (st != WC_OK) return st;
 
-    // |b|^2 and the start of every solve, one synchronisation for all
+    // |b|^2 and |x|^2 (a zero start needs no operator application), then
+    // the start of every solve, one synchronisation for each
     std::vector<double> bb(n), tol2(n);
+    std::vector<char> x_zero(n, 0);
     for (int i = 0; i < n && st == WC_OK; ++i) {
         SolverState &S = R.S[i];
-        st = check_cuda(lats[i], norm2_to_result(lats[i], S, static_cast<const double2 *>(bs[i]->data)), "norm2");
+        st = check_cuda(lats[i], norm2_to_result(lats[i], S, static_cast<const double2 *>(xs[i]->data)), "norm2");
+        if (st == WC_OK)
+            st = check_cuda(lats[i], cudaMemcpyAsync(S.red.host_result + 1, S.red.result, sizeof(double),
+                                                     cudaMemcpyDeviceToHost, S.stream), "copy");
+        if (st == WC_OK)
+            st = check_cuda(lats[i], norm2_to_result(lats[i], S, static_cast<const double2 *>(bs[i]->data)), "norm2");
         if (st == WC_OK)
             st = check_cuda(lats[i], cudaMemcpyAsync(S.red.host_result, S.red.result, sizeof(double),
                                                      cudaMemcpyDeviceToHost, S.stream), "copy");
-        if (st == WC_OK)
-            st = reliable ? enqueue_lo_start(lats[i], S, 0, xs[i], bs[i], R.W[i].r, R.LW[i])
-                          : enqueue_init(lats[i], S, 0, xs[i], bs[i], R.W[i]);
+    }
+    for (int i = 0; i < n && st == WC_OK; ++i) st = check_cuda(lats[i], cudaStreamSynchronize(R.streams[i]), "sync");
+    for (int i = 0; i < n && st == WC_OK; ++i) {
+        SolverState &S = R.S[i];
+        bb[i] = S.red.host_result[0];
+        x_zero[i] = S.red.host_result[1] == 0.0;
+        st = reliable ? enqueue_lo_start(lats[i], S, 0, xs[i], bs[i], R.W[i].r, R.LW[i], x_zero[i] != 0)
+                      : enqueue_init(lats[i], S, 0, xs[i], bs[i], R.W[i], x_zero[i] != 0);
         if (st == WC_OK)
             st = check_cuda(lats[i], cudaMemcpyAsync(S.scal_host, S.scal, sizeof(SolverScalars),
                                                      cudaMemcpyDeviceToHost, S.stream), "copy");
     }
     for (int i = 0; i < n && st == WC_OK; ++i) st = check_cuda(lats[i], cudaStreamSynchronize(R.streams[i]), "sync");
     if (st != WC_OK) return st;
-    std::vector<int> active(n, 0), iters(n, 0), zeros(n, 0);
+    std::vector<int> active(n, 0), iters(n, 0), zeros(n, 0), fresh(n, 0);
     std::vector<double> rmax2(n, 0.0);
     int any = 0;
     for (int i = 0; i < n; ++i) {
         infos[i] = wc_solve_info{};
-        bb[i] = R.S[i].red.host_result[0];
         tol2[i] = P[i].tol * P[i].tol * bb[i];
         const SolverScalars &h = *R.S[i].scal_host;
         rmax2[i] = h.rr;
@@ -556,6 +602,7 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
         if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_refresh, zeros), "copy");
         if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_rmax2, rmax2), "copy");
         if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_group, group), "copy");
+        if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_fresh, zeros), "copy");
         R.d_members.assign(ngroups, nullptr);
         for (int g = 0; g < ngroups && st == WC_OK; ++g) {
             std::vector<LoMember> tab;
@@ -611,7 +658,7 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
         if (st == WC_OK && reliable) st = check_cuda(nullptr, to_device(&R.d_href, h_ref), "copy");
         if (st == WC_OK && ngroups > 0) st = check_cuda(nullptr, to_device(&R.d_hgroup, h_grp), "copy");
         BatchDev dev{R.d_items, R.d_iters, R.d_active, R.d_refresh, R.d_rmax2, R.d_hiter, R.d_href,
-                     R.d_group, R.d_hgroup, ngroups};
+                     R.d_fresh, R.d_group, R.d_hgroup, ngroups};
         int reliable_i = reliable ? 1 : 0;
         void *args1[] = {&dev, &n, &reliable_i, &wh};
         void *args2[] = {&dev, &n, &wh};
@@ -643,6 +690,9 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
         if (st == WC_OK)
             st = check_cuda(nullptr, cudaMemcpy(iters.data(), R.d_iters, sizeof(int) * n, cudaMemcpyDeviceToHost),
                             "copy");
+        if (st == WC_OK)
+            st = check_cuda(nullptr, cudaMemcpy(fresh.data(), R.d_fresh, sizeof(int) * n, cudaMemcpyDeviceToHost),
+                            "copy");
         // the host-driven continuation below runs the same step kernels
         for (int i = 0; i < n && st == WC_OK; ++i)
             if (group[i] >= 0)
@@ -651,14 +701,20 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
     }
 
     // true residuals in FP64 for every RHS (the reliable solver folded its
-    // FP32 correction into x at its last refresh), then host-driven
-    // continuation of any RHS that missed tol
+    // FP32 correction into x at its last refresh, whose FP64 residual is
+    // still in the scalars when the RHS stopped right after it), then
+    // host-driven continuation of any RHS that missed tol
     for (int i = 0; i < n && st == WC_OK; ++i) {
         if (infos[i].status == WC_ERR_NAN) continue;
         SolverState &S = R.S[i];
         if (bb[i] == 0.0) {
             st = check_cuda(lats[i], cudaMemsetAsync(xs[i]->data, 0, spinor_bytes(WC_F64, lats[i]->g.V), S.stream),
                             "memset");
+            continue;
+        }
+        if (reliable && fresh[i]) {
+            st = check_cuda(lats[i], cudaMemcpyAsync(S.scal_host, S.scal, sizeof(SolverScalars),
+                                                     cudaMemcpyDeviceToHost, S.stream), "copy");
             continue;
         }
         if (reliable)
@@ -715,6 +771,7 @@ static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_
     std::vector<double> bb(n, 0.0), scale(n, 1.0);
     wc_status st = WC_OK;
     auto F = [&](int i, int k) -> wc_field & { return fe[5 * (size_t)i + k]; };
+    std::map<wc_lattice, int> used;   // right-hand sides so far per lattice
     for (int i = 0; i < n && st == WC_OK; ++i) {
         wc_lattice lat = lats[i];
         st = half_lattice(lat, &H[i]);
@@ -722,7 +779,15 @@ static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_
             st = set_error(nullptr, st, "wc_solve_batch: RHS " + std::to_string(i) + ": " + lat->err);
             break;
         }
-        for (int k = 0; k < 5 && st == WC_OK; ++k) st = wc_field_create(H[i], WC_F64, &F(i, k));
+        // the five half-lattice fields of this RHS, from the lattice's pool
+        const size_t base = 5 * (size_t)used[lat]++;
+        auto &pool = lat->batch_fields;
+        while (st == WC_OK && pool.size() < base + 5) {
+            wc_field f = nullptr;
+            st = wc_field_create(H[i], WC_F64, &f);
+            if (st == WC_OK) pool.push_back(f);
+        }
+        for (int k = 0; k < 5 && st == WC_OK; ++k) F(i, k) = pool[base + k];
         cudaStream_t s = lat->stream;
         wc_field t = H[i]->schur_tmp[WC_F64];
         if (st == WC_OK) st = check_cuda(lat, launch_split(lat, bs[i], F(i, 0), F(i, 1), s), "split");
@@ -769,7 +834,6 @@ static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_
         inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (inf.status != WC_OK && worst == WC_OK) worst = inf.status;
     }
-    for (auto &f : fe) wc_field_destroy(f);
     if (st != WC_OK) return st;
     return worst;
 }

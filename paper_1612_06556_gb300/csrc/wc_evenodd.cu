@@ -507,9 +507,20 @@ wc_status half_lattice(wc_lattice lat, wc_lattice *out)
     return WC_OK;
 }
 
+void free_batch_pool(wc_lattice lat)
+{
+    for (auto &s : lat->batch_states) state_free(s);
+    lat->batch_states.clear();
+    for (auto f : lat->batch_fields) wc_field_destroy(f);
+    lat->batch_fields.clear();
+}
+
 void free_half(wc_lattice lat)
 {
     if (!lat->half) return;
+    free_batch_pool(lat->half);
+    for (auto f : lat->batch_fields) wc_field_destroy(f);   // half-lattice fields
+    lat->batch_fields.clear();
     for (auto &f : lat->half->schur_tmp) wc_field_destroy(f);
     state_free(lat->half->st);
     delete lat->half;

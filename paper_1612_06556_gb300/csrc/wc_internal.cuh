@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/wc.h"
 #include "wc_device.cuh"
@@ -93,6 +94,12 @@ struct wc_lattice_s {
     int offset[4] = {0, 0, 0, 0};
     int split_mask = 0;
     wc_lattice_s *ext = nullptr;
+    // wc_solve_batch: the solver states of its right-hand sides on this
+    // lattice, and (full lattice of an even-odd batch) five FP64
+    // half-lattice fields per right-hand side, kept for the next batch (a
+    // batch with k right-hand sides here takes the first k)
+    std::vector<wc::SolverState> batch_states;
+    std::vector<wc_field_s *> batch_fields;
     std::string err;
 };
 
@@ -165,6 +172,8 @@ cudaError_t launch_merge(const wc_lattice_s *full, const wc_field_s *ev, const w
 wc_status build_clover_inverse(wc_lattice lat);
 wc_status half_lattice(wc_lattice lat, wc_lattice *out);
 void free_half(wc_lattice lat);
+// the solver states and fields a lattice keeps for wc_solve_batch
+void free_batch_pool(wc_lattice lat);
 int apply_shape_count();
 
 // solver states

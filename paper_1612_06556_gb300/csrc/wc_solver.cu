@@ -456,9 +456,11 @@ wc_status enqueue_refresh_full(wc_lattice lat, SolverState &S, int kind, wc_fiel
                                const LoVecs &w);
 
 wc_status enqueue_lo_start(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
-                           const LoVecs &w)
+                           const LoVecs &w, bool x_zero)
 {
-    wc_status st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S), "apply");
+    wc_status st = x_zero ? check_cuda(lat, cudaMemsetAsync(r_hp->data, 0, spinor_bytes(WC_F64, lat->g.V), S.stream),
+                                       "memset")
+                          : check_cuda(lat, launch_apply(lat, r_hp, x, kind, S), "apply");
     if (st == WC_OK)
         st = check_cuda(lat, residual(lat, S, static_cast<const double2 *>(b->data),
                                       static_cast<double2 *>(r_hp->data)), "residual");

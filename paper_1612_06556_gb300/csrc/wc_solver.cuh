@@ -50,10 +50,11 @@ wc_status enqueue_lo_iteration(wc_lattice lat, SolverState &S, const wc_solve_pa
 // r = fl32(r_hp); rho and beta recomputed
 wc_status enqueue_refresh_full(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
                                const LoVecs &w);
-// start of a reliable solve: r_hp = b - op x; r = fl32(r_hp); rhat = r,
-// p = v = xlo = 0, scalars reset (rr = |r|^2 of the FP32 copy)
+// start of a reliable solve: r_hp = b - op x (r_hp = b when the caller
+// knows x = 0); r = fl32(r_hp); rhat = r, p = v = xlo = 0, scalars reset
+// (rr = |r|^2 of the FP32 copy)
 wc_status enqueue_lo_start(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
-                           const LoVecs &w);
+                           const LoVecs &w, bool x_zero = false);
 
 cudaError_t ras_prepare();
 
