@@ -86,11 +86,21 @@ typedef enum { WC_ARITH_F64 = 0, WC_ARITH_DF32 = 1 } wc_fp64_arith;
  * restricted to the extended block with hops that leave it dropped, and
  * mr_iters minimal-residual steps from zero solve it; only the block's core
  * is written back.  Requires L[mu] % block[mu] == 0 and
- * L[mu] > block[mu] + 2*overlap. */
+ * L[mu] > block[mu] + 2*overlap.
+ * schur (even-odd solves only): 0 -- the preconditioner of the even-site
+ * system is the RAS above applied to the even vector extended by zeros to
+ * the full lattice and restricted back to the even sites; 1 -- RAS on block
+ * Schur complements: the MR steps solve the even-site Schur complement of
+ * the cut block operator, M^_B = A_ee - kappa^2 H^B_eo A_oo^-1 H^B_oe (H^B:
+ * hops with both ends in the extended block), on the block's even sites
+ * (parity of the global coordinates), and the core's even sites are written
+ * back (wc_ras_schur).  schur = 1 needs block[0] + 2*overlap even, at most
+ * 1536 sites per extended block, and an explicit block shape. */
 typedef struct {
     int block[4];
     int overlap;
     int mr_iters;
+    int schur;
 } wc_ras_params;
 
 /* How a preconditioned solve splits its precisions.
@@ -388,6 +398,14 @@ wc_status wc_apply_surface(wc_lattice lat, wc_field out, wc_field in, int dagger
 /* out = RAS(in) (see wc_ras_params).  FP32 arithmetic on FP32 or FP16
  * fields of the same precision.  Asynchronous. */
 wc_status wc_ras_precond(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params *p);
+
+/* out = the RAS on block Schur complements (see wc_ras_params, schur = 1;
+ * p->schur itself is ignored) of the even sites of in, M^ (dagger = 0) or
+ * M^+ (dagger = 1): FP32 arithmetic on FP32 or FP16 full-lattice fields of
+ * one precision; the odd sites of in are ignored and those of out set to
+ * zero.  All extents even.  Builds A^-1 on first use.  Asynchronous on the
+ * lattice stream (temporaries are freed after a synchronisation). */
+wc_status wc_ras_schur(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params *p, int dagger);
 
 /* Solve M x = b.  x (FP64) holds the initial guess on entry and the
  * solution on return; b is FP64.  Blocking; fills *info. */

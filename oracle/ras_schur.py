@@ -93,29 +93,32 @@ def block_schur_apply(dims, tbc: int, kappa: float, U, A, gsite, gc, lc, e, psi,
     return out
 
 
-def ras_schur(dims, tbc: int, kappa: float, U, T, block, delta: int, k: int, v, dagger: bool = False):
-    """z_e = sum_B Rtilde_B^T MR_k(M^_B, R_B v_e); zero on the odd sites."""
+def ras_schur(dims, tbc: int, kappa: float, U, T, block, delta: int, k: int, v, dagger: bool = False,
+              blocks=None):
+    """z_e = sum_B Rtilde_B^T MR_k(M^_B, R_B v_e); zero on the odd sites.
+    blocks: optional list of block coordinates (bx, by, bz, bt) to compute
+    (the cores of the others stay zero)."""
     U = np.asarray(U, dtype=np.complex128)
     A = np.eye(12, dtype=np.complex128)[None] + np.asarray(T, dtype=np.complex128)
     v = np.asarray(v, dtype=np.complex128)
     L = [int(d) for d in dims]
     nb = [L[m] // int(block[m]) for m in range(4)]
     z = np.zeros_like(v)
-    for bt in range(nb[3]):
-        for bz in range(nb[2]):
-            for by in range(nb[1]):
-                for bx in range(nb[0]):
-                    gsite, gc, lc, e = block_geometry(dims, block, delta, (bx, by, bz, bt))
-                    ev = gc.sum(axis=1) % 2 == 0
-                    r = np.where(ev[:, None, None], v[gsite], 0.0)
-                    x = np.zeros_like(r)
-                    for _ in range(k):
-                        q = block_schur_apply(dims, tbc, kappa, U, A, gsite, gc, lc, e, r, dagger)
-                        qq = np.vdot(q, q).real
-                        alpha = np.vdot(q, r) / qq if qq > 0 else 0.0
-                        x += alpha * r
-                        r -= alpha * q
-                    core = np.all((lc >= delta) & (lc < delta + np.array([int(c) for c in block])), axis=1)
-                    w = core & ev
-                    z[gsite[w]] = x[w]
+    if blocks is None:
+        blocks = [(bx, by, bz, bt) for bt in range(nb[3]) for bz in range(nb[2]) for by in range(nb[1])
+                  for bx in range(nb[0])]
+    for bc in blocks:
+        gsite, gc, lc, e = block_geometry(dims, block, delta, bc)
+        ev = gc.sum(axis=1) % 2 == 0
+        r = np.where(ev[:, None, None], v[gsite], 0.0)
+        x = np.zeros_like(r)
+        for _ in range(k):
+            q = block_schur_apply(dims, tbc, kappa, U, A, gsite, gc, lc, e, r, dagger)
+            qq = np.vdot(q, q).real
+            alpha = np.vdot(q, r) / qq if qq > 0 else 0.0
+            x += alpha * r
+            r -= alpha * q
+        core = np.all((lc >= delta) & (lc < delta + np.array([int(c) for c in block])), axis=1)
+        w = core & ev
+        z[gsite[w]] = x[w]
     return z

@@ -40,7 +40,7 @@ EXPORTED = [
     "wc_create_lattice", "wc_destroy_lattice", "wc_set_stream", "wc_load_gauge", "wc_load_clover",
     "wc_field_create", "wc_field_destroy", "wc_field_import", "wc_field_export", "wc_field_copy",
     "wc_apply_M", "wc_apply_Mdag", "wc_apply_hop", "wc_dot", "wc_norm2", "wc_axpy_norm",
-    "wc_ras_precond", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
+    "wc_ras_precond", "wc_ras_schur", "wc_solve_bicgstab", "wc_solve_batch", "wc_action_force", "wc_last_error",
     "wc_dot_noalloc", "wc_ras_autotune", "wc_apply_shape", "wc_apply_schur", "wc_apply_multi",
     "wc_force_times_links", "wc_set_fp64_arith", "wc_field_import_f32", "wc_field_export_f32",
     "wc_field_import_async", "wc_field_export_async", "wc_sync",
@@ -50,7 +50,8 @@ EXPORTED = [
 
 
 class RasParams(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_int * 4), ("overlap", ctypes.c_int), ("mr_iters", ctypes.c_int)]
+    _fields_ = [("block", ctypes.c_int * 4), ("overlap", ctypes.c_int), ("mr_iters", ctypes.c_int),
+                ("schur", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
@@ -95,6 +96,7 @@ _L.wc_dot.argtypes = [_vp, _vp, _vp, _dp]
 _L.wc_norm2.argtypes = [_vp, _vp, _dp]
 _L.wc_axpy_norm.argtypes = [_vp, _dp, _vp, _vp, _dp]
 _L.wc_ras_precond.argtypes = [_vp, _vp, _vp, ctypes.POINTER(RasParams)]
+_L.wc_ras_schur.argtypes = [_vp, _vp, _vp, ctypes.POINTER(RasParams), ctypes.c_int]
 _L.wc_solve_bicgstab.argtypes = [_vp, _vp, _vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]
 _L.wc_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                               ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]
@@ -168,15 +170,15 @@ def _ptr64(a):
     return a.ctypes.data
 
 
-def ras_params(block=(4, 4, 4, 4), overlap=1, mr_iters=4) -> RasParams:
-    return RasParams((ctypes.c_int * 4)(*block), int(overlap), int(mr_iters))
+def ras_params(block=(4, 4, 4, 4), overlap=1, mr_iters=4, schur=False) -> RasParams:
+    return RasParams((ctypes.c_int * 4)(*block), int(overlap), int(mr_iters), int(bool(schur)))
 
 
 def solve_params(tol=1e-10, max_iter=10000, max_restarts=5, precond=PRECOND_NONE, inner_prec=F32,
                  block=(4, 4, 4, 4), overlap=1, mr_iters=4, solver=SOLVER_FLEXIBLE, delta=0.01, inner_tol=0.01,
-                 inner_iters=100, krylov_prec=F32, even_odd=False) -> SolveParams:
+                 inner_iters=100, krylov_prec=F32, even_odd=False, ras_schur=False) -> SolveParams:
     return SolveParams(float(tol), int(max_iter), int(max_restarts), int(precond), int(inner_prec),
-                       ras_params(block, overlap, mr_iters), int(solver), float(delta), float(inner_tol),
+                       ras_params(block, overlap, mr_iters, ras_schur), int(solver), float(delta), float(inner_tol),
                        int(inner_iters), int(krylov_prec), int(bool(even_odd)))
 
 
@@ -349,6 +351,13 @@ class Lattice:
     def ras(self, out: Field, inp: Field, block=(4, 4, 4, 4), overlap=1, mr_iters=4):
         p = ras_params(block, overlap, mr_iters)
         _check(_L.wc_ras_precond(self.handle, out.handle, inp.handle, ctypes.byref(p)), self.handle)
+
+    def ras_schur(self, out: Field, inp: Field, block=(4, 4, 4, 4), overlap=1, mr_iters=4, dagger=False):
+        """RAS on block Schur complements of the even sites of inp (odd sites
+        of out zero)."""
+        p = ras_params(block, overlap, mr_iters, True)
+        _check(_L.wc_ras_schur(self.handle, out.handle, inp.handle, ctypes.byref(p), int(bool(dagger))),
+               self.handle)
 
     def solve(self, x: Field, b: Field, params: SolveParams | None = None, check=True, **kw) -> SolveInfo:
         p = params if params is not None else solve_params(**kw)

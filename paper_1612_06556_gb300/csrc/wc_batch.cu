@@ -412,6 +412,8 @@ wc_status resolve_ras(wc_lattice lat, wc_field b, const wc_solve_params &p, wc_r
         *out = p.ras;
         return WC_OK;
     }
+    if (p.ras.schur)
+        return set_error(lat, WC_ERR_ARG, "give the block shape of the block-Schur RAS explicitly");
     return autotune_ras(lat, b, p, out);
 }
 

@@ -128,6 +128,11 @@ cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind /*0
 cudaError_t launch_apply(wc_lattice lat, wc_field out, wc_field in, int kind, SolverState &S);
 cudaError_t launch_copy(wc_lattice lat, wc_field dst, wc_field src, double scale, const double *dev_scale,
                         int invert_scale, cudaStream_t stream);
+// RAS on block Schur complements, on half-lattice (even-site) fields of the
+// half lattice of full (A^-1 built)
+bool ras_schur_fits(const wc_ras_params &p);
+cudaError_t launch_ras_schur(const wc_lattice_s *full, wc_field out, wc_field in, const wc_ras_params &p, int dagger,
+                             cudaStream_t stream);
 cudaError_t launch_ras(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params &p, int dagger,
                        cudaStream_t stream);
 

@@ -701,6 +701,216 @@ __global__ void __cluster_dims__(kRasNC, 1, 1) __launch_bounds__(kRasCThreads, 1
     }
 }
 
+// ------------------------------------------------------------------------
+// RAS on block Schur complements (even-odd solves): MR on
+// M^_B = A_ee - kappa^2 H^B_eo A_oo^-1 H^B_oe, the even-site Schur
+// complement of the Dirichlet-cut block operator M_B
+// ------------------------------------------------------------------------
+
+constexpr int kRasEoMaxThreads = 768;
+
+// One CTA per extended block; thread j owns the j-th even and the j-th odd
+// site of the block.  The local x extent e[0] is even, so along every local
+// x row the two parities alternate and local site l of either parity has
+// compact index l >> 1 in its parity's arrays: thread j = (row, k) owns the
+// sites 2k + p_row (even) and 2k + 1 - p_row (odd) of its row, p_row the
+// global parity of the row's first site.  Shared memory: r (even), t
+// (odd intermediate) and x (even), float4 planes [6][nh].  One MR step:
+// odd pass t = A_oo^-1 H^B r, barrier, even pass q = A_ee r - kappa^2 H^B t
+// and the partial sums, alpha (barrier inside), x += alpha r,
+// r -= alpha q, barrier.  Links, A and A^-1 are read from global memory.
+
+// acc += coef * (the hops of direction MU into local site l whose source,
+// of the opposite parity, lies inside the extended block); src: compact
+// planes of that parity
+template <class P, int MU, int SF>
+__device__ __forceinline__ void ras_eo_hops(const Geom &g, const RasGeom &rg, const GaugeStore &U,
+                                            const float4 *src, int nh, int l, int site, unsigned lpack,
+                                            unsigned wbits, float coef, cx<float> acc[12])
+{
+    const int lm = (lpack >> (8 * MU)) & 255u;
+    const int stl = rg.es[MU];
+    if (lm + 1 < rg.e[MU]) {
+        const float c = (MU == 3 && (wbits & (16u << 3))) ? coef * (float)g.tbc : coef;
+        cx<float> h[6], u[6], r2[3], w[6];
+        project_sm<MU, SF>(src, nh, wc_idx((l + stl) >> 1, nh), h);
+        P::load_link(U, g.V, MU, site, u, r2);
+        su3_mul(u, r2, h, c, w);
+        reconstruct_add<MU, SF>(acc, w);
+    }
+    if (lm >= 1) {
+        const int sb = wc_idx((wbits & (1u << MU)) ? site + (g.L[MU] - 1) * g.stride[MU] : site - g.stride[MU], g.V);
+        const float c = (MU == 3 && (wbits & (1u << 3))) ? coef * (float)g.tbc : coef;
+        cx<float> h[6], u[6], r2[3], w[6];
+        project_sm<MU, -SF>(src, nh, wc_idx((l - stl) >> 1, nh), h);
+        P::load_link(U, g.V, MU, sb, u, r2);
+        su3_adj_mul(u, r2, h, c, w);
+        reconstruct_add<MU, -SF>(acc, w);
+    }
+}
+
+template <class P, int SF>
+__device__ __forceinline__ void ras_eo_all_hops(const Geom &g, const RasGeom &rg, const GaugeStore &U,
+                                                const float4 *src, int nh, int l, int site, unsigned lpack,
+                                                unsigned wbits, cx<float> acc[12])
+{
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+        switch (mu) {
+        case 0: ras_eo_hops<P, 0, SF>(g, rg, U, src, nh, l, site, lpack, wbits, 1.f, acc); break;
+        case 1: ras_eo_hops<P, 1, SF>(g, rg, U, src, nh, l, site, lpack, wbits, 1.f, acc); break;
+        case 2: ras_eo_hops<P, 2, SF>(g, rg, U, src, nh, l, site, lpack, wbits, 1.f, acc); break;
+        default: ras_eo_hops<P, 3, SF>(g, rg, U, src, nh, l, site, lpack, wbits, 1.f, acc); break;
+        }
+    }
+}
+
+// local site l = row * e0 + lx of block bc: global site, packed local
+// coordinates, boundary bits (bit mu: global coordinate 0, bit 4+mu: L-1),
+// core flag
+__device__ __forceinline__ int ras_eo_site(const Geom &g, const RasGeom &rg, const int bc[4], int l,
+                                           unsigned &lpack, unsigned &wbits, bool &in_core)
+{
+    int t = l, site = 0;
+    lpack = 0u;
+    wbits = 0u;
+    in_core = true;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int lm = t % rg.e[m];
+        t /= rg.e[m];
+        lpack |= (unsigned)lm << (8 * m);
+        int gm = bc[m] * rg.b[m] - rg.delta + lm;
+        gm = gm < 0 ? gm + g.L[m] : (gm >= g.L[m] ? gm - g.L[m] : gm);
+        site += gm * g.stride[m];
+        if (gm == 0) wbits |= 1u << m;
+        if (gm == g.L[m] - 1) wbits |= 16u << m;
+        if (lm < rg.delta || lm >= rg.delta + rg.b[m]) in_core = false;
+    }
+    return wc_idx(site, g.V);
+}
+
+// vin, zout: half-lattice (even-site) fields, index full_site >> 1; A: the
+// parity-ordered A (position x >> 1 for even x), Ai: A^-1 (position
+// V/2 + (x >> 1) for odd x)
+template <class P, int SF>
+__global__ void __launch_bounds__(kRasEoMaxThreads, 1)
+    k_ras_schur(Geom g, RasGeom rg, GaugeStore U, CloverStore A, CloverStore Ai, const void *vin,
+                const float *vin_nrm, void *zout, float *zout_nrm, float kappa)
+{
+    extern __shared__ float4 smem_raw[];
+    const int nh = rg.ne >> 1;
+    float4 *r = smem_raw;          // [6][nh] even
+    float4 *t = r + 6 * nh;        // [6][nh] odd
+    float4 *x = t + 6 * nh;        // [6][nh] even
+    __shared__ float red[32 * 3];
+    if (kChecked) {   // every slot read before it is written shows up as NaN
+        const float nan = __int_as_float(0x7fc00000);
+        for (int q = threadIdx.x; q < 18 * nh; q += blockDim.x) r[q] = make_float4(nan, nan, nan, nan);
+        __syncthreads();
+    }
+    int bc[4];
+    {
+        int ib = blockIdx.x;
+        bc[0] = ib % rg.nb[0];
+        ib /= rg.nb[0];
+        bc[1] = ib % rg.nb[1];
+        ib /= rg.nb[1];
+        bc[2] = ib % rg.nb[2];
+        bc[3] = ib / rg.nb[2];
+    }
+    const int V = g.V, Vh = V >> 1;
+    const int j = threadIdx.x;
+    const bool own = j < nh;
+    int le = 0, lo = 0, ge = 0, go = 0;
+    unsigned lpe = 0u, wbe = 0u, lpo = 0u, wbo = 0u;
+    bool core = false;
+    if (own) {
+        const int h0 = rg.e[0] >> 1, row = j / h0, k = j - row * h0;
+        const int ly = row % rg.e[1], lz = (row / rg.e[1]) % rg.e[2], lt = row / (rg.e[1] * rg.e[2]);
+        int par = ly + lz + lt;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) par += bc[m] * rg.b[m] - rg.delta;
+        const int prow = par & 1;
+        le = row * rg.e[0] + 2 * k + prow;
+        lo = row * rg.e[0] + 2 * k + 1 - prow;
+        bool dummy;
+        ge = ras_eo_site(g, rg, bc, le, lpe, wbe, core);
+        go = ras_eo_site(g, rg, bc, lo, lpo, wbo, dummy);
+        cx<float> sp[12];
+        P::load_spinor(vin, vin_nrm, Vh, ge >> 1, sp);
+        sm_store(r, nh, j, sp);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) x[c * nh + j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const float beta = -kappa * kappa;
+    for (int it = 0; it < rg.k; ++it) {
+        // odd pass: t = A_oo^-1 H^B r
+        if (own) {
+            cx<float> h[12], o[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) h[c] = mkc(0.f, 0.f);
+            ras_eo_all_hops<P, SF>(g, rg, U, r, nh, lo, go, lpo, wbo, h);
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                float cl[36];
+                P::load_clover(Ai, V, wc_idx(Vh + (go >> 1), V), b, cl);
+                clover_block_mul(cl, h + 6 * b, o + 6 * b);
+            }
+            sm_store(t, nh, j, o);
+        }
+        __syncthreads();
+        // even pass: q = A_ee r - kappa^2 H^B t
+        cx<float> q[12];
+        float acc[3] = {0.f, 0.f, 0.f};
+        if (own) {
+            cx<float> h[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) h[c] = mkc(0.f, 0.f);
+            ras_eo_all_hops<P, SF>(g, rg, U, t, nh, le, ge, lpe, wbe, h);
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                cx<float> rl[6];
+                sm_load_block(r, nh, j, b, rl);
+                float cl[36];
+                P::load_clover(A, V, wc_idx(ge >> 1, V), b, cl);
+                clover_block_mul(cl, rl, q + 6 * b);
+            }
+            cx<float> rl[12];
+            sm_load(r, nh, j, rl);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                q[c] = q[c] + beta * h[c];
+                acc[0] = fmaf(q[c].re, rl[c].re, fmaf(q[c].im, rl[c].im, acc[0]));    // Re <q, r>
+                acc[1] = fmaf(q[c].re, rl[c].im, fmaf(-q[c].im, rl[c].re, acc[1]));   // Im <q, r>
+                acc[2] = fmaf(q[c].re, q[c].re, fmaf(q[c].im, q[c].im, acc[2]));
+            }
+        }
+        // contains __syncthreads: every read of r and t is done after it
+        const cx<float> alpha = block_alpha(acc, red);
+        if (own) {
+            cx<float> rk[12], xk[12];
+            sm_load(r, nh, j, rk);
+            sm_load(x, nh, j, xk);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                xk[c] = cfma(alpha, rk[c], xk[c]);
+                rk[c] = rk[c] - alpha * q[c];
+            }
+            sm_store(x, nh, j, xk);
+            sm_store(r, nh, j, rk);
+        }
+        __syncthreads();
+    }
+    // restricted prolongation: the even sites of the core
+    if (own && core) {
+        cx<float> sp[12];
+        sm_load(x, nh, j, sp);
+        P::store_spinor(zout, zout_nrm, Vh, ge >> 1, sp);
+    }
+}
+
 }  // namespace
 
 int ras_threads(const wc_ras_params &p);
@@ -819,6 +1029,67 @@ cudaError_t launch_ras_c(wc_lattice lat, const RasGeom &rg, int nblocks, const R
     return cudaGetLastError();
 }
 
+// Block-Schur RAS: one CTA per block, e[0] even, at most 2 x 768 sites
+int ras_schur_threads(const wc_ras_params &p)
+{
+    int ne = 1;
+    for (int m = 0; m < 4; ++m) ne *= p.block[m] + 2 * p.overlap;
+    return (ne / 2 + 31) / 32 * 32;
+}
+
+bool ras_schur_fits(const wc_ras_params &p)
+{
+    if ((p.block[0] + 2 * p.overlap) % 2 != 0) return false;
+    int ne = 1;
+    for (int m = 0; m < 4; ++m) ne *= p.block[m] + 2 * p.overlap;
+    return ras_schur_threads(p) <= kRasEoMaxThreads && (size_t)(ne / 2) * 18 * sizeof(float4) <= 226 * 1024;
+}
+
+template <class P, int SF>
+cudaError_t ras_schur_optin()
+{
+    static unsigned long long done = 0;
+    return smem_optin(k_ras_schur<P, SF>, done, 226 * 1024);
+}
+
+cudaError_t launch_ras_schur(const wc_lattice_s *full, wc_field out, wc_field in, const wc_ras_params &p, int dagger,
+                             cudaStream_t stream)
+{
+    if (!ras_schur_fits(p) || !full->cinv_loaded) return cudaErrorInvalidValue;
+    RasGeom rg;
+    rg.ne = 1;
+    rg.ncore = 1;
+    int nblocks = 1;
+    for (int m = 0; m < 4; ++m) {
+        rg.b[m] = p.block[m];
+        rg.e[m] = p.block[m] + 2 * p.overlap;
+        rg.nb[m] = full->g.L[m] / p.block[m];
+        rg.es[m] = m == 0 ? 1 : rg.es[m - 1] * rg.e[m - 1];
+        rg.ne *= rg.e[m];
+        rg.ncore *= rg.b[m];
+        nblocks *= rg.nb[m];
+    }
+    rg.delta = p.overlap;
+    rg.k = p.mr_iters;
+    const size_t smem = (size_t)(rg.ne / 2) * 18 * sizeof(float4);
+    const int threads = ras_schur_threads(p);
+    const float kappa = (float)full->kappa;
+    cudaError_t e = cudaSuccess;
+#define WC_RAS_SCHUR(PP, SS)                                                                                   \
+    e = ras_schur_optin<PP, SS>();                                                                             \
+    if (e == cudaSuccess)                                                                                      \
+        k_ras_schur<PP, SS><<<nblocks, threads, smem, stream>>>(full->g, rg, full->gauge, full->ceo, full->cinv, \
+                                                                in->data, in->nrm, out->data, out->nrm, kappa)
+    if (in->prec == WC_F16) {
+        if (dagger) { WC_RAS_SCHUR(P16, +1); } else { WC_RAS_SCHUR(P16, -1); }
+    } else {
+        if (dagger) { WC_RAS_SCHUR(P32, +1); } else { WC_RAS_SCHUR(P32, -1); }
+    }
+#undef WC_RAS_SCHUR
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 cudaError_t ras_prepare()
 {
     cudaError_t e = ras_smem_optin<P32, -1>();
@@ -827,6 +1098,10 @@ cudaError_t ras_prepare()
     if (e == cudaSuccess) e = ras_smem_optin<P16, +1>();
     if (e == cudaSuccess) e = ras_cluster_optin<P32, -1>();
     if (e == cudaSuccess) e = ras_cluster_optin<P32, +1>();
+    if (e == cudaSuccess) e = ras_schur_optin<P32, -1>();
+    if (e == cudaSuccess) e = ras_schur_optin<P32, +1>();
+    if (e == cudaSuccess) e = ras_schur_optin<P16, -1>();
+    if (e == cudaSuccess) e = ras_schur_optin<P16, +1>();
     return e;
 }
 

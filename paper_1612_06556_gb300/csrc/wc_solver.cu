@@ -52,6 +52,10 @@ wc_status check_ras_params(wc_lattice lat, const wc_ras_params *p)
     }
     if (!ras_fits(*p))
         return set_error(lat, WC_ERR_ARG, "RAS extended block too large for one CTA (shared memory / threads)");
+    if (p->schur != 0 && p->schur != 1) return set_error(lat, WC_ERR_ARG, "RAS schur must be 0 or 1");
+    if (p->schur && !ras_schur_fits(*p))
+        return set_error(lat, WC_ERR_ARG,
+                         "block-Schur RAS needs block[0] + 2 overlap even and at most 1536 extended sites");
     return WC_OK;
 }
 
@@ -121,6 +125,7 @@ static wc_status ras_apply(wc_lattice lat, SolverState &S, wc_field out, wc_fiel
 {
     if (!lat->schur_parent) return check_cuda(lat, launch_ras(lat, out, in, ras, kind, S.stream), "ras");
     wc_lattice full = lat->schur_parent;
+    if (ras.schur) return check_cuda(lat, launch_ras_schur(full, out, in, ras, kind, S.stream), "ras_schur");
     const int base = kRasEoSlot + 2 * (in->prec == WC_F16);
     wc_field a = S.work[base], b = S.work[base + 1];
     if (!a || !b) return set_error(lat, WC_ERR_STATE, "even-odd RAS fields missing");
@@ -745,6 +750,34 @@ wc_status wc_ras_precond(wc_lattice lat, wc_field out, wc_field in, const wc_ras
     st = require_operator(lat);
     if (st != WC_OK) return st;
     return check_cuda(lat, launch_ras(lat, out, in, *p, 0, lat->stream), "ras");
+}
+
+wc_status wc_ras_schur(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params *p, int dagger)
+{
+    if (!lat || !out || !in || !p) return set_error(lat, WC_ERR_ARG, "NULL argument");
+    if (out->lat != lat || in->lat != lat) return set_error(lat, WC_ERR_ARG, "fields belong to another lattice");
+    if (out == in) return set_error(lat, WC_ERR_ARG, "out and in must be distinct");
+    if (out->prec != in->prec || in->prec == WC_F64)
+        return set_error(lat, WC_ERR_ARG, "RAS works on FP32 or FP16 fields of one precision");
+    wc_ras_params q = *p;
+    q.schur = 1;
+    wc_status st = check_ras_params(lat, &q);
+    if (st != WC_OK) return st;
+    st = require_operator(lat);
+    if (st != WC_OK) return st;
+    wc_lattice h = nullptr;
+    st = half_lattice(lat, &h);
+    if (st != WC_OK) return st;
+    wc_field e = nullptr, z = nullptr;
+    st = wc_field_create(h, in->prec, &e);
+    if (st == WC_OK) st = wc_field_create(h, in->prec, &z);
+    if (st == WC_OK) st = check_cuda(lat, launch_split(lat, in, e, nullptr, lat->stream), "split");
+    if (st == WC_OK) st = check_cuda(lat, launch_ras_schur(lat, z, e, q, dagger ? 1 : 0, lat->stream), "ras_schur");
+    if (st == WC_OK) st = check_cuda(lat, launch_merge(lat, z, nullptr, out, lat->stream), "merge");
+    if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync");
+    wc_field_destroy(e);
+    wc_field_destroy(z);
+    return st;
 }
 
 wc_status wc_solve_bicgstab(wc_lattice lat, wc_field x, wc_field b, const wc_solve_params *p, wc_solve_info *info)

@@ -70,6 +70,8 @@ def test_null_handles_are_argument_errors_without_a_gpu(lib):
     assert L.wc_field_export_f32(None, buf) == 1
     assert L.wc_field_import_async(None, buf, 0) == 1
     assert L.wc_field_export_async(None, buf, 1) == 1
+    rp = wc.ras_params((4, 4, 4, 4), 1, 4, True)
+    assert L.wc_ras_schur(None, None, None, ctypes.byref(rp), 0) == 1
     assert L.wc_last_error(None)
 
 
