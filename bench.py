@@ -429,8 +429,9 @@ def batch_comparison(wc, args):
     gauge field) to 1e-10 with FP32 RAS (block shapes from the autotuner):
     one graph-launched batch (reliable-update solver; also the flexible FP64
     outer solver, and the even-odd reliable-update solver without RAS, whose
-    12 sources per lattice step in lockstep groups, timed also with one
-    branch per right-hand side) vs 36 sequential solves on the same GPU."""
+    12 sources per lattice step in lockstep groups with FP32 Krylov vectors
+    and in one branch each with FP16 vectors, each timed also with the other
+    schedule) vs 36 sequential solves on the same GPU."""
     import synth
     cfg = synth.CONFIGS[4]
     lats, bs, srcs = [], [], []
@@ -477,9 +478,11 @@ def batch_comparison(wc, args):
                              delta=0.01, krylov_prec=wc.F16, even_odd=True)
     run_batch(eo_h16)
     infos_eo_h16, t_eo_h16 = run_batch(eo_h16)
-    os.environ["WC_BATCH_LOCKSTEP"] = "0"
+    # FP16 vectors take one branch per right-hand side by default; the
+    # lockstep schedule for comparison
+    os.environ["WC_BATCH_LOCKSTEP"] = "1"
     try:
-        infos_eo_h16_br, t_eo_h16_br = run_batch(eo_h16)
+        infos_eo_h16_ls, t_eo_h16_ls = run_batch(eo_h16)
     finally:
         del os.environ["WC_BATCH_LOCKSTEP"]
     # the same with the FP64 operator steps in double-FP32 arithmetic
@@ -521,8 +524,8 @@ def batch_comparison(wc, args):
             "even_odd_batch_seconds": t_eo, "even_odd_all_ok": all(i.status == 0 for i in infos_eo),
             "even_odd_branch_per_rhs_batch_seconds": t_eo_br,
             "even_odd_branch_per_rhs_all_ok": all(i.status == 0 for i in infos_eo_br),
-            "even_odd_fp16_vectors_branch_per_rhs_batch_seconds": t_eo_h16_br,
-            "even_odd_fp16_vectors_branch_per_rhs_all_ok": all(i.status == 0 for i in infos_eo_h16_br),
+            "even_odd_fp16_vectors_lockstep_batch_seconds": t_eo_h16_ls,
+            "even_odd_fp16_vectors_lockstep_all_ok": all(i.status == 0 for i in infos_eo_h16_ls),
             "even_odd_sequential_seconds": t_seq_eo, "even_odd_sequential_all_ok": all(i.status == 0 for i in seq_eo),
             "even_odd_fp16_vectors_batch_seconds": t_eo_h16,
             "even_odd_fp16_vectors_all_ok": all(i.status == 0 for i in infos_eo_h16),
@@ -615,6 +618,18 @@ def ras_timing(wc, lat, dims, src, stream, reps=50):
         ms = e0.elapsed_time(e1) / reps
         tf = flops / (ms * 1e-3) / 1e12
         out[name] = {"ms": ms, "effective_tflops": tf, "frac_of_fp32_fma_peak": tf / peak}
+        # the same blocks on the even-odd system: MR on each block's
+        # even-site Schur complement (648 even sites per extended block; the
+        # time includes the split of the input and the merge of the output)
+        for _ in range(3):
+            lat.ras_schur(z, a)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            lat.ras_schur(z, a)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["schur_" + name] = {"ms": e0.elapsed_time(e1) / reps}
         a.close()
         z.close()
     return out
@@ -853,6 +868,12 @@ def solve_comparison(wc, lat, src, args):
                                             inner_iters=100, even_odd=True)),
                      ("eo_reliable_ras_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
                                                   solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True)),
+                     ("eo_reliable_ras_schur_f16", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
+                                                        solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True,
+                                                        ras_schur=True)),
+                     ("eo_reliable_ras_schur_f32", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F32,
+                                                        solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True,
+                                                        ras_schur=True)),
                      ("eo_reliable_h16", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_RELIABLE, delta=0.01,
                                               krylov_prec=wc.F16, even_odd=True)),
                      ("eo_nested_h16", dict(precond=wc.PRECOND_NONE, solver=wc.SOLVER_NESTED, inner_tol=0.01,
@@ -893,7 +914,8 @@ def solve_comparison(wc, lat, src, args):
         best = min(ok, key=lambda k: out[k]["seconds"])
         out["fastest_mixed"] = best
         out["speedup_fastest_mixed_vs_fp64"] = out["fp64_plain"]["seconds"] / out[best]["seconds"]
-    out["ras"] = "4^4 blocks, overlap 1, 4 MR iterations"
+    out["ras"] = ("4^4 blocks, overlap 1, 4 MR iterations; _ras_schur_: RAS on block Schur complements "
+                  "(wc_ras_params.schur)")
     out["df32"] = "suffix _df32: FP64 operator steps in double-FP32 arithmetic (wc_set_fp64_arith)"
     return out
 

@@ -404,7 +404,8 @@ wc_status wc_ras_precond(wc_lattice lat, wc_field out, wc_field in, const wc_ras
  * M^+ (dagger = 1): FP32 arithmetic on FP32 or FP16 full-lattice fields of
  * one precision; the odd sites of in are ignored and those of out set to
  * zero.  All extents even.  Builds A^-1 on first use.  Asynchronous on the
- * lattice stream (temporaries are freed after a synchronisation). */
+ * lattice stream (two half-lattice temporaries per precision are kept by
+ * the lattice). */
 wc_status wc_ras_schur(wc_lattice lat, wc_field out, wc_field in, const wc_ras_params *p, int dagger);
 
 /* Solve M x = b.  x (FP64) holds the initial guess on entry and the
@@ -422,12 +423,13 @@ wc_status wc_solve_bicgstab(wc_lattice lat, wc_field x, wc_field b, const wc_sol
  * RELIABLE; NESTED is WC_ERR_ARG here).  With even_odd every right-hand side
  * is first reduced to its even-site Schur system (all extents even), the
  * Schur systems are solved in the graph, and each solution is completed on
- * the odd sites and checked on the full system.  Reliable update without a
- * preconditioner on even-odd systems runs the right-hand sides of one
- * lattice in lockstep groups of up to 16 (each step's Schur applications are
- * one multi-right-hand-side launch for the group; a stopped member skips its
- * kernels); the environment variable WC_BATCH_LOCKSTEP=0 gives every
- * right-hand side its own branch instead.  A zero initial guess skips the
+ * the odd sites and checked on the full system.  Reliable update with FP32
+ * Krylov vectors and without a preconditioner on even-odd systems runs the
+ * right-hand sides of one lattice in lockstep groups of up to 16 (each
+ * step's Schur applications are one multi-right-hand-side launch for the
+ * group; a stopped member skips its kernels); the environment variable
+ * WC_BATCH_LOCKSTEP=0 gives every right-hand side its own branch instead,
+ * WC_BATCH_LOCKSTEP=1 groups FP16 Krylov vectors too.  A zero initial guess skips the
  * start's operator application.  Each lattice keeps the solver states and
  * work fields of its largest batch (and, with even_odd, five FP64
  * half-lattice fields per right-hand side) for the next batch, until

@@ -521,6 +521,11 @@ void free_half(wc_lattice lat)
     free_batch_pool(lat->half);
     for (auto f : lat->batch_fields) wc_field_destroy(f);   // half-lattice fields
     lat->batch_fields.clear();
+    for (auto &pr : lat->ras_half)
+        for (auto &f : pr) {
+            wc_field_destroy(f);
+            f = nullptr;
+        }
     for (auto &f : lat->half->schur_tmp) wc_field_destroy(f);
     state_free(lat->half->st);
     delete lat->half;

@@ -100,6 +100,9 @@ struct wc_lattice_s {
     // batch with k right-hand sides here takes the first k)
     std::vector<wc::SolverState> batch_states;
     std::vector<wc_field_s *> batch_fields;
+    // wc_ras_schur: the even-site input and output on the half lattice, per
+    // precision (created on first use)
+    wc_field_s *ras_half[3][2] = {};
     std::string err;
 };
 

@@ -768,15 +768,13 @@ wc_status wc_ras_schur(wc_lattice lat, wc_field out, wc_field in, const wc_ras_p
     wc_lattice h = nullptr;
     st = half_lattice(lat, &h);
     if (st != WC_OK) return st;
-    wc_field e = nullptr, z = nullptr;
-    st = wc_field_create(h, in->prec, &e);
-    if (st == WC_OK) st = wc_field_create(h, in->prec, &z);
-    if (st == WC_OK) st = check_cuda(lat, launch_split(lat, in, e, nullptr, lat->stream), "split");
-    if (st == WC_OK) st = check_cuda(lat, launch_ras_schur(lat, z, e, q, dagger ? 1 : 0, lat->stream), "ras_schur");
-    if (st == WC_OK) st = check_cuda(lat, launch_merge(lat, z, nullptr, out, lat->stream), "merge");
-    if (st == WC_OK) st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync");
-    wc_field_destroy(e);
-    wc_field_destroy(z);
+    wc_field *tmp = lat->ras_half[in->prec];
+    for (int k = 0; k < 2 && st == WC_OK; ++k)
+        if (!tmp[k]) st = wc_field_create(h, in->prec, &tmp[k]);
+    if (st == WC_OK) st = check_cuda(lat, launch_split(lat, in, tmp[0], nullptr, lat->stream), "split");
+    if (st == WC_OK)
+        st = check_cuda(lat, launch_ras_schur(lat, tmp[1], tmp[0], q, dagger ? 1 : 0, lat->stream), "ras_schur");
+    if (st == WC_OK) st = check_cuda(lat, launch_merge(lat, tmp[1], nullptr, out, lat->stream), "merge");
     return st;
 }
 

@@ -215,6 +215,7 @@ def test_lockstep_batch(krylov, monkeypatch):
     srcs += [synth.gaussian_source(dims, 40 + k) for k in range(5)]
     srcs += [np.zeros_like(srcs[0]), synth.z2_source(dims, 7)]
     bs = [lat.field(0).load(s) for s in srcs]
+    monkeypatch.setenv("WC_BATCH_LOCKSTEP", "1")
 
     def run():
         xs = [lat.field(0) for _ in srcs]
