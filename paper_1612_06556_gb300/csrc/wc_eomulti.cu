@@ -11,10 +11,11 @@
 // sites of one parity for all n right-hand sides: it stages those shared
 // words once in shared memory (coalesced along the sites), then thread
 // (s, r) computes site s of right-hand side r from the staged links and
-// block and the 8 neighbour spinors of field r (through L1/L2).  The
-// arithmetic per (site, right-hand side) is that of the single-field pass
-// (spin projection, two-row links with the third row rebuilt, the block
-// product, beta = -kappa^2 on the even pass).  Per-field device flags (the
+// block and the 8 neighbour spinors of field r (through L1/L2).  The third
+// row of each link is rebuilt once per site after staging (into shared
+// memory), not once per right-hand side.  The arithmetic per (site,
+// right-hand side) is otherwise that of the single-field pass (spin
+// projection, the block product, beta = -kappa^2 on the even pass).  Per-field device flags (the
 // skip word of a lockstep batch's solver scalars) may skip fields.
 #include <string>
 #include <type_traits>
@@ -66,17 +67,16 @@ struct EoMStage<P32> {
         else
             out = block_word(C, V, pos, item - 24);
     }
-    static __device__ __forceinline__ void link(const W (*st)[kEoMSites], int s, int mu, bool bwd, cx<float> a[6],
-                                                cx<float> c[3])
+    // the two stored rows of link lam = 4 bwd + mu
+    static __device__ __forceinline__ void rows(const W (*st)[kEoMSites], int s, int lam, cx<float> a[6])
     {
-        const int base = (bwd ? 12 : 0) + 3 * mu;
+        const int base = (lam >= 4 ? 12 : 0) + 3 * (lam & 3);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const float4 v = st[base + j][s];
             a[2 * j] = mkc(v.x, v.y);
             a[2 * j + 1] = mkc(v.z, v.w);
         }
-        reconstruct_row2(a, c);
     }
     static __device__ __forceinline__ void block(const W (*st)[kEoMSites], int s, int b, float r[36])
     {
@@ -114,9 +114,10 @@ struct EoMStage<P16> {
             out = __ldg(C.c16 + (size_t)(item - 12) * V + pos);
         }
     }
-    static __device__ __forceinline__ void link(const W (*st)[kEoMSites], int s, int mu, bool bwd, cx<float> a[6],
-                                                cx<float> c[3])
+    static __device__ __forceinline__ void rows(const W (*st)[kEoMSites], int s, int lam, cx<float> a[6])
     {
+        const int mu = lam & 3;
+        const bool bwd = lam >= 4;
         const uint4 v = st[(bwd ? 4 : 0) + mu][s];
         const uint4 w = st[8 + (bwd ? 2 : 0) + (mu >> 1)][s];
         a[0] = h2c(v.x);
@@ -125,7 +126,6 @@ struct EoMStage<P16> {
         a[3] = h2c(v.w);
         a[4] = h2c((mu & 1) ? w.z : w.x);
         a[5] = h2c((mu & 1) ? w.w : w.y);
-        reconstruct_row2(a, c);
     }
     static __device__ __forceinline__ void block(const W (*st)[kEoMSites], int s, int b, float r[36])
     {
@@ -143,10 +143,25 @@ struct EoMStage<P16> {
 
 // the two hops of direction MU of site x (full index, coordinates c) of the
 // half field `in` (opposite parity), links from the stage
+// link lam (mu, or 4 + mu for U_mu(x - mu)) of site s from the stage: the
+// two stored rows and the third row rebuilt once per site at staging
+template <class P>
+__device__ __forceinline__ void eom_link(const typename EoMStage<P>::W (*st)[kEoMSites],
+                                         const float2 (*r3)[3][kEoMSites], int s, int lam, cx<float> a[6],
+                                         cx<float> c[3])
+{
+    EoMStage<P>::rows(st, s, lam, a);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float2 v = r3[lam][j][s];
+        c[j] = mkc(v.x, v.y);
+    }
+}
+
 template <class P, int MU, int SF, int SB>
-__device__ __forceinline__ void eom_hops(const Geom &g, const typename EoMStage<P>::W (*st)[kEoMSites], int s,
-                                        const void *in, const float *in_nrm, int Vh, int x, const int c[4],
-                                        cx<float> acc[12])
+__device__ __forceinline__ void eom_hops(const Geom &g, const typename EoMStage<P>::W (*st)[kEoMSites],
+                                        const float2 (*r3)[3][kEoMSites], int s, const void *in,
+                                        const float *in_nrm, int Vh, int x, const int c[4], cx<float> acc[12])
 {
     const int L = g.L[MU], stride = g.stride[MU];
     {
@@ -156,7 +171,7 @@ __device__ __forceinline__ void eom_hops(const Geom &g, const typename EoMStage<
         const float scale = P::load_spinor_raw(in, in_nrm, Vh, xf >> 1, p);
         const float coef = ((MU == 3 && wrap) ? (float)g.tbc : 1.f) * scale;
         project<MU, SF>(p, h);
-        EoMStage<P>::link(st, s, MU, false, u, r2);
+        eom_link<P>(st, r3, s, MU, u, r2);
         su3_mul(u, r2, h, coef, w);
         reconstruct_add<MU, SF>(acc, w);
     }
@@ -167,24 +182,20 @@ __device__ __forceinline__ void eom_hops(const Geom &g, const typename EoMStage<
         const float scale = P::load_spinor_raw(in, in_nrm, Vh, xb >> 1, p);
         const float coef = ((MU == 3 && wrap) ? (float)g.tbc : 1.f) * scale;
         project<MU, SB>(p, h);
-        EoMStage<P>::link(st, s, MU, true, u, r2);
+        eom_link<P>(st, r3, s, 4 + MU, u, r2);
         su3_adj_mul(u, r2, h, coef, w);
         reconstruct_add<MU, SB>(acc, w);
     }
 }
 
-// full index and coordinates of half index i of parity p (all extents even)
+// full index and coordinates of half index i of parity p (all extents
+// even): 2i is the full index of the site with x rounded down to even
 __device__ __forceinline__ int eom_full_site(const Geom &g, int i, int p, int c[4])
 {
-    const int hx = g.L[0] >> 1;
-    const int xh = i % hx;
-    int rest = i / hx;
-    c[1] = rest % g.L[1];
-    rest /= g.L[1];
-    c[2] = rest % g.L[2];
-    c[3] = rest / g.L[2];
-    c[0] = 2 * xh + ((p + c[1] + c[2] + c[3]) & 1);
-    return wc_idx(c[0] + g.stride[1] * c[1] + g.stride[2] * c[2] + g.stride[3] * c[3], g.V);
+    site_coords_fast(g, 2 * i, c);
+    const int bit = (p + c[1] + c[2] + c[3]) & 1;
+    c[0] += bit;
+    return wc_idx(2 * i + bit, g.V);
 }
 
 // MODE 0 (odd pass): out_r = Blk H hin_r      (Blk = A^-1)
@@ -197,34 +208,46 @@ __global__ void __maxnreg__(80) k_eo_multi(Geom g, int p, GaugeStore U, CloverSt
     using W = typename EoMStage<P>::W;
     constexpr int NW = EoMStage<P>::kWords;
     __shared__ W st[NW][kEoMSites];
+    __shared__ float2 r3[8][3][kEoMSites];   // third rows of the 8 links
     const int Vh = g.V >> 1;
     const int i0 = blockIdx.x * kEoMSites;
-    for (int k = threadIdx.x; k < NW * kEoMSites; k += blockDim.x) {
-        const int s = k % kEoMSites, item = k / kEoMSites, i = i0 + s;
-        if (i >= Vh) continue;
-        int c[4];
-        const int x = eom_full_site(g, i, p, c);
+    // blockDim is a multiple of kEoMSites: a thread stages and computes the
+    // same site s
+    const int s = threadIdx.x % kEoMSites, r = threadIdx.x / kEoMSites, i = i0 + s;
+    int c[4] = {0, 0, 0, 0}, x = 0;
+    if (i < Vh) {
+        x = eom_full_site(g, i, p, c);
         int xb[4];
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu)
             xb[mu] = wc_idx(c[mu] == 0 ? x + (g.L[mu] - 1) * g.stride[mu] : x - g.stride[mu], g.V);
-        EoMStage<P>::stage(U, Blk, g.V, item, x, xb, wc_idx(p * Vh + i, g.V), st[item][s]);
+        const int pos = wc_idx(p * Vh + i, g.V);
+        for (int item = r; item < NW; item += blockDim.x / kEoMSites)
+            EoMStage<P>::stage(U, Blk, g.V, item, x, xb, pos, st[item][s]);
     }
     __syncthreads();
-    const int s = threadIdx.x % kEoMSites, r = threadIdx.x / kEoMSites, i = i0 + s;
+    // the third row of every staged link, once per site
+    for (int q = threadIdx.x; q < 8 * kEoMSites; q += blockDim.x) {
+        const int ss = q % kEoMSites, lam = q / kEoMSites;
+        if (i0 + ss >= Vh) continue;
+        cx<float> u[6], c3[3];
+        EoMStage<P>::rows(st, ss, lam, u);
+        reconstruct_row2(u, c3);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) r3[lam][j][ss] = make_float2(c3[j].re, c3[j].im);
+    }
+    __syncthreads();
     if (r >= a.n || i >= Vh) return;
     if (a.skip[r] && *a.skip[r]) return;
-    int c[4];
-    const int x = eom_full_site(g, i, p, c);
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
     cx<float> h[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) h[k] = mkc(0.f, 0.f);
-    eom_hops<P, 0, SF, SB>(g, st, s, a.hin[r], a.hin_nrm[r], Vh, x, c, h);
-    eom_hops<P, 1, SF, SB>(g, st, s, a.hin[r], a.hin_nrm[r], Vh, x, c, h);
-    eom_hops<P, 2, SF, SB>(g, st, s, a.hin[r], a.hin_nrm[r], Vh, x, c, h);
-    eom_hops<P, 3, SF, SB>(g, st, s, a.hin[r], a.hin_nrm[r], Vh, x, c, h);
+    eom_hops<P, 0, SF, SB>(g, st, r3, s, a.hin[r], a.hin_nrm[r], Vh, x, c, h);
+    eom_hops<P, 1, SF, SB>(g, st, r3, s, a.hin[r], a.hin_nrm[r], Vh, x, c, h);
+    eom_hops<P, 2, SF, SB>(g, st, r3, s, a.hin[r], a.hin_nrm[r], Vh, x, c, h);
+    eom_hops<P, 3, SF, SB>(g, st, r3, s, a.hin[r], a.hin_nrm[r], Vh, x, c, h);
     cx<float> v[12], o[12];
     const float bt = (float)beta;
     if (MODE == 0) {
