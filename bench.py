@@ -990,15 +990,19 @@ def profile_run(args):
     U = synth.haar_links(dims, 1002)
     src = synth.z2_source(dims, 2002)
     lat = wc.Lattice(dims, -1).load_gauge(U).load_clover(1.0, 0.125)
-    which = args.profile_apply or args.profile_ras or args.profile_schur_multi or args.profile_ras_schur
+    which = (args.profile_apply or args.profile_ras or args.profile_schur_multi or args.profile_ras_schur or
+             args.profile_apply_multi)
     prec = {"f32": wc.F32, "f16": wc.F16, "f64": wc.F64}[which]
     if args.profile_apply and args.apply_shape >= 0:
         lat.apply_shape(prec, 0, args.apply_shape)
     a, b = lat.field(prec).load(src), lat.field(prec)
-    if args.profile_schur_multi:
+    if args.profile_schur_multi or args.profile_apply_multi:
         ins = [lat.field(prec).load(synth.point_source(dims, spin=k % 4, colour=k // 4)) for k in range(12)]
         outs = [lat.field(prec) for _ in range(12)]
-        step = lambda: lat.apply_schur_multi(outs, ins)   # noqa: E731
+        if args.profile_apply_multi:
+            step = lambda: lat.apply_multi(outs, ins)   # noqa: E731
+        else:
+            step = lambda: lat.apply_schur_multi(outs, ins)   # noqa: E731
     elif args.profile_apply:
         step = lambda: lat.apply_M(b, a)   # noqa: E731
     elif args.profile_ras_schur:
@@ -1012,7 +1016,7 @@ def profile_run(args):
         step()
     torch.cuda.synchronize()
     kind = ("apply" if args.profile_apply else "ras" if args.profile_ras else
-            "ras_schur" if args.profile_ras_schur else "schur_multi")
+            "ras_schur" if args.profile_ras_schur else "apply_multi" if args.profile_apply_multi else "schur_multi")
     print(json.dumps({"profile": kind, "prec": which,
                       "dims": list(dims), "steps": args.steps}))
 
@@ -1042,13 +1046,16 @@ def main():
                     help="run only --steps RAS applications on --profile-dims (for ncu captures)")
     ap.add_argument("--profile-schur-multi", choices=["f32", "f16"], default=None,
                     help="run only --steps multi-RHS Schur applications (12 fields) on --profile-dims")
+    ap.add_argument("--profile-apply-multi", choices=["f32"], default=None,
+                    help="run only --steps multi-RHS M applications (12 fields) on --profile-dims")
     ap.add_argument("--profile-ras-schur", choices=["f32", "f16"], default=None,
                     help="run only --steps block-Schur RAS applications on --profile-dims")
     ap.add_argument("--profile-dims", default="24,24,24,32")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.profile_apply or args.profile_ras or args.profile_schur_multi or args.profile_ras_schur:
+    if (args.profile_apply or args.profile_ras or args.profile_schur_multi or args.profile_ras_schur or
+            args.profile_apply_multi):
         profile_run(args)
         return
     world, rank, local = dist_setup()

@@ -9,7 +9,8 @@
 // (42 float4 per site, coalesced along the sites), then thread (s, r)
 // computes site s of right-hand side r, reading links and clover from
 // shared memory and the 9 spinors of field r from global memory (neighbours
-// through L1/L2).  Compulsory bytes per site and right-hand side:
+// through L1/L2); the third row of each link is rebuilt once per site
+// after staging.  Compulsory bytes per site and right-hand side:
 // 2 x 96 (spinor in, out) + 480 / n, i.e. 232 B at n = 12 against 672 B for
 // separate applies.  The arithmetic per (site, right-hand side) is that of
 // the single-field operator (spin projection, two-row links with the third
@@ -30,21 +31,34 @@ struct MrhsArgs {
     float4 *out[kMrhsMax];
 };
 
-__device__ __forceinline__ void link_from_stage(const float4 (*st)[kMrhsSites], int base, int s, cx<float> a[6],
-                                                cx<float> c[3])
+// the two stored rows of staged link lam (mu, or 4 + mu for U_mu(x - mu))
+__device__ __forceinline__ void rows_from_stage(const float4 (*st)[kMrhsSites], int lam, int s, cx<float> a[6])
 {
+    const int base = 3 * lam;   // words 0-11 forward, 12-23 backward links
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const float4 v = st[base + j][s];
         a[2 * j] = mkc(v.x, v.y);
         a[2 * j + 1] = mkc(v.z, v.w);
     }
-    reconstruct_row2(a, c);
+}
+
+// link lam of site s: stored rows and the third row rebuilt at staging
+__device__ __forceinline__ void link_from_stage(const float4 (*st)[kMrhsSites], const float2 (*r3)[3][kMrhsSites],
+                                                int lam, int s, cx<float> a[6], cx<float> c[3])
+{
+    rows_from_stage(st, lam, s, a);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float2 v = r3[lam][j][s];
+        c[j] = mkc(v.x, v.y);
+    }
 }
 
 template <int MU, int SF>
-__device__ __forceinline__ void hop_mrhs(const Geom &g, const float4 (*st)[kMrhsSites], int s, const float4 *in,
-                                         int x, const int c[4], float k, cx<float> acc[12])
+__device__ __forceinline__ void hop_mrhs(const Geom &g, const float4 (*st)[kMrhsSites],
+                                         const float2 (*r3)[3][kMrhsSites], int s, const float4 *in, int x,
+                                         const int c[4], float k, cx<float> acc[12])
 {
     const int L = g.L[MU], stl = g.stride[MU];
     {
@@ -54,7 +68,7 @@ __device__ __forceinline__ void hop_mrhs(const Geom &g, const float4 (*st)[kMrhs
         P32::load_spinor(in, nullptr, g.V, xf, p);
         const float coef = (MU == 3 && wrap) ? k * (float)g.tbc : k;
         project<MU, SF>(p, h);
-        link_from_stage(st, 3 * MU, s, u, r2);
+        link_from_stage(st, r3, MU, s, u, r2);
         su3_mul(u, r2, h, coef, w);
         reconstruct_add<MU, SF>(acc, w);
     }
@@ -65,7 +79,7 @@ __device__ __forceinline__ void hop_mrhs(const Geom &g, const float4 (*st)[kMrhs
         P32::load_spinor(in, nullptr, g.V, xb, p);
         const float coef = (MU == 3 && wrap) ? k * (float)g.tbc : k;
         project<MU, -SF>(p, h);
-        link_from_stage(st, 12 + 3 * MU, s, u, r2);
+        link_from_stage(st, r3, 4 + MU, s, u, r2);
         su3_adj_mul(u, r2, h, coef, w);
         reconstruct_add<MU, -SF>(acc, w);
     }
@@ -80,30 +94,42 @@ __global__ void __maxnreg__(80)
                  double kappa)
 {
     __shared__ float4 st[kStageF4][kMrhsSites];
+    __shared__ float2 r3[8][3][kMrhsSites];   // third rows of the 8 links
     const int x0 = blockIdx.x * kMrhsSites;
-    for (int k = threadIdx.x; k < kStageF4 * kMrhsSites; k += blockDim.x) {
-        const int s = k % kMrhsSites, item = k / kMrhsSites, x = x0 + s;
-        if (x >= g.V) continue;
-        float4 v;
-        if (item < 12) {                                   // U_mu(x), plane item of [4][3][V]
-            v = __ldg(U.u32 + (size_t)item * g.V + x);
-        } else if (item < 24) {                            // U_mu(x - mu)
-            const int mu = (item - 12) / 3, j = (item - 12) % 3;
-            int c[4];
-            site_coords(g, x, c);
-            const int xb = wc_idx(c[mu] == 0 ? x + (g.L[mu] - 1) * g.stride[mu] : x - g.stride[mu], g.V);
-            v = __ldg(U.u32 + ((size_t)mu * 3 + j) * g.V + xb);
-        } else {                                           // clover plane item - 24 of [18][V]
-            v = __ldg(C.c32 + (size_t)(item - 24) * g.V + x);
+    // blockDim is a multiple of kMrhsSites: a thread stages and computes the
+    // same site s
+    const int s = threadIdx.x % kMrhsSites, r = threadIdx.x / kMrhsSites, x = x0 + s;
+    int c[4] = {0, 0, 0, 0};
+    if (x < g.V) {
+        site_coords_fast(g, x, c);
+        for (int item = r; item < kStageF4; item += blockDim.x / kMrhsSites) {
+            float4 v;
+            if (item < 12) {                               // U_mu(x), plane item of [4][3][V]
+                v = __ldg(U.u32 + (size_t)item * g.V + x);
+            } else if (item < 24) {                        // U_mu(x - mu)
+                const int mu = (item - 12) / 3, j = (item - 12) % 3;
+                const int xb = wc_idx(c[mu] == 0 ? x + (g.L[mu] - 1) * g.stride[mu] : x - g.stride[mu], g.V);
+                v = __ldg(U.u32 + ((size_t)mu * 3 + j) * g.V + xb);
+            } else {                                       // clover plane item - 24 of [18][V]
+                v = __ldg(C.c32 + (size_t)(item - 24) * g.V + x);
+            }
+            st[item][s] = v;
         }
-        st[item][s] = v;
     }
     __syncthreads();
-    const int s = threadIdx.x % kMrhsSites, r = threadIdx.x / kMrhsSites, x = x0 + s;
+    // the third row of every staged link, once per site
+    for (int q = threadIdx.x; q < 8 * kMrhsSites; q += blockDim.x) {
+        const int ss = q % kMrhsSites, lam = q / kMrhsSites;
+        if (x0 + ss >= g.V) continue;
+        cx<float> u[6], c3[3];
+        rows_from_stage(st, lam, ss, u);
+        reconstruct_row2(u, c3);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) r3[lam][j][ss] = make_float2(c3[j].re, c3[j].im);
+    }
+    __syncthreads();
     if (r >= a.n || x >= g.V || (active && !active[r])) return;
     const float4 *in = a.in[r];
-    int c[4];
-    site_coords(g, x, c);
     cx<float> acc[12];
     {
         cx<float> p[12];
@@ -124,10 +150,10 @@ __global__ void __maxnreg__(80)
     }
     const float k = (float)(-kappa);
     constexpr int SF = KIND == 1 ? +1 : -1;
-    hop_mrhs<0, SF>(g, st, s, in, x, c, k, acc);
-    hop_mrhs<1, SF>(g, st, s, in, x, c, k, acc);
-    hop_mrhs<2, SF>(g, st, s, in, x, c, k, acc);
-    hop_mrhs<3, SF>(g, st, s, in, x, c, k, acc);
+    hop_mrhs<0, SF>(g, st, r3, s, in, x, c, k, acc);
+    hop_mrhs<1, SF>(g, st, r3, s, in, x, c, k, acc);
+    hop_mrhs<2, SF>(g, st, r3, s, in, x, c, k, acc);
+    hop_mrhs<3, SF>(g, st, r3, s, in, x, c, k, acc);
     P32::store_spinor(a.out[r], nullptr, g.V, x, acc);
 }
 
