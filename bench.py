@@ -60,7 +60,7 @@ NCU_TRAFFIC = {
 def kernel_sources_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1612_06556_gb300", "csrc")
-    for f in ("wc_dslash.cu", "wc_stencil.cuh", "wc_device.cuh", "wc_df.cuh", "wc_check.cuh"):
+    for f in ("wc_dslash.cu", "wc_stencil.cuh", "wc_device.cuh", "wc_df.cuh", "wc_df2.cuh", "wc_check.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -91,6 +91,13 @@ __host__ __device__ __forceinline__ cx<R> cfma_conj(cx<R> a, cx<R> b, cx<R> acc)
     return acc;
 }
 
+}  // namespace wc
+
+// the same operators for complex double-FP32 values, on packed float pairs
+#include "wc_df2.cuh"
+
+namespace wc {
+
 // ------------------------------------------------------------------------
 // geometry
 // ------------------------------------------------------------------------
