@@ -968,8 +968,11 @@ def fp64_apply_timing(wc, lat, dims, src, stream, steps=60):
         ms = time_applies(lat, outs, ins, "M", steps, stream)
         lat.apply_M(outs[0], ins[0])
         got[name] = outs[0].store(np.zeros_like(src))
+        # gbs: on the 1536 B this layout moves (18-real links); gbs_1344: on
+        # 1344 B per site, the compulsory bytes with 12-real links
         res[name] = {"ms": ms, "fp64_equiv_tflops": FLOPS_PER_SITE * V / (ms * 1e-3) / 1e12,
-                     "gbs": BYTES_PER_SITE["f64"] * V / (ms * 1e-3) / 1e9}
+                     "gbs": BYTES_PER_SITE["f64"] * V / (ms * 1e-3) / 1e9,
+                     "gbs_1344": 1344 * V / (ms * 1e-3) / 1e9}
     lat.set_fp64_arith(wc.ARITH_F64)
     for f in ins + outs:
         f.close()
