@@ -170,6 +170,7 @@ struct Resources {
     double *d_rmax2 = nullptr;
     cudaGraphConditionalHandle *d_hiter = nullptr, *d_href = nullptr, *d_hgroup = nullptr;
     std::vector<LoMember *> d_members;   // per lockstep group
+    std::vector<double *> d_part;        // per lockstep group: fused partial sums (FP32 vectors)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 
@@ -190,6 +191,7 @@ struct Resources {
         cudaFree(d_hgroup);
         cudaFree(d_fresh);
         for (auto m : d_members) cudaFree(m);
+        for (auto q : d_part) cudaFree(q);
         // states go back to their lattice's pool, with the work fields
         // this batch added
         for (size_t i = 0; i < S.size(); ++i) {
@@ -275,12 +277,16 @@ bool lockstep_enabled(wc_prec kp)
 }
 
 // One lockstep step of the reliable update for the right-hand sides idx of
-// one half lattice, queued on stream s: each of the five vector updates is
-// one launch for all members (member table dm on the device), each of the
-// two Schur applications one multi-right-hand-side launch; the kernels of a
-// stopped member return at once (its skip word).
+// one half lattice, queued on stream s: each vector update is one launch for
+// all members (member table dm on the device), each of the two Schur
+// applications one multi-right-hand-side launch; the kernels of a stopped
+// member return at once (its skip word).  With FP32 vectors the inner
+// products of alpha (<rhat, v>) and omega (<t, s>, |t|^2, |s|^2) are summed
+// by the even Schur pass that produces v and t (partials in part) and
+// finished by a one-CTA-per-member kernel, instead of two more passes over
+// the vectors.
 wc_status enqueue_group_step(wc_lattice half, const std::vector<int> &idx, Resources &R, const LoMember *dm,
-                             cudaStream_t s)
+                             double *part, cudaStream_t s)
 {
     const int m = (int)idx.size();
     std::vector<wc_field> p(m), v(m), sv(m), t(m), tmp(m);
@@ -297,17 +303,24 @@ wc_status enqueue_group_step(wc_lattice half, const std::vector<int> &idx, Resou
         if (!tmp[k]) return set_error(half, WC_ERR_STATE, "lockstep: no odd-site intermediate");
     }
     const bool hv = R.LW[idx[0]].v->prec == WC_F16;
-    const int mb = R.S[idx[0]].red.max_blocks;
+    const bool fused = !hv && part;
+    const int mb = R.S[idx[0]].red.max_blocks, nblk = schur_multi_blocks(half);
+    std::vector<wc_field> rh(m);
+    for (int k = 0; k < m; ++k) rh[k] = R.LW[idx[k]].rhat;
     wc_status st = check_cuda(half, lo_group(LO_STEP_P, half, m, dm, hv, mb, s), "lo_p");
     if (st == WC_OK)
-        st = check_cuda(half, launch_schur_multi(half, m, v.data(), p.data(), tmp.data(), 0, skip.data(), s),
-                        "schur_multi");
-    if (st == WC_OK) st = check_cuda(half, lo_group(LO_STEP_ALPHA, half, m, dm, hv, mb, s), "lo_alpha");
+        st = check_cuda(half, launch_schur_multi(half, m, v.data(), p.data(), tmp.data(), 0, skip.data(), s,
+                                                 fused ? 1 : 0, rh.data(), part), "schur_multi");
+    if (st == WC_OK)
+        st = fused ? check_cuda(half, lo_group_finalize(LO_STEP_ALPHA, m, nblk, part, dm, s), "alpha")
+                   : check_cuda(half, lo_group(LO_STEP_ALPHA, half, m, dm, hv, mb, s), "lo_alpha");
     if (st == WC_OK) st = check_cuda(half, lo_group(LO_STEP_S, half, m, dm, hv, mb, s), "lo_s");
     if (st == WC_OK)
-        st = check_cuda(half, launch_schur_multi(half, m, t.data(), sv.data(), tmp.data(), 0, skip.data(), s),
-                        "schur_multi");
-    if (st == WC_OK) st = check_cuda(half, lo_group(LO_STEP_OMEGA, half, m, dm, hv, mb, s), "lo_omega");
+        st = check_cuda(half, launch_schur_multi(half, m, t.data(), sv.data(), tmp.data(), 0, skip.data(), s,
+                                                 fused ? 2 : 0, nullptr, part), "schur_multi");
+    if (st == WC_OK)
+        st = fused ? check_cuda(half, lo_group_finalize(LO_STEP_OMEGA, m, nblk, part, dm, s), "omega")
+                   : check_cuda(half, lo_group(LO_STEP_OMEGA, half, m, dm, hv, mb, s), "lo_omega");
     if (st == WC_OK) st = check_cuda(half, lo_group(LO_STEP_XR, half, m, dm, hv, mb, s), "lo_xr");
     return st;
 }
@@ -611,7 +624,15 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
         if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_group, group), "copy");
         if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_fresh, zeros), "copy");
         R.d_members.assign(ngroups, nullptr);
+        R.d_part.assign(ngroups, nullptr);
         for (int g = 0; g < ngroups && st == WC_OK; ++g) {
+            const int i0 = members[g][0];
+            if (R.LW[i0].v->prec == WC_F32)
+                st = check_cuda(nullptr, cudaMalloc(reinterpret_cast<void **>(&R.d_part[g]),
+                                                    sizeof(double) * 4 * members[g].size() *
+                                                        (size_t)schur_multi_blocks(lats[i0])),
+                                "cudaMalloc");
+            if (st != WC_OK) break;
             std::vector<LoMember> tab;
             for (int i : members[g]) {
                 const LoVecs &w = R.LW[i];
@@ -677,7 +698,7 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
             }, &iter_nodes);
         if (st == WC_OK)
             st = add_if_nodes(body, {}, h_grp, grp_lead, R, [&](int g) {
-                return enqueue_group_step(lats[members[g][0]], members[g], R, R.d_members[g],
+                return enqueue_group_step(lats[members[g][0]], members[g], R, R.d_members[g], R.d_part[g],
                                           R.streams[members[g][0]]);
             }, &iter_nodes);
         cudaGraphNode_t check1 = nullptr, check2 = nullptr;

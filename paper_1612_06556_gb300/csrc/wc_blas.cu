@@ -941,6 +941,39 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_group(int V, const LoMember *m
     }
 }
 
+// The alpha or omega scalars of every member from the partial sums the
+// even multi-RHS Schur pass wrote (one member per CTA, the partials summed
+// in a fixed order, so the result does not depend on scheduling).
+template <int STEP>
+__global__ void __launch_bounds__(256) k_lo_group_finalize(int nblk, const double *part, const LoMember *members)
+{
+    const LoMember &a = members[blockIdx.x];
+    if (a.sc->skip) return;   // its partials were not written
+    const double *p = part + (size_t)blockIdx.x * nblk * 4;
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) t[c] += p[(size_t)b * 4 + c];
+    __shared__ double sm[8][4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) t[c] = warp_sum(t[c]);
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sm[wid][c] = t[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double res[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) res[c] += sm[w][c];
+        if (STEP == LO_STEP_ALPHA)
+            lo_alpha_update(res, a.sc);
+        else
+            lo_omega_update(res, a.sc);
+    }
+}
+
 // x (FP64) += xlo (FP32); xlo = 0.  FP32 plane j holds components 2j and
 // 2j+1 of each site; FP64 plane k holds component k.
 __global__ void k_hp_add_lo(long long n, int V, double2 *x, float4 *xlo)
@@ -1126,6 +1159,19 @@ cudaError_t lo_group(LoStep step, wc_lattice lat, int m, const LoMember *members
     default: return cudaErrorInvalidValue;
     }
 #undef WC_GROUP_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t lo_group_finalize(LoStep step, int m, int nblk, const double *part, const LoMember *members,
+                              cudaStream_t stream)
+{
+    if (m < 1 || nblk < 1) return cudaErrorInvalidValue;
+    if (step == LO_STEP_ALPHA)
+        k_lo_group_finalize<LO_STEP_ALPHA><<<m, 256, 0, stream>>>(nblk, part, members);
+    else if (step == LO_STEP_OMEGA)
+        k_lo_group_finalize<LO_STEP_OMEGA><<<m, 256, 0, stream>>>(nblk, part, members);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -39,6 +39,13 @@ struct EoMultiArgs {
     void *out[kMrhsMax];
     float *out_nrm[kMrhsMax];
     const int *skip[kMrhsMax];     // nullable: *skip[r] != 0 skips right-hand side r
+    // even pass only: partial sums of field r for the solver step that
+    // follows, per CTA, written to part[(r * gridDim.x + blockIdx.x) * 4 + c]:
+    // red 1: <dot[r], out> (c = 0, 1: real, imaginary part); red 2: <out, vin>,
+    // |out|^2, |vin|^2.  FP32 fields only.
+    int red;
+    const void *dot[kMrhsMax];
+    double *part;
 };
 
 // the staged words of one site: 4 forward and 4 backward links, the block
@@ -237,8 +244,10 @@ __global__ void __maxnreg__(80) k_eo_multi(Geom g, int p, GaugeStore U, CloverSt
         for (int j = 0; j < 3; ++j) r3[lam][j][ss] = make_float2(c3[j].re, c3[j].im);
     }
     __syncthreads();
-    if (r >= a.n || i >= Vh) return;
-    if (a.skip[r] && *a.skip[r]) return;
+    if (r >= a.n) return;
+    if (a.skip[r] && *a.skip[r]) return;   // the whole warp: one field per warp
+    float red[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < Vh) {
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
     cx<float> h[12];
@@ -266,11 +275,40 @@ __global__ void __maxnreg__(80) k_eo_multi(Geom g, int p, GaugeStore U, CloverSt
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = o[k] + bt * h[k];
     P::store_spinor(a.out[r], a.out_nrm[r], Vh, i, o);
+    if (MODE == 1 && a.red == 1) {
+        cx<float> d[12];
+        P32::load_spinor(a.dot[r], nullptr, Vh, i, d);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            red[0] = fmaf(d[k].re, o[k].re, fmaf(d[k].im, o[k].im, red[0]));
+            red[1] = fmaf(d[k].re, o[k].im, fmaf(-d[k].im, o[k].re, red[1]));
+        }
+    } else if (MODE == 1 && a.red == 2) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            red[0] = fmaf(o[k].re, v[k].re, fmaf(o[k].im, v[k].im, red[0]));
+            red[1] = fmaf(o[k].re, v[k].im, fmaf(-o[k].im, v[k].re, red[1]));
+            red[2] = fmaf(o[k].re, o[k].re, fmaf(o[k].im, o[k].im, red[2]));
+            red[3] = fmaf(v[k].re, v[k].re, fmaf(v[k].im, v[k].im, red[3]));
+        }
+    }
+    }   // i < Vh
+    if (MODE == 1 && a.red != 0) {
+        // the warp holds the 32 sites of this CTA for field r
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int o2 = 16; o2 > 0; o2 >>= 1) red[c] += __shfl_xor_sync(0xffffffffu, red[c], o2);
+        if (s == 0)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a.part[((size_t)r * gridDim.x + blockIdx.x) * 4 + c] = (double)red[c];
+    }
 }
 
 template <class P, int DAG>
 cudaError_t launch_eom(const wc_lattice_s *full, int n, wc_field const *outs, wc_field const *ins,
-                       wc_field const *tmps, const int *const *skip, cudaStream_t stream)
+                       wc_field const *tmps, const int *const *skip, int red, wc_field const *dots, double *part,
+                       cudaStream_t stream)
 {
     const int Vh = full->g.V >> 1;
     const dim3 grid((Vh + kEoMSites - 1) / kEoMSites), block(kEoMSites * n);
@@ -296,6 +334,9 @@ cudaError_t launch_eom(const wc_lattice_s *full, int n, wc_field const *outs, wc
         a.out[r] = outs[r]->data;
         a.out_nrm[r] = outs[r]->nrm;
     }
+    a.red = red;
+    a.part = part;
+    for (int r = 0; r < n && red == 1; ++r) a.dot[r] = dots[r]->data;
     k_eo_multi<P, DAG, 1><<<grid, block, 0, stream>>>(full->g, 0, full->gauge, full->ceo, a,
                                                       -full->kappa * full->kappa);
     return cudaGetLastError();
@@ -304,19 +345,23 @@ cudaError_t launch_eom(const wc_lattice_s *full, int n, wc_field const *outs, wc
 }  // namespace
 
 cudaError_t launch_schur_multi(wc_lattice half, int n, wc_field const *outs, wc_field const *ins,
-                               wc_field const *tmps, int dagger, const int *const *skip, cudaStream_t stream)
+                               wc_field const *tmps, int dagger, const int *const *skip, cudaStream_t stream,
+                               int red, wc_field const *dots, double *part)
 {
     if (n < 1 || n > kMrhsMax || !half->schur_parent) return cudaErrorInvalidValue;
     const wc_lattice_s *full = half->schur_parent;
     const wc_prec pr = ins[0]->prec;
+    if (red != 0 && (pr != WC_F32 || !part || (red == 1 && !dots))) return cudaErrorInvalidValue;
     if (pr == WC_F32)
-        return dagger ? launch_eom<P32, 1>(full, n, outs, ins, tmps, skip, stream)
-                      : launch_eom<P32, 0>(full, n, outs, ins, tmps, skip, stream);
+        return dagger ? launch_eom<P32, 1>(full, n, outs, ins, tmps, skip, red, dots, part, stream)
+                      : launch_eom<P32, 0>(full, n, outs, ins, tmps, skip, red, dots, part, stream);
     if (pr == WC_F16)
-        return dagger ? launch_eom<P16, 1>(full, n, outs, ins, tmps, skip, stream)
-                      : launch_eom<P16, 0>(full, n, outs, ins, tmps, skip, stream);
+        return dagger ? launch_eom<P16, 1>(full, n, outs, ins, tmps, skip, 0, nullptr, nullptr, stream)
+                      : launch_eom<P16, 0>(full, n, outs, ins, tmps, skip, 0, nullptr, nullptr, stream);
     return cudaErrorInvalidValue;
 }
+
+int schur_multi_blocks(wc_lattice half) { return (half->g.V + kEoMSites - 1) / kEoMSites; }
 
 }  // namespace wc
 

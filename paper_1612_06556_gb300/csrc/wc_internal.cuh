@@ -164,7 +164,11 @@ cudaError_t launch_apply_multi(wc_lattice lat, int n, const wc_field *outs, cons
 // `half`, tmps[r] its odd-site intermediates; skip (nullable) holds per field
 // a device flag (nullable) whose nonzero value skips it
 cudaError_t launch_schur_multi(wc_lattice half, int n, wc_field const *outs, wc_field const *ins,
-                               wc_field const *tmps, int dagger, const int *const *skip, cudaStream_t stream);
+                               wc_field const *tmps, int dagger, const int *const *skip, cudaStream_t stream,
+                               int red = 0, wc_field const *dots = nullptr, double *part = nullptr);
+// CTAs of one multi-RHS Schur pass on the half lattice `half` (the second
+// dimension of its partial sums)
+int schur_multi_blocks(wc_lattice half);
 
 // even-odd preconditioning (wc_evenodd.cu)
 // tmp: a half-lattice field of out's precision for the odd-site

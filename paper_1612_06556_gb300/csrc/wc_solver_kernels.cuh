@@ -67,5 +67,10 @@ LoMember lo_member(SolverState &S, wc_field r, wc_field rhat, wc_field p, wc_fie
 // scalars; a member whose skip word is set does nothing.
 cudaError_t lo_group(LoStep step, wc_lattice lat, int m, const LoMember *members, bool half, int max_blocks,
                      cudaStream_t stream);
+// alpha (step LO_STEP_ALPHA) or omega (LO_STEP_OMEGA) of the m members from
+// the partial sums part[member][nblk][4] that the even multi-RHS Schur pass
+// wrote (FP32 vectors), one CTA per member
+cudaError_t lo_group_finalize(LoStep step, int m, int nblk, const double *part, const LoMember *members,
+                              cudaStream_t stream);
 
 }  // namespace wc
