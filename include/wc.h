@@ -223,17 +223,19 @@ wc_status wc_field_export_f32(wc_field f, float *data);
  * the library: data (canonical complex128, or complex64 when complex64 is
  * nonzero) must be device memory or page-locked host memory (WC_ERR_ARG
  * otherwise, nothing queued); the call returns once the work is queued.
- * Host-to-device copies run on a second stream of the lattice, so the copy
- * of the next step's input overlaps the kernels and the device-to-host copy
- * of the current step; the import kernel and everything after it stay in
- * the lattice stream's order.  The caller keeps imported host data unchanged
- * and reads exported host data only after wc_sync(lat).  The lattice holds
- * two extra canonical-size device buffers from the first asynchronous call
- * with host data until it is destroyed. */
+ * Host-to-device copies run on a second stream of the lattice and
+ * device-to-host copies on a third one (from two alternating staging
+ * buffers), so the copy of the next step's input and the copy out of the
+ * current step's result overlap each other and the kernels; the import and
+ * export kernels and everything between them stay in the lattice stream's
+ * order.  The caller keeps imported host data unchanged and reads exported
+ * host data only after wc_sync(lat).  The lattice holds three extra
+ * canonical-size device buffers from the first asynchronous call with host
+ * data until it is destroyed. */
 wc_status wc_field_import_async(wc_field f, const void *data, int complex64);
 wc_status wc_field_export_async(wc_field f, void *data, int complex64);
-/* Block until every kernel and copy queued on the lattice (both streams)
- * has finished. */
+/* Block until every kernel and copy queued on the lattice (all three
+ * streams) has finished. */
 wc_status wc_sync(wc_lattice lat);
 /* dst = src converted to dst's precision, times scale (any precisions). */
 wc_status wc_field_copy(wc_field dst, wc_field src, double scale);

@@ -520,28 +520,40 @@ wc_status async_setup(wc_lattice lat)
 {
     if (lat->copy_stream) return WC_OK;
     const size_t bytes = sizeof(double2) * 12 * (size_t)lat->g.V;
-    cudaStream_t cs = nullptr;
-    cudaEvent_t ready = nullptr, freed = nullptr;
-    double2 *in = nullptr, *out = nullptr;
+    cudaStream_t cs = nullptr, co = nullptr;
+    cudaEvent_t ev[6] = {};   // in ready, in free, out ready 0/1, out free 0/1
+    double2 *in = nullptr, *out[2] = {nullptr, nullptr};
     wc_status st = check_cuda(lat, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate(copy)");
-    if (st == WC_OK) st = check_cuda(lat, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "cudaEventCreate");
-    if (st == WC_OK) st = check_cuda(lat, cudaEventCreateWithFlags(&freed, cudaEventDisableTiming), "cudaEventCreate");
+    if (st == WC_OK)
+        st = check_cuda(lat, cudaStreamCreateWithFlags(&co, cudaStreamNonBlocking), "cudaStreamCreate(copy out)");
+    for (int k = 0; k < 6 && st == WC_OK; ++k)
+        st = check_cuda(lat, cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming), "cudaEventCreate");
     if (st == WC_OK) st = check_cuda(lat, dalloc(&in, bytes), "cudaMalloc(staging)");
-    if (st == WC_OK) st = check_cuda(lat, dalloc(&out, bytes), "cudaMalloc(staging)");
-    // nothing to wait for before the first copy
-    if (st == WC_OK) st = check_cuda(lat, cudaEventRecord(freed, lat->stream), "cudaEventRecord");
+    for (int b = 0; b < 2 && st == WC_OK; ++b) st = check_cuda(lat, dalloc(&out[b], bytes), "cudaMalloc(staging)");
+    // nothing to wait for before the first copies
+    if (st == WC_OK) st = check_cuda(lat, cudaEventRecord(ev[1], lat->stream), "cudaEventRecord");
+    for (int b = 0; b < 2 && st == WC_OK; ++b)
+        st = check_cuda(lat, cudaEventRecord(ev[4 + b], co), "cudaEventRecord");
     if (st != WC_OK) {
         if (cs) cudaStreamDestroy(cs);
-        if (ready) cudaEventDestroy(ready);
-        if (freed) cudaEventDestroy(freed);
+        if (co) cudaStreamDestroy(co);
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
         cudaFree(in);
-        cudaFree(out);
+        cudaFree(out[0]);
+        cudaFree(out[1]);
         return st;
     }
-    lat->ev_in_ready = ready;
-    lat->ev_in_free = freed;
+    lat->ev_in_ready = ev[0];
+    lat->ev_in_free = ev[1];
+    for (int b = 0; b < 2; ++b) {
+        lat->ev_out_ready[b] = ev[2 + b];
+        lat->ev_out_free[b] = ev[4 + b];
+        lat->astage_out[b] = out[b];
+    }
     lat->astage_in = in;
-    lat->astage_out = out;
+    lat->out_buf = 0;
+    lat->copy_out_stream = co;
     lat->copy_stream = cs;
     return WC_OK;
 }
@@ -595,10 +607,14 @@ wc_status field_export_async(wc_field f, T *data)
     const int V = lat->g.V;
     T *dst = data;
     wc_status st = WC_OK;
+    const int b = lat->out_buf;
     if (!dev) {
         st = async_setup(lat);
         if (st != WC_OK) return st;
-        dst = reinterpret_cast<T *>(lat->astage_out);   // the previous copy out is earlier in this stream
+        // the copy out that last used buffer b must be done
+        st = check_cuda(lat, cudaStreamWaitEvent(lat->stream, lat->ev_out_free[b], 0), "wait");
+        if (st != WC_OK) return st;
+        dst = reinterpret_cast<T *>(lat->astage_out[b]);
     }
     dim3 grid((V + 255) / 256), block(256);
     if (f->prec == WC_F64)
@@ -608,9 +624,17 @@ wc_status field_export_async(wc_field f, T *data)
     else
         k_export<P16, T><<<grid, block, 0, lat->stream>>>(V, f->data, f->nrm, dst);
     st = check_launch(lat, "export");
-    if (st == WC_OK && !dev)
-        st = check_cuda(lat, cudaMemcpyAsync(data, lat->astage_out, sizeof(T) * 12 * (size_t)V,
-                                             cudaMemcpyDeviceToHost, lat->stream), "cudaMemcpyAsync(export)");
+    if (st == WC_OK && !dev) {
+        st = check_cuda(lat, cudaEventRecord(lat->ev_out_ready[b], lat->stream), "record");
+        if (st == WC_OK)
+            st = check_cuda(lat, cudaStreamWaitEvent(lat->copy_out_stream, lat->ev_out_ready[b], 0), "wait");
+        if (st == WC_OK)
+            st = check_cuda(lat, cudaMemcpyAsync(data, lat->astage_out[b], sizeof(T) * 12 * (size_t)V,
+                                                 cudaMemcpyDeviceToHost, lat->copy_out_stream),
+                            "cudaMemcpyAsync(export)");
+        if (st == WC_OK) st = check_cuda(lat, cudaEventRecord(lat->ev_out_free[b], lat->copy_out_stream), "record");
+        if (st == WC_OK) lat->out_buf = b ^ 1;
+    }
     return st;
 }
 
@@ -662,14 +686,17 @@ wc_status wc_destroy_lattice(wc_lattice lat)
     free_clover(lat->cinv);
     free_clover(lat->ceo);
     cudaFree(lat->staging);
-    if (lat->copy_stream) {
-        cudaStreamSynchronize(lat->copy_stream);
-        cudaStreamDestroy(lat->copy_stream);
-    }
-    if (lat->ev_in_ready) cudaEventDestroy(lat->ev_in_ready);
-    if (lat->ev_in_free) cudaEventDestroy(lat->ev_in_free);
+    for (cudaStream_t cs : {lat->copy_stream, lat->copy_out_stream})
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+    for (cudaEvent_t e : {lat->ev_in_ready, lat->ev_in_free, lat->ev_out_ready[0], lat->ev_out_ready[1],
+                          lat->ev_out_free[0], lat->ev_out_free[1]})
+        if (e) cudaEventDestroy(e);
     cudaFree(lat->astage_in);
-    cudaFree(lat->astage_out);
+    cudaFree(lat->astage_out[0]);
+    cudaFree(lat->astage_out[1]);
     wc_destroy_lattice(lat->ext);
     delete lat;
     return WC_OK;
@@ -847,6 +874,8 @@ wc_status wc_sync(wc_lattice lat)
     if (!lat) return set_error(nullptr, WC_ERR_ARG, "lattice is NULL");
     wc_status st = check_cuda(lat, cudaStreamSynchronize(lat->stream), "sync");
     if (st == WC_OK && lat->copy_stream) st = check_cuda(lat, cudaStreamSynchronize(lat->copy_stream), "sync");
+    if (st == WC_OK && lat->copy_out_stream)
+        st = check_cuda(lat, cudaStreamSynchronize(lat->copy_out_stream), "sync");
     return st;
 }
 

@@ -72,11 +72,15 @@ struct wc_lattice_s {
     size_t staging_bytes = 0;
     // asynchronous import/export: host-to-device copies run on copy_stream
     // into astage_in (ev_in_ready: copied; ev_in_free: consumed by the
-    // import kernel), device-to-host copies on the lattice stream from
-    // astage_out
-    cudaStream_t copy_stream = nullptr;
+    // import kernel); device-to-host copies run on copy_out_stream from two
+    // alternating buffers astage_out[b] (ev_out_ready[b]: written by the
+    // export kernel; ev_out_free[b]: copied out), so that a step's copy out
+    // overlaps the next step's kernels
+    cudaStream_t copy_stream = nullptr, copy_out_stream = nullptr;
     cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr;
-    double2 *astage_in = nullptr, *astage_out = nullptr;
+    cudaEvent_t ev_out_ready[2] = {nullptr, nullptr}, ev_out_free[2] = {nullptr, nullptr};
+    double2 *astage_in = nullptr, *astage_out[2] = {nullptr, nullptr};
+    int out_buf = 0;
     // even-odd: A^-1 (built on first use) and the half lattice whose
     // operator is the Schur complement M^ (V/2 sites, shares gauge/clover)
     wc::CloverStore cinv;                     // A^-1, parity-ordered planes (even-odd kernels)

@@ -150,7 +150,7 @@ def test_async_import_export_pipeline():
     dims = (4, 6, 4, 6)
     U = synth.exp_links(dims, 0.3, 2101)
     lat = make_lattice(dims, U, 1.0, 0.12, -1)
-    srcs = [synth.gaussian_source(dims, 2102 + i) for i in range(4)]
+    srcs = [synth.gaussian_source(dims, 2102 + i) for i in range(7)]   # the two copy-out buffers alternate
     fin, fout = lat.field(1), lat.field(1)
     for dt in (np.complex64, np.complex128):
         ref = []
