@@ -355,3 +355,26 @@ def test_singular_clover_block_is_reported():
     lat.apply_M(out, lat.field(0).load(psi))
     ref = oracle.apply_M(dims, -1, 0.125, 8.0, U, psi)
     assert_elementwise(out.store(np.zeros_like(psi)), ref, 1e-12)
+
+
+def test_batch_pools_survive_clover_reload_and_destroy():
+    """The solver states and half-lattice fields a lattice keeps for its
+    batches are reused by a batch after a clover reload with another kappa
+    (A^-1 rebuilt, same half lattice) and freed with the lattice; the
+    solutions stay correct."""
+    w = wc()
+    dims = (6, 6, 6, 8)
+    U = synth.exp_links(dims, 0.3, 1601)
+    lat = make_lattice(dims, U, 1.0, 0.124, -1)
+    srcs = [synth.point_source(dims, spin=k, colour=k % 3) for k in range(4)]
+    for kappa in (0.124, 0.12):
+        if kappa != 0.124:
+            lat.load_clover(1.0, kappa)
+        xs = [lat.field(0) for _ in srcs]
+        infos = w.solve_batch([lat] * 4, xs, [lat.field(0).load(s) for s in srcs], tol=1e-10,
+                              solver=w.SOLVER_RELIABLE, even_odd=True)
+        for info, x, s in zip(infos, xs, srcs):
+            assert info.status == 0
+            r = s - oracle.apply_M(dims, -1, kappa, 1.0, U, x.store(np.zeros_like(s)))
+            assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(s)
+    lat.close()
