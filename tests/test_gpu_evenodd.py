@@ -47,7 +47,7 @@ def test_schur_matches_oracle(dims, tbc, prec, dagger):
     assert_elementwise(out, eo.schur(psi, dagger), TOL[prec])
 
 
-@pytest.mark.parametrize("n", [1, 5, 12])
+@pytest.mark.parametrize("n", [1, 5, 12, 16])
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_schur_multi_matches_oracle(n, prec, dagger):
