@@ -496,6 +496,12 @@ def batch_comparison(wc, args):
                              block=(4, 4, 4, 4), solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True)
     run_batch(eo_ras)
     infos_eo_ras, t_eo_ras = run_batch(eo_ras)
+    # the same with RAS on the blocks' own Schur complements
+    eo_ras_schur = wc.solve_params(tol=1e-10, max_iter=5000, precond=wc.PRECOND_RAS, inner_prec=wc.F32,
+                                   block=(4, 4, 4, 4), solver=wc.SOLVER_RELIABLE, delta=0.01, even_odd=True,
+                                   ras_schur=True)
+    run_batch(eo_ras_schur)
+    infos_eo_ras_s, t_eo_ras_s = run_batch(eo_ras_schur)
     t0 = time.perf_counter()
     seq_eo = []
     for lat, b in zip(lats, bs):
@@ -532,6 +538,9 @@ def batch_comparison(wc, args):
             "even_odd_fp16_vectors_df32_batch_seconds": t_eo_h16_df,
             "even_odd_fp16_vectors_df32_all_ok": all(i.status == 0 for i in infos_eo_h16_df),
             "even_odd_ras_batch_seconds": t_eo_ras, "even_odd_ras_all_ok": all(i.status == 0 for i in infos_eo_ras),
+            "even_odd_ras_schur_batch_seconds": t_eo_ras_s,
+            "even_odd_ras_schur_all_ok": all(i.status == 0 for i in infos_eo_ras_s),
+            "even_odd_ras_schur_steps": [min(i.iters for i in infos_eo_ras_s), max(i.iters for i in infos_eo_ras_s)],
             "even_odd_ras_steps": [min(i.iters for i in infos_eo_ras), max(i.iters for i in infos_eo_ras)],
             "even_odd_steps": [min(i.iters for i in infos_eo), max(i.iters for i in infos_eo)],
             "even_odd_max_true_rel_resid": max(i.true_rel_resid for i in infos_eo),
@@ -880,6 +889,7 @@ def solve_comparison(wc, lat, src, args):
                                             inner_iters=100, krylov_prec=wc.F16, even_odd=True)),
                      # the same solvers with their FP64 operator steps in double-FP32 arithmetic
                      ("fp64_plain_df32", dict(precond=wc.PRECOND_NONE)),
+                     ("mixed_ras_f32_df32", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F32)),
                      ("eo_fp64_plain_df32", dict(precond=wc.PRECOND_NONE, even_odd=True)),
                      ("reliable_ras_f16_df32", dict(precond=wc.PRECOND_RAS, inner_prec=wc.F16,
                                                     solver=wc.SOLVER_RELIABLE, delta=0.01)),
