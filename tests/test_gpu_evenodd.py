@@ -378,3 +378,28 @@ def test_batch_pools_survive_clover_reload_and_destroy():
             r = s - oracle.apply_M(dims, -1, kappa, 1.0, U, x.store(np.zeros_like(s)))
             assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(s)
     lat.close()
+
+
+def test_lockstep_member_with_nan_source_does_not_disturb_the_group(monkeypatch):
+    """A source with a NaN entry in a lockstep group: that right-hand side
+    reports WC_ERR_NAN and skips every step; the other members of its group
+    converge to the oracle's solutions."""
+    w = wc()
+    monkeypatch.setenv("WC_BATCH_LOCKSTEP", "1")
+    dims = (6, 6, 6, 8)
+    U = synth.exp_links(dims, 0.3, 1701)
+    lat = make_lattice(dims, U, 1.0, 0.124, -1)
+    srcs = [synth.point_source(dims, spin=k, colour=k % 3) for k in range(4)]
+    bad = synth.gaussian_source(dims, 1702)
+    bad[5, 1, 2] = np.nan
+    srcs.insert(2, bad)
+    xs = [lat.field(0) for _ in srcs]
+    infos = w.solve_batch([lat] * len(srcs), xs, [lat.field(0).load(s) for s in srcs], tol=1e-10,
+                          solver=w.SOLVER_RELIABLE, even_odd=True, check=False)
+    assert infos[2].status == 6   # WC_ERR_NAN
+    for k, (info, x, s) in enumerate(zip(infos, xs, srcs)):
+        if k == 2:
+            continue
+        assert info.status == 0
+        r = s - oracle.apply_M(dims, -1, 0.124, 1.0, U, x.store(np.zeros_like(s)))
+        assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(s)
