@@ -280,7 +280,7 @@ wc_status wc_apply_schur(wc_lattice lat, wc_field out, wc_field in, int dagger);
  * kind (0 M, 1 M^+, 2 H) by timing the candidates on the first apply (that
  * first call blocks; not done while the stream is being captured, where the
  * default shape is used).  force_index >= 0 pins candidate #force_index
- * (0..21; WC_ERR_ARG if its tile does not divide the lattice or it is a
+ * (0..23; WC_ERR_ARG if its tile does not divide the lattice or it is a
  * register-capped shape with FP64); -1 only reports.  shape_out receives
  * {threads per CTA, tile x, y, z, t (all 0: lexicographic), flags}, flags
  * = register cap (0 none, 1: 64, 2: 85 registers per thread) + 4 if the

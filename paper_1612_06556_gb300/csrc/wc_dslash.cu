@@ -144,6 +144,10 @@ constexpr ApplyShape kShapes[] = {
     {256, {0, 0, 0, 0}, 2, 0}, {128, {8, 4, 4, 1}, 2, 0}, {256, {8, 4, 4, 2}, 2, 0}, {128, {8, 4, 2, 2}, 2, 0},
     {128, {0, 0, 0, 0}, 2, 1}, {256, {0, 0, 0, 0}, 2, 1}, {128, {0, 0, 0, 0}, 0, 1}, {256, {0, 0, 0, 0}, 0, 1},
     {128, {0, 0, 0, 0}, 2, 1, 1}, {256, {0, 0, 0, 0}, 2, 1, 1},
+    // small lattices: CTAs of 32 or 64 sites spread a few thousand sites
+    // over more SMs (the FP64 operator is bound by the FP64 pipe of the SMs
+    // it runs on)
+    {32, {0, 0, 0, 0}, 0, 0}, {64, {0, 0, 0, 0}, 0, 0},
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
@@ -249,6 +253,26 @@ int tune_shape(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t
         cudaEventDestroy(e0);
         return 0;
     }
+    // the candidates are timed on four input / output pairs in turn (the
+    // caller's and three copies of its input), so that on lattices whose
+    // fields outgrow L2 every launch streams its spinors from HBM as the
+    // solvers' applies do; without memory for the copies, on the caller's
+    // pair alone
+    const size_t bytes = spinor_bytes(in->prec, lat->g.V);
+    wc_field ins[4] = {in, nullptr, nullptr, nullptr}, outs[4] = {out, nullptr, nullptr, nullptr};
+    int npair = 1;
+    for (int k = 1; k < 4; ++k) {
+        if (wc_field_create(lat, in->prec, &ins[k]) != WC_OK) break;
+        if (wc_field_create(lat, in->prec, &outs[k]) != WC_OK) {
+            wc_field_destroy(ins[k]);
+            ins[k] = nullptr;
+            break;
+        }
+        cudaMemcpyAsync(ins[k]->data, in->data, bytes, cudaMemcpyDeviceToDevice, stream);
+        if (in->nrm) cudaMemcpyAsync(ins[k]->nrm, in->nrm, sizeof(float) * lat->g.V, cudaMemcpyDeviceToDevice, stream);
+        npair = k + 1;
+    }
+    cudaGetLastError();
     float best_ms[kNumShapes];
     for (int i = 0; i < kNumShapes; ++i) best_ms[i] = 1e30f;
     for (int round = 0; round < 3; ++round) {
@@ -256,7 +280,8 @@ int tune_shape(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t
             if (!shape_fits(lat->g, kShapes[i], P::kCaps)) continue;
             if (launch_shape<P>(lat, out, in, kind, kShapes[i], stream) != cudaSuccess) continue;
             cudaEventRecord(e0, stream);
-            for (int r = 0; r < 16; ++r) launch_shape<P>(lat, out, in, kind, kShapes[i], stream);
+            for (int r = 0; r < 16; ++r)
+                launch_shape<P>(lat, outs[r % npair], ins[r % npair], kind, kShapes[i], stream);
             cudaEventRecord(e1, stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) continue;
             float ms = 0.f;
@@ -269,6 +294,10 @@ int tune_shape(wc_lattice lat, wc_field out, wc_field in, int kind, cudaStream_t
         if (best_ms[i] < best_ms[best]) best = i;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    for (int k = 1; k < npair; ++k) {
+        wc_field_destroy(ins[k]);
+        wc_field_destroy(outs[k]);
+    }
     cudaGetLastError();
     return best;
 }

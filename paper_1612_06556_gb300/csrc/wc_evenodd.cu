@@ -347,7 +347,10 @@ cudaError_t launch_eo_p(const wc_lattice_s *full, int parity, int mode, const wc
                         wc_field_s *out, double beta, cudaStream_t stream)
 {
     const int Vh = full->g.V >> 1;
-    dim3 grid((Vh + 127) / 128), block(128);
+    // CTAs of 128 sites; on small lattices (fewer than two such CTAs per SM)
+    // CTAs of 32, so that the sites spread over more SMs
+    const int threads = Vh < 2 * 128 * sm_count() ? 32 : 128;
+    dim3 grid((Vh + threads - 1) / threads), block(threads);
     const void *hd = hin ? hin->data : nullptr;
     const float *hn = hin ? hin->nrm : nullptr;
     const void *vd = vin ? vin->data : nullptr;

@@ -239,7 +239,7 @@ def test_apply_argument_errors():
     assert e.value.status == 1
 
 
-N_SHAPES = 22
+N_SHAPES = 24
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
@@ -263,7 +263,7 @@ def test_every_launch_shape_matches_oracle(prec):
         assert_elementwise(gpu_apply(lat, psi, prec, "M"), ref, TOL[prec])
         assert_elementwise(gpu_apply(lat, psi, prec, "Mdag"), refd, TOL[prec])
         tested += 1
-    assert tested == (9 if prec == 0 else 22)   # FP64 takes no register-capped shape
+    assert tested == (11 if prec == 0 else 24)   # FP64 takes no register-capped shape
     with pytest.raises(w.WCError):
         lat.apply_shape(prec, 0, force=N_SHAPES)
 
