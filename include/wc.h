@@ -123,7 +123,12 @@ typedef struct {
  * without RAS.  even_odd = 1 runs any of the three on the even-site Schur
  * complement (with or without RAS), as the paper's solvers do (Sec. 2).
  * The true residual |b - M x| / |b| reported and tested against tol is FP64
- * in all of them, on the full lattice. */
+ * in all of them, on the full lattice.  An even-odd RELIABLE solve leaves
+ * the convergence test to that full residual: its half-lattice solve stops,
+ * without a last FP64 refresh, once the low-precision recurrence residual is
+ * below 0.5 tol (the environment variable WC_EO_DEFER_MARGIN sets another
+ * factor; 0 keeps the refresh), and resumes, confirming in FP64 itself, if
+ * the full residual is then above tol. */
 typedef enum { WC_SOLVER_FLEXIBLE = 0, WC_SOLVER_RELIABLE = 1, WC_SOLVER_NESTED = 2 } wc_solver_kind;
 
 typedef struct {

@@ -841,20 +841,10 @@ static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_
     wc_status worst = WC_OK;
     for (int i = 0; i < n && st == WC_OK; ++i) {
         wc_lattice lat = lats[i];
-        cudaStream_t s = lat->stream;
-        st = check_cuda(lat, launch_eo(lat, 1, 3, 0, F(i, 2), F(i, 1), F(i, 3), lat->kappa, s), "x_o");
-        if (st == WC_OK) st = check_cuda(lat, launch_merge(lat, F(i, 2), F(i, 3), xs[i], s), "merge");
-        SolverVecs w;
-        wc_solve_params p0 = *p;
-        p0.precond = WC_PRECOND_NONE;
-        p0.even_odd = 0;
-        lat->st.stream = s;
-        if (st == WC_OK) st = solver_vectors(lat, lat->st, p0, &w);
-        if (st == WC_OK) st = enqueue_true_residual(lat, lat->st, 0, xs[i], bs[i], w);
-        if (st == WC_OK) st = read_scalars(lat, lat->st);
+        double rr = 0.0;
+        st = eo_reconstruct_residual(lat, 0, F(i, 0), F(i, 1), F(i, 2), F(i, 3), xs[i], &rr);
         if (st != WC_OK) break;
         wc_solve_info &inf = infos[i];
-        const double rr = lat->st.scal_host->rr;
         inf.true_rel_resid = bb[i] > 0.0 ? sqrt(rr / bb[i]) : 0.0;
         if (!isfinite(rr)) inf.status = WC_ERR_NAN;
         else if (bb[i] == 0.0 || rr <= p->tol * p->tol * bb[i]) inf.status = WC_OK;

@@ -903,6 +903,44 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_rho_h(int V, HF rhat, HF r, Re
     if (grid_reduce_f<2>(acc, rs, rs.result)) lo_rho_update(rs.result, sc);
 }
 
+// End of a reliable update in one pass (the FP64 residual, its
+// low-precision copy and the new rho of the recurrence): r = b - r (r holds
+// op x), rr = |r|^2; rlo = r rounded to the Krylov storage PL (FP32, or
+// FP16 with its per-site scale); rho = <rhat, rlo> of the stored rlo, beta
+// recomputed as lo_rho does.  One site per thread.
+template <class PL>
+__global__ void __launch_bounds__(kRedBlock) k_refresh_tail(int V, const void *b, void *r, void *rlo, float *rlo_n,
+                                                            const void *rhat, const float *rhat_n, ReduceScratch rs,
+                                                            SolverScalars *sc)
+{
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        cx<double> bv[12], rv[12];
+        P64::load_spinor(b, nullptr, V, x, bv);
+        P64::load_spinor(r, nullptr, V, x, rv);
+        cx<float> lo[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            rv[k] = bv[k] - rv[k];
+            acc[0] += rv[k].re * rv[k].re + rv[k].im * rv[k].im;
+            lo[k] = mkc((float)rv[k].re, (float)rv[k].im);
+        }
+        P64::store_spinor(r, nullptr, V, x, rv);
+        PL::store_spinor(rlo, rlo_n, V, x, lo);
+        PL::as_stored(lo);
+        cx<float> h[12];
+        PL::load_spinor(rhat, rhat_n, V, x, h);
+        float d[2] = {0.f, 0.f};
+        cdot_acc(h, lo, d);
+        acc[1] += d[0];
+        acc[2] += d[1];
+    }
+    if (grid_reduce<3>(acc, rs, rs.result)) {
+        sc->rr = rs.result[0];
+        lo_rho_update(rs.result + 1, sc);
+    }
+}
+
 // The step kernels for all members of a lockstep group: member blockIdx.y,
 // its part of the grid blockIdx.x (grid-stride loops and the block-partial
 // reductions use only the x extent).
@@ -1117,6 +1155,17 @@ cudaError_t lo_rho(wc_lattice lat, SolverState &S, wc_field rhat, wc_field r)
         k_lo_rho_h<<<WC_GRID_SITES(V)>>>(V, hf(rhat), hf(r), S.red, S.scal);
     else
         k_lo_rho<<<WC_GRID(n)>>>(n, f4(rhat), f4(r), S.red, S.scal);
+    return cudaGetLastError();
+}
+cudaError_t refresh_tail(wc_lattice lat, SolverState &S, const wc_field b, wc_field r_hp, wc_field r, wc_field rhat)
+{
+    const int V = lat->g.V;
+    if (half_vectors(r))
+        k_refresh_tail<P16><<<WC_GRID_SITES(V)>>>(V, b->data, r_hp->data, r->data, r->nrm, rhat->data, rhat->nrm,
+                                                  S.red, S.scal);
+    else
+        k_refresh_tail<P32><<<WC_GRID_SITES(V)>>>(V, b->data, r_hp->data, r->data, nullptr, rhat->data, nullptr,
+                                                  S.red, S.scal);
     return cudaGetLastError();
 }
 LoMember lo_member(SolverState &S, wc_field r, wc_field rhat, wc_field p, wc_field v, wc_field s, wc_field t,

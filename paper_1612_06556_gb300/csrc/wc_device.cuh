@@ -272,6 +272,10 @@ struct P64 {
 #pragma unroll
         for (int k = 0; k < 12; ++k) p[(size_t)k * V + x] = make_double2(s[k].re, s[k].im);
     }
+    // s as a store_spinor followed by a load_spinor returns it (computed in
+    // registers: load_spinor reads through the non-coherent path, which need
+    // not see a write of the same kernel)
+    static __device__ __forceinline__ void as_stored(cx<double> s[12]) {}
     // U_mu(x): a[0..2] = row 0, a[3..5] = row 1, c[0..2] = row 2
     static __device__ __forceinline__ void load_link(const GaugeStore &g, int V, int mu, int x,
                                                      cx<double> a[6], cx<double> c[3])
@@ -332,6 +336,8 @@ struct P32 {
         for (int j = 0; j < 6; ++j)
             p[(size_t)j * V + x] = make_float4(s[2 * j].re, s[2 * j].im, s[2 * j + 1].re, s[2 * j + 1].im);
     }
+    // s as a store_spinor followed by a load_spinor returns it
+    static __device__ __forceinline__ void as_stored(cx<float> s[12]) {}
     static __device__ __forceinline__ void load_link(const GaugeStore &g, int V, int mu, int x,
                                                      cx<float> a[6], cx<float> c[3])
     {
@@ -386,6 +392,13 @@ struct PDF {
         double2 *p = static_cast<double2 *>(d);
 #pragma unroll
         for (int k = 0; k < 12; ++k) p[(size_t)k * V + x] = make_double2(df_to_double(s[k].re), df_to_double(s[k].im));
+    }
+    // s as a store_spinor followed by a load_spinor returns it
+    static __device__ __forceinline__ void as_stored(cx<df> s[12])
+    {
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            s[k] = {df_from_double(df_to_double(s[k].re)), df_from_double(df_to_double(s[k].im))};
     }
     static __device__ __forceinline__ void load_link(const GaugeStore &g, int V, int mu, int x, cx<df> a[6],
                                                      cx<df> c[3])
@@ -479,6 +492,16 @@ struct P16 {
             p[(size_t)j * V + x] = v;
         }
         nrm[x] = m;
+    }
+    // s as a store_spinor followed by a load_spinor returns it
+    static __device__ __forceinline__ void as_stored(cx<float> s[12])
+    {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) m = fmax3(m, fabsf(s[k].re), fabsf(s[k].im));
+        const float inv = m > 0.f ? 1.f / m : 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s[k] = m * h2c(c2h(s[k].re * inv, s[k].im * inv));
     }
     static __device__ __forceinline__ void load_link(const GaugeStore &g, int V, int mu, int x,
                                                      cx<float> a[6], cx<float> c[3])

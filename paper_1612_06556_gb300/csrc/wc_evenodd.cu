@@ -232,12 +232,16 @@ __device__ __forceinline__ void clover_eo(const CloverStore &S, int V, int pos, 
 //        2: out = vin + beta h
 //        3: out = Cinv (vin + beta h)
 //        4: out = Cinv vin
+//        5: out = Cinv w and out2 = w - C out, w = vin + beta h (with
+//           vin = b_o, h = H_oe x_e, beta = k: the reconstructed x_o and
+//           the odd-site residual b_o - (A_oo x_o - k H_oe x_e) of the
+//           x_o as stored, in one pass; FP64 fields only)
 // The site-local part of k_eo after the hops h: everything but the hops,
 // in the arithmetic of P.
 template <class P, int MODE>
 __device__ __forceinline__ void eo_tail(const Geom &g, int p, const CloverStore &C, const CloverStore &Ci,
-                                        const void *vin, const float *vin_nrm, void *out, float *out_nrm, double beta,
-                                        int Vh, int i, const cx<typename P::real> h[12])
+                                        const void *vin, const float *vin_nrm, void *out, float *out_nrm,
+                                        void *out2, double beta, int Vh, int i, const cx<typename P::real> h[12])
 {
     using R = typename P::real;
     cx<R> v[12], o[12];
@@ -254,7 +258,7 @@ __device__ __forceinline__ void eo_tail(const Geom &g, int p, const CloverStore 
             P::store_spinor(out, out_nrm, Vh, i, o);
             return;
         }
-        if (MODE == 2 || MODE == 3)
+        if (MODE == 2 || MODE == 3 || MODE == 5)
 #pragma unroll
             for (int k = 0; k < 12; ++k) v[k] = v[k] + bt * h[k];
         if (MODE == 2) {
@@ -264,12 +268,22 @@ __device__ __forceinline__ void eo_tail(const Geom &g, int p, const CloverStore 
     }
     clover_eo<P>(Ci, g.V, wc_idx(p * Vh + i, g.V), v, o);
     P::store_spinor(out, out_nrm, Vh, i, o);
+    if constexpr (MODE == 5) {
+        // the residual of x_o as the caller receives it (the stored value)
+        cx<R> y[12];
+        P::as_stored(o);
+        clover_eo<P>(C, g.V, wc_idx(p * Vh + i, g.V), o, y);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) y[k] = v[k] - y[k];
+        P::store_spinor(out2, nullptr, Vh, i, y);
+    }
 }
 
 template <class P, int DAG, int MODE>
 __global__ void __launch_bounds__(128, P::kEoMinBlocks) k_eo(Geom g, int p, GaugeStore U, CloverStore C, CloverStore Ci,
                                             const void *hin, const float *hin_nrm, const void *vin,
-                                            const float *vin_nrm, void *out, float *out_nrm, double beta)
+                                            const float *vin_nrm, void *out, float *out_nrm, void *out2,
+                                            double beta)
 {
     using R = typename P::real;
     const int Vh = g.V >> 1;
@@ -279,15 +293,17 @@ __global__ void __launch_bounds__(128, P::kEoMinBlocks) k_eo(Geom g, int p, Gaug
     const int x = full_site(g, i, p, c);
     if constexpr (std::is_same<P, PDF>::value) {
         // compact form (instruction cache): hops and clover rows in runtime
-        // loops.  (Moving the site-local A / A^-1 products, or the two x
-        // hops, to FP64 as the full-lattice kernel does measured 3 % slower
-        // here: this kernel runs at a fixed 128-register cap.)
+        // loops.  Measured at 24^3x32 (even-odd FP64-class solve, 40 such
+        // passes): the site-local A / A^-1 products in FP64 on the FP64 pipe
+        // 2 % slower, with the two x hops in FP64 too 8 % slower, and a
+        // 168- or 255-register cap (12 or 8 warps per SM, no spills) 2 % and
+        // 23 % slower than this form at 128 registers and 16 warps.
         cx<R> h[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) h[k] = mkc(R(0.0f, 0.0f), R(0.0f, 0.0f));
         if (MODE != 4)
             hops_rt<P, DAG ? +1 : -1>(g, U, hin, hin_nrm, Vh, x, c, R(1.0f, 0.0f), h, [](int y) { return y >> 1; });
-        eo_tail<P, MODE>(g, p, C, Ci, vin, vin_nrm, out, out_nrm, beta, Vh, i, h);
+        eo_tail<P, MODE>(g, p, C, Ci, vin, vin_nrm, out, out_nrm, out2, beta, Vh, i, h);
     } else {
         cx<R> h[12];
 #pragma unroll
@@ -301,7 +317,7 @@ __global__ void __launch_bounds__(128, P::kEoMinBlocks) k_eo(Geom g, int p, Gaug
             eo_hop_dir<P, 2, SF, SB>(g, U, hin, hin_nrm, Vh, x, c, one, h);
             eo_hop_dir<P, 3, SF, SB>(g, U, hin, hin_nrm, Vh, x, c, one, h);
         }
-        eo_tail<P, MODE>(g, p, C, Ci, vin, vin_nrm, out, out_nrm, beta, Vh, i, h);
+        eo_tail<P, MODE>(g, p, C, Ci, vin, vin_nrm, out, out_nrm, out2, beta, Vh, i, h);
     }
 }
 
@@ -344,7 +360,7 @@ __global__ void k_merge(Geom g, const void *ev, const float *ev_nrm, const void 
 
 template <class P, int DAG>
 cudaError_t launch_eo_p(const wc_lattice_s *full, int parity, int mode, const wc_field_s *hin, const wc_field_s *vin,
-                        wc_field_s *out, double beta, cudaStream_t stream)
+                        wc_field_s *out, double beta, cudaStream_t stream, wc_field_s *out2)
 {
     const int Vh = full->g.V >> 1;
     // CTAs of 128 sites; on small lattices (fewer than two such CTAs per SM)
@@ -355,15 +371,23 @@ cudaError_t launch_eo_p(const wc_lattice_s *full, int parity, int mode, const wc
     const float *hn = hin ? hin->nrm : nullptr;
     const void *vd = vin ? vin->data : nullptr;
     const float *vn = vin ? vin->nrm : nullptr;
+    void *o2 = out2 ? out2->data : nullptr;
 #define WC_EO(M)                                                                                                \
     k_eo<P, DAG, M><<<grid, block, 0, stream>>>(full->g, parity, full->gauge, full->ceo, full->cinv, hd, hn,    \
-                                                vd, vn, out->data, out->nrm, beta)
+                                                vd, vn, out->data, out->nrm, o2, beta)
     switch (mode) {
     case 0: WC_EO(0); break;
     case 1: WC_EO(1); break;
     case 2: WC_EO(2); break;
     case 3: WC_EO(3); break;
-    default: WC_EO(4);
+    case 4: WC_EO(4); break;
+    default:
+        if constexpr (std::is_same<P, P64>::value || std::is_same<P, PDF>::value) {
+            if (!out2 || out2->prec != WC_F64) return cudaErrorInvalidValue;
+            WC_EO(5);
+        } else {
+            return cudaErrorInvalidValue;
+        }
     }
 #undef WC_EO
     return cudaGetLastError();
@@ -373,20 +397,20 @@ cudaError_t launch_eo_p(const wc_lattice_s *full, int parity, int mode, const wc
 
 // one parity-stencil step on half fields of the full lattice `full`
 cudaError_t launch_eo(const wc_lattice_s *full, int parity, int mode, int dagger, const wc_field_s *hin,
-                      const wc_field_s *vin, wc_field_s *out, double beta, cudaStream_t stream)
+                      const wc_field_s *vin, wc_field_s *out, double beta, cudaStream_t stream, wc_field_s *out2)
 {
     const wc_prec pr = out->prec;
     if (pr == WC_F64 && full->fp64_arith == WC_ARITH_DF32)
-        return dagger ? launch_eo_p<PDF, 1>(full, parity, mode, hin, vin, out, beta, stream)
-                      : launch_eo_p<PDF, 0>(full, parity, mode, hin, vin, out, beta, stream);
+        return dagger ? launch_eo_p<PDF, 1>(full, parity, mode, hin, vin, out, beta, stream, out2)
+                      : launch_eo_p<PDF, 0>(full, parity, mode, hin, vin, out, beta, stream, out2);
     if (pr == WC_F64)
-        return dagger ? launch_eo_p<P64, 1>(full, parity, mode, hin, vin, out, beta, stream)
-                      : launch_eo_p<P64, 0>(full, parity, mode, hin, vin, out, beta, stream);
+        return dagger ? launch_eo_p<P64, 1>(full, parity, mode, hin, vin, out, beta, stream, out2)
+                      : launch_eo_p<P64, 0>(full, parity, mode, hin, vin, out, beta, stream, out2);
     if (pr == WC_F32)
-        return dagger ? launch_eo_p<P32, 1>(full, parity, mode, hin, vin, out, beta, stream)
-                      : launch_eo_p<P32, 0>(full, parity, mode, hin, vin, out, beta, stream);
-    return dagger ? launch_eo_p<P16, 1>(full, parity, mode, hin, vin, out, beta, stream)
-                  : launch_eo_p<P16, 0>(full, parity, mode, hin, vin, out, beta, stream);
+        return dagger ? launch_eo_p<P32, 1>(full, parity, mode, hin, vin, out, beta, stream, out2)
+                      : launch_eo_p<P32, 0>(full, parity, mode, hin, vin, out, beta, stream, out2);
+    return dagger ? launch_eo_p<P16, 1>(full, parity, mode, hin, vin, out, beta, stream, out2)
+                  : launch_eo_p<P16, 0>(full, parity, mode, hin, vin, out, beta, stream, out2);
 }
 
 // od may be NULL: only the even half is written

@@ -40,18 +40,20 @@ namespace wc {
 // even-odd operator on a half lattice, 27-31: the half-lattice FP64 fields
 // b_e, b_o, x_e, x_o, b^_e of an even-odd solve, 32-35: full-lattice FP32
 // and FP16 in/out fields of the RAS preconditioner of an even-odd solve,
-// 36-43: the low-precision BiCGStab vectors when they are FP16) and the
-// stream the solve is queued on.  A lattice owns one for its single-RHS
+// 36-43: the low-precision BiCGStab vectors when they are FP16, 44-45: the
+// even and odd halves of the final full residual of an even-odd solve) and
+// the stream the solve is queued on.  A lattice owns one for its single-RHS
 // calls; a batched solve creates one per RHS.
 constexpr int kSchurSlot = 24;
 constexpr int kEoSlot = 27;
 constexpr int kRasEoSlot = 32;
 constexpr int kHalfKrylovSlot = 36;
+constexpr int kEoResSlot = 44;
 struct SolverState {
     SolverScalars *scal = nullptr;
     SolverScalars *scal_host = nullptr;
     ReduceScratch red;
-    wc_field_s *work[44] = {};
+    wc_field_s *work[46] = {};
     cudaStream_t stream = nullptr;
     SolverState *inner = nullptr;   // state of a nested inner solve, created on first use
 };
@@ -179,8 +181,10 @@ int schur_multi_blocks(wc_lattice half);
 // intermediate (nullptr: the half lattice's own, shared by its callers)
 cudaError_t launch_schur(wc_lattice half, wc_field out, wc_field in, int dagger, cudaStream_t stream,
                          wc_field tmp = nullptr);
+// out2: the second output of mode 5 (nullptr for the other modes)
 cudaError_t launch_eo(const wc_lattice_s *full, int parity, int mode, int dagger, const wc_field_s *hin,
-                      const wc_field_s *vin, wc_field_s *out, double beta, cudaStream_t stream);
+                      const wc_field_s *vin, wc_field_s *out, double beta, cudaStream_t stream,
+                      wc_field_s *out2 = nullptr);
 cudaError_t launch_split(const wc_lattice_s *full, const wc_field_s *f, wc_field_s *ev, wc_field_s *od,
                          cudaStream_t stream);
 cudaError_t launch_merge(const wc_lattice_s *full, const wc_field_s *ev, const wc_field_s *od, wc_field_s *f,

@@ -25,6 +25,7 @@
 // (the flexible one with an FP32 BiCGStab as K), and the even-odd wrapper
 // that runs any of them on the Schur complement of a half lattice.
 #include <math.h>
+#include <stdlib.h>
 
 #include <chrono>
 #include <new>
@@ -62,6 +63,17 @@ wc_status check_ras_params(wc_lattice lat, const wc_ras_params *p)
 namespace {
 
 double2 *d2(wc_field f) { return static_cast<double2 *>(f->data); }
+
+// An even-odd reliable half solve ends unconfirmed at |r| <= m tol, m = 0.5
+// unless WC_EO_DEFER_MARGIN gives another (0: always confirm in the half
+// solve; a large m makes the confirmation fail, for tests of the resume).
+double defer_margin()
+{
+    const char *e = getenv("WC_EO_DEFER_MARGIN");
+    if (!e || !*e) return 0.5;
+    const double m = atof(e);
+    return m > 0.0 && isfinite(m) ? m : 0.0;
+}
 
 }  // namespace
 
@@ -190,6 +202,39 @@ wc_status enqueue_true_residual(wc_lattice lat, SolverState &S, int kind, wc_fie
 static wc_status bicgstab_impl(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
                                const wc_solve_params &p, double bb, wc_solve_info *info, int iters_done);
 
+// End of an even-odd solve on the lattice's stream: x_o = A_oo^-1 (b_o +
+// k H_oe x_e) together with the odd-site residual r_o = b_o - (A_oo x_o -
+// k H_oe x_e) of the stored x_o (one pass), the even-site (M x)_e = A_ee x_e
+// - k H_eo x_o, x = (x_e, x_o), and *rr = |b_e - (M x)_e|^2 + |r_o|^2, the
+// squared true residual of the full system (M^+ for kind 1), in the FP64
+// operator arithmetic of the lattice.  Scratch: slots kEoResSlot, +1 of the
+// half lattice's own state; one synchronisation.
+wc_status eo_reconstruct_residual(wc_lattice lat, int kind, wc_field be, wc_field bo, wc_field xe, wc_field xo,
+                                  wc_field x, double *rr)
+{
+    wc_lattice h = nullptr;
+    wc_status st = half_lattice(lat, &h);
+    if (st != WC_OK) return st;
+    SolverState &R = h->st;
+    R.stream = lat->stream;
+    cudaStream_t s = lat->stream;
+    wc_field re = state_work(h, R, kEoResSlot, WC_F64, &st);
+    wc_field ro = st == WC_OK ? state_work(h, R, kEoResSlot + 1, WC_F64, &st) : nullptr;
+    if (st != WC_OK) return st;
+    const double k = lat->kappa;
+    st = check_cuda(lat, launch_eo(lat, 1, 5, kind, xe, bo, xo, k, s, ro), "x_o and r_o");
+    if (st == WC_OK) st = check_cuda(lat, launch_eo(lat, 0, 1, kind, xo, xe, re, -k, s), "(M x)_e");
+    if (st == WC_OK) st = check_cuda(lat, launch_merge(lat, xe, xo, x, s), "merge");
+    if (st == WC_OK) st = check_cuda(lat, residual(h, R, d2(be), d2(re)), "residual");
+    if (st == WC_OK) st = check_cuda(lat, norm2_to_result(h, R, d2(ro)), "norm2");
+    if (st == WC_OK)
+        st = check_cuda(lat, cudaMemcpyAsync(R.red.host_result, R.red.result, sizeof(double), cudaMemcpyDeviceToHost, s),
+                        "copy");
+    if (st == WC_OK) st = read_scalars(h, R);
+    if (st == WC_OK) *rr = R.scal_host->rr + R.red.host_result[0];
+    return st;
+}
+
 // x == 0 (one reduction and a synchronisation): the residual of a zero
 // start vector is b and needs no FP64 operator application
 static wc_status x_is_zero(wc_lattice lat, SolverState &S, wc_field x, bool *zero)
@@ -203,19 +248,21 @@ static wc_status x_is_zero(wc_lattice lat, SolverState &S, wc_field x, bool *zer
     return st;
 }
 wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
-                            const wc_solve_params &p, wc_solve_info *info, int iters_done, double bb);
+                            const wc_solve_params &p, wc_solve_info *info, int iters_done, double bb,
+                            double defer_rr, bool *unconfirmed);
 
 // Solve op x = b (op = M for kind 0, M^+ for kind 1); x, b FP64 fields.
 // S: solver state (scratch); S.stream: the stream everything is queued on.
 wc_status bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, const wc_solve_params &p,
-                   wc_solve_info *info, int iters_done, double bb)
+                   wc_solve_info *info, int iters_done, double bb, double defer_rr, bool *unconfirmed)
 {
     wc_solve_info local{};
     wc_solve_info *out = info ? info : &local;
     *out = wc_solve_info{};
     out->status = WC_ERR_CUDA;
+    if (unconfirmed) *unconfirmed = false;
     const wc_status st = p.solver == WC_SOLVER_RELIABLE
-                             ? reliable_bicgstab(lat, S, kind, x, b, p, out, iters_done, bb)
+                             ? reliable_bicgstab(lat, S, kind, x, b, p, out, iters_done, bb, defer_rr, unconfirmed)
                              : bicgstab_impl(lat, S, kind, x, b, p, bb, out, iters_done);
     if (st != WC_OK && (out->status == WC_OK || out->status == WC_ERR_CUDA)) out->status = st;
     return st;
@@ -237,6 +284,13 @@ wc_status bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_so
 //   residual equals the Schur residual on the even sites and vanishes on
 //   the odd ones), x_o = A_oo^-1 (b_o + k H_oe x_e); the true FP64 residual
 //   of the full system is recomputed at the end.
+// The reliable-update solver's last FP64 refresh of the Schur residual
+// would compute, up to rounding, the same number as that final full
+// residual, so the half solve ends without it once its low-precision
+// recurrence residual is below half the tolerance (defer_margin): the
+// full residual then confirms convergence.  Where it does not (the
+// recurrence had drifted), the half solve resumes from x_e with its own
+// FP64 confirmation and the full residual is taken again.
 static wc_status eo_bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p,
                              wc_solve_info *info)
 {
@@ -261,31 +315,39 @@ static wc_status eo_bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, c
     double bb = 0.0, bbh = 0.0;
     if (st == WC_OK) st = reduce_norm2(lat, b, &bb);
     if (st == WC_OK) st = reduce_norm2(h, bh, &bbh);
+    wc_solve_params q = p;
+    q.even_odd = 0;
+    if (bbh > 0.0 && bb > 0.0) q.tol = p.tol * sqrt(bb / bbh);
+    const double m = defer_margin();
+    const double defer_rr = p.solver == WC_SOLVER_RELIABLE ? m * m * q.tol * q.tol * bbh : 0.0;
+    bool unconfirmed = false;
     if (st == WC_OK) {
-        wc_solve_params q = p;
-        q.even_odd = 0;
-        if (bbh > 0.0 && bb > 0.0) q.tol = p.tol * sqrt(bb / bbh);
-        const wc_status sr = bicgstab(h, h->st, kind, xe, bh, q, &inf, 0, bbh);
+        const wc_status sr = bicgstab(h, h->st, kind, xe, bh, q, &inf, 0, bbh, defer_rr, &unconfirmed);
         if (sr != WC_OK && sr != WC_ERR_NOT_CONVERGED && sr != WC_ERR_BREAKDOWN) st = sr;
     }
-    const int iters = inf.iters, restarts = inf.restarts;
+    int iters = inf.iters, restarts = inf.restarts;
     wc_status half_status = inf.status;
-    if (st == WC_OK) st = check_cuda(lat, launch_eo(lat, 1, 3, kind, xe, bo, xo, k, s), "x_o");
-    if (st == WC_OK) st = check_cuda(lat, launch_merge(lat, xe, xo, x, s), "merge");
-    // true residual of the full system in FP64
-    SolverVecs w;
-    wc_solve_params p0 = p;
-    p0.precond = WC_PRECOND_NONE;
-    p0.even_odd = 0;
-    if (st == WC_OK) st = solver_vectors(lat, lat->st, p0, &w);
-    if (st == WC_OK) st = enqueue_true_residual(lat, lat->st, kind, x, b, w);
-    if (st == WC_OK) st = read_scalars(lat, lat->st);
+    bool ok = false;
+    double rr = 0.0;
+    for (int pass = 0; pass < 2 && st == WC_OK; ++pass) {
+        if (pass == 1) {   // the deferred confirmation failed: resume from x_e
+            const wc_status sr = bicgstab(h, h->st, kind, xe, bh, q, &inf, iters, bbh);
+            if (sr != WC_OK && sr != WC_ERR_NOT_CONVERGED && sr != WC_ERR_BREAKDOWN) st = sr;
+            iters = inf.iters;
+            restarts += inf.restarts;
+            half_status = inf.status;
+            if (st != WC_OK) break;
+        }
+        st = eo_reconstruct_residual(lat, kind, be, bo, xe, xo, x, &rr);
+        if (st != WC_OK) break;
+        ok = bb == 0.0 || rr <= p.tol * p.tol * bb;
+        if (ok || !unconfirmed) break;
+    }
     if (st != WC_OK) return inf.status = st;
     inf = wc_solve_info{};
     inf.iters = iters;
     inf.restarts = restarts;
-    inf.true_rel_resid = bb > 0.0 ? sqrt(lat->st.scal_host->rr / bb) : 0.0;
-    const bool ok = bb == 0.0 || lat->st.scal_host->rr <= p.tol * p.tol * bb;
+    inf.true_rel_resid = bb > 0.0 ? sqrt(rr / bb) : 0.0;
     inf.status = ok ? WC_OK : (half_status != WC_OK ? half_status : WC_ERR_NOT_CONVERGED);
     if (!ok) set_error(lat, inf.status, "even-odd solve: true residual above tol");
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -490,9 +552,9 @@ static wc_status enqueue_refresh(wc_lattice lat, SolverState &S, int kind, wc_fi
 wc_status enqueue_refresh_full(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, wc_field r_hp,
                                const LoVecs &w)
 {
-    wc_status st = enqueue_refresh(lat, S, kind, x, b, r_hp, w);
-    if (st == WC_OK) st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
-    if (st == WC_OK) st = check_cuda(lat, lo_rho(lat, S, w.rhat, w.r), "lo_rho");
+    wc_status st = check_cuda(lat, hp_add_lo(lat, S, static_cast<double2 *>(x->data), w.xlo), "hp_add_lo");
+    if (st == WC_OK) st = check_cuda(lat, launch_apply(lat, r_hp, x, kind, S), "apply");
+    if (st == WC_OK) st = check_cuda(lat, refresh_tail(lat, S, b, r_hp, w.r, w.rhat), "refresh");
     return st;
 }
 
@@ -542,7 +604,8 @@ static wc_status nested_inner(wc_lattice lat, SolverState &S, const wc_solve_par
 }
 
 wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
-                            const wc_solve_params &p, wc_solve_info *info, int iters_done, double bb)
+                            const wc_solve_params &p, wc_solve_info *info, int iters_done, double bb,
+                            double defer_rr, bool *unconfirmed)
 {
     auto t0 = std::chrono::steady_clock::now();
     wc_solve_info &inf = *info;
@@ -627,10 +690,21 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
                 break;
             }
             if (h.rr > rmax2) rmax2 = h.rr;
-            if (h.rr <= d2 * rmax2 || h.rr <= tol2) {
+            if (defer_rr > 0.0 && h.rr <= defer_rr) {
+                // the caller confirms with its own true residual: fold the
+                // correction only
+                st = check_cuda(lat, hp_add_lo(lat, S, static_cast<double2 *>(x->data), w.xlo), "hp_add_lo");
+                if (st != WC_OK) return st;
+                if (unconfirmed) *unconfirmed = true;
+                inf.true_rel_resid = sqrt(h.rr / bb);
+                converged = true;
+                break;
+            }
+            if (h.rr <= d2 * rmax2 || (defer_rr <= 0.0 && h.rr <= tol2)) {
                 // reliable update: fold the FP32 correction into the FP64
                 // solution and restart the recurrence from the true residual
-                st = enqueue_refresh(lat, S, kind, x, b, r_hp, w);
+                // (its low-precision copy and rho in the same pass)
+                st = enqueue_refresh_full(lat, S, kind, x, b, r_hp, w);
                 if (st == WC_OK) st = read_scalars(lat, S);
                 if (st != WC_OK) return st;
                 rr_true = S.scal_host->rr;
@@ -639,9 +713,6 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
                     converged = true;
                     break;
                 }
-                st = check_cuda(lat, launch_copy(lat, w.r, r_hp, 1.0, nullptr, 0, S.stream), "cast residual");
-                if (st == WC_OK) st = check_cuda(lat, lo_rho(lat, S, w.rhat, w.r), "lo_rho");
-                if (st != WC_OK) return st;
                 rmax2 = rr_true;
                 rr_refresh = rr_true;
             }

@@ -28,11 +28,20 @@ wc_status enqueue_iteration(wc_lattice lat, SolverState &S, const wc_solve_param
                             const SolverVecs &w);
 wc_status enqueue_true_residual(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
                                 const SolverVecs &w);
+// end of an even-odd solve of the full lattice lat from its half fields:
+// x_o reconstructed, x = (x_e, x_o), *rr = |b - op x|^2 (one synchronisation)
+wc_status eo_reconstruct_residual(wc_lattice lat, int kind, wc_field be, wc_field bo, wc_field xe, wc_field xo,
+                                  wc_field x, double *rr);
 
 // Host-driven solve of op x = b (kind 0: M, 1: M^+) with state S, counting
 // iters_done iterations already spent; bb = |b|^2 or < 0 to compute it.
+// defer_rr > 0 (reliable-update solver only): a caller that recomputes the
+// true residual itself lets the solve end, without an FP64 operator
+// application, once the low-precision recurrence residual |r|^2 is at most
+// defer_rr; *unconfirmed is then set (x holds the folded correction).
 wc_status bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b, const wc_solve_params &p,
-                   wc_solve_info *info, int iters_done, double bb);
+                   wc_solve_info *info, int iters_done, double bb, double defer_rr = 0.0,
+                   bool *unconfirmed = nullptr);
 // Same with the lattice's own state and stream.
 wc_status bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, const wc_solve_params &p, wc_solve_info *info);
 

@@ -146,6 +146,56 @@ def test_even_odd_solve(solver):
         assert info.iters < full.iters
 
 
+@pytest.mark.parametrize("solver,krylov,arith", [(0, 1, 0), (1, 1, 0), (1, 2, 0), (1, 2, 1), (2, 2, 1)])
+def test_even_odd_reported_residual_is_that_of_the_solution(solver, krylov, arith):
+    """The full residual an even-odd solve reports (x_o reconstructed
+    together with the odd-site residual in one pass, the even sites in a
+    second) is |b - M x| / |b| of the x it returns, recomputed by the
+    oracle; also for a solve stopped after one step."""
+    w = wc()
+    dims, kappa, csw, tbc = (8, 8, 8, 16), 0.125, 1.0, -1
+    U = synth.exp_links(dims, 0.3, 151)
+    src = synth.gaussian_source(dims, 152)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    lat.set_fp64_arith(arith)
+    b = lat.field(0).load(src)
+    for max_iter, tol in [(2000, 1e-10), (1, 1e-14)]:
+        x = lat.field(0)
+        info = lat.solve(x, b, tol=tol, solver=solver, krylov_prec=krylov, even_odd=True, max_iter=max_iter,
+                         max_restarts=0, check=False)
+        sol = x.store(np.zeros_like(src))
+        ref = np.linalg.norm(src - oracle.apply_M(dims, tbc, kappa, csw, U, sol)) / np.linalg.norm(src)
+        assert abs(info.true_rel_resid - ref) <= 1e-3 * ref + 1e-14
+        if max_iter == 2000:
+            assert info.status == 0 and ref <= 1e-10
+        else:
+            assert info.status != 0 and ref > 1e-6
+
+
+@pytest.mark.parametrize("margin", ["0", "1e3"])
+def test_even_odd_reliable_confirmation_paths(margin, monkeypatch):
+    """Even-odd reliable solves with the half solve's own FP64 confirmation
+    (margin 0) and with a deferral margin so large that the full-residual
+    check fails and the half solve resumes: both end converged, checked with
+    the oracle's M, in at least the default path's iterations."""
+    w = wc()
+    dims, kappa, csw, tbc = (8, 8, 8, 16), 0.125, 1.0, -1
+    U = synth.exp_links(dims, 0.3, 161)
+    src = synth.gaussian_source(dims, 162)
+    lat = make_lattice(dims, U, csw, kappa, tbc)
+    b = lat.field(0).load(src)
+    kw = dict(tol=1e-10, solver=w.SOLVER_RELIABLE, krylov_prec=w.F16, even_odd=True, max_iter=2000)
+    base = lat.solve(lat.field(0), b, **kw)
+    monkeypatch.setenv("WC_EO_DEFER_MARGIN", margin)
+    x = lat.field(0)
+    info = lat.solve(x, b, **kw)
+    assert info.status == 0 and info.true_rel_resid <= 1e-10
+    sol = x.store(np.zeros_like(src))
+    r = src - oracle.apply_M(dims, tbc, kappa, csw, U, sol)
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+    assert info.iters >= base.iters - 1
+
+
 def test_even_odd_action_and_zero_source():
     """M^+ solves through the action (even-odd vs full lattice give the same
     S), and a zero source gives x = 0."""
