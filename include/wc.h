@@ -436,7 +436,10 @@ wc_status wc_solve_bicgstab(wc_lattice lat, wc_field x, wc_field b, const wc_sol
  * step's Schur applications are one multi-right-hand-side launch for the
  * group; a stopped member skips its kernels); the environment variable
  * WC_BATCH_LOCKSTEP=0 gives every right-hand side its own branch instead,
- * WC_BATCH_LOCKSTEP=1 groups FP16 Krylov vectors too.  A zero initial guess skips the
+ * WC_BATCH_LOCKSTEP=1 groups FP16 Krylov vectors too.  An even-odd
+ * RELIABLE batch leaves each right-hand side's convergence test to its full
+ * residual, as a single even-odd solve does (see wc_solve_params;
+ * WC_EO_DEFER_MARGIN).  A zero initial guess skips the
  * start's operator application.  Each lattice keeps the solver states and
  * work fields of its largest batch (and, with even_odd, five FP64
  * half-lattice fields per right-hand side) for the next batch, until

@@ -66,6 +66,7 @@ struct BatchItem {
     double d2;      // delta^2 (reliable update)
     int max_iter;
     int pad;
+    double defer2;  // > 0: stop unconfirmed once the recurrence |r|^2 <= defer2 (the caller confirms)
 };
 
 // Device-side per-RHS state of the loop.
@@ -77,7 +78,8 @@ struct BatchDev {
     double *rmax2;
     const cudaGraphConditionalHandle *h_iter;   // per RHS outside lockstep groups
     const cudaGraphConditionalHandle *h_ref;
-    int *fresh;                                 // per RHS: stopped right after a refresh
+    int *fresh;                                 // per RHS: 1 stopped right after a refresh, 2 stopped
+                                                // unconfirmed (below defer2, no refresh)
     const int *group;                           // per RHS: lockstep group, -1 if none
     const cudaGraphConditionalHandle *h_group;  // per group
     int ngroups;
@@ -107,7 +109,13 @@ __global__ void k_batch_check_iter(BatchDev d, int n, int reliable, cudaGraphCon
                 if (d.group[i] >= 0) it.scal->skip = 1;
             } else {
                 if (s.rr > d.rmax2[i]) d.rmax2[i] = s.rr;
-                ref = (s.rr <= it.d2 * d.rmax2[i] || s.rr <= it.tol2 || k >= it.max_iter) ? 1 : 0;
+                if (it.defer2 > 0.0 && s.rr <= it.defer2) {
+                    a = 0;   // the caller folds the correction and confirms
+                    d.fresh[i] = 2;
+                } else {
+                    ref = (s.rr <= it.d2 * d.rmax2[i] || (it.defer2 <= 0.0 && s.rr <= it.tol2) ||
+                           k >= it.max_iter) ? 1 : 0;
+                }
             }
             d.active[i] = a;
         }
@@ -440,7 +448,8 @@ wc_status resolve_ras(wc_lattice lat, wc_field b, const wc_solve_params &p, wc_r
 using namespace wc;
 
 static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_field *bs, const wc_solve_params *p,
-                            const double *tol_scale, wc_solve_info *infos);
+                            const double *tol_scale, wc_solve_info *infos, double defer_margin = 0.0,
+                            int *unconfirmed = nullptr);
 static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_field *bs,
                                 const wc_solve_params *p, wc_solve_info *infos);
 
@@ -474,9 +483,12 @@ extern "C" wc_status wc_solve_batch(int n, const wc_lattice *lats, wc_field *xs,
 }
 
 // The batched solve proper, on checked arguments.  tol_scale (may be null):
-// per-RHS factors on p->tol.
+// per-RHS factors on p->tol.  defer_margin > 0 (reliable solver, a caller
+// that recomputes every true residual): an RHS whose recurrence residual
+// falls below defer_margin tol stops without a last FP64 refresh, its
+// correction folded into x; unconfirmed[i] (n entries) is then set to 1.
 static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_field *bs, const wc_solve_params *p,
-                            const double *tol_scale, wc_solve_info *infos)
+                            const double *tol_scale, wc_solve_info *infos, double defer_margin, int *unconfirmed)
 {
     const bool reliable = p->solver == WC_SOLVER_RELIABLE;
     auto t0 = std::chrono::steady_clock::now();
@@ -614,7 +626,8 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
         std::vector<BatchItem> items(n);
         for (int i = 0; i < n; ++i) {
             const double dl = (P[i].delta > 0.0 && P[i].delta < 1.0) ? P[i].delta : 0.01;
-            items[i] = BatchItem{R.S[i].scal, tol2[i], dl * dl, P[i].max_iter, 0};
+            items[i] = BatchItem{R.S[i].scal, tol2[i], dl * dl, P[i].max_iter, 0,
+                                 defer_margin * defer_margin * tol2[i]};
         }
         st = check_cuda(nullptr, to_device(&R.d_items, items), "copy");
         if (st == WC_OK) st = check_cuda(nullptr, to_device(&R.d_iters, iters), "copy");
@@ -740,9 +753,15 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
                             "memset");
             continue;
         }
+        if (reliable && fresh[i] == 2) {   // stopped unconfirmed: fold the correction only
+            st = check_cuda(lats[i], hp_add_lo(lats[i], S, static_cast<double2 *>(xs[i]->data), R.LW[i].xlo),
+                            "hp_add_lo");
+            if (unconfirmed) unconfirmed[i] = 1;
+        }
         if (reliable && fresh[i]) {
-            st = check_cuda(lats[i], cudaMemcpyAsync(S.scal_host, S.scal, sizeof(SolverScalars),
-                                                     cudaMemcpyDeviceToHost, S.stream), "copy");
+            if (st == WC_OK)
+                st = check_cuda(lats[i], cudaMemcpyAsync(S.scal_host, S.scal, sizeof(SolverScalars),
+                                                         cudaMemcpyDeviceToHost, S.stream), "copy");
             continue;
         }
         if (reliable)
@@ -796,7 +815,8 @@ static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_
     auto t0 = std::chrono::steady_clock::now();
     std::vector<wc_lattice> H(n, nullptr);
     std::vector<wc_field> fe(5 * (size_t)n, nullptr);   // per RHS: b_e, b_o, x_e, x_o, b^_e
-    std::vector<double> bb(n, 0.0), scale(n, 1.0);
+    std::vector<double> bb(n, 0.0), bbh(n, 0.0), scale(n, 1.0);
+    std::vector<int> unconfirmed(n, 0);
     wc_status st = WC_OK;
     auto F = [&](int i, int k) -> wc_field & { return fe[5 * (size_t)i + k]; };
     std::map<wc_lattice, int> used;   // right-hand sides so far per lattice
@@ -822,10 +842,9 @@ static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_
         if (st == WC_OK) st = check_cuda(lat, launch_split(lat, xs[i], F(i, 2), F(i, 3), s), "split");
         if (st == WC_OK) st = check_cuda(lat, launch_eo(lat, 1, 4, 0, nullptr, F(i, 1), t, 0.0, s), "A_oo^-1 b_o");
         if (st == WC_OK) st = check_cuda(lat, launch_eo(lat, 0, 2, 0, t, F(i, 0), F(i, 4), lat->kappa, s), "b^_e");
-        double bbh = 0.0;
         if (st == WC_OK) st = reduce_norm2(lat, bs[i], &bb[i]);
-        if (st == WC_OK) st = reduce_norm2(H[i], F(i, 4), &bbh);
-        if (st == WC_OK && bb[i] > 0.0 && bbh > 0.0) scale[i] = sqrt(bb[i] / bbh);
+        if (st == WC_OK) st = reduce_norm2(H[i], F(i, 4), &bbh[i]);
+        if (st == WC_OK && bb[i] > 0.0 && bbh[i] > 0.0) scale[i] = sqrt(bb[i] / bbh[i]);
     }
     std::vector<wc_field> xe(n), bh(n);
     for (int i = 0; i < n; ++i) {
@@ -834,8 +853,12 @@ static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_
     }
     wc_solve_params q = *p;
     q.even_odd = 0;
+    // reliable: the half solves end without their last FP64 refresh (the
+    // full residual below confirms, as in the single even-odd solve)
+    const double margin = p->solver == WC_SOLVER_RELIABLE ? defer_margin() : 0.0;
     if (st == WC_OK) {
-        const wc_status sc = batch_core(n, H.data(), xe.data(), bh.data(), &q, scale.data(), infos);
+        const wc_status sc = batch_core(n, H.data(), xe.data(), bh.data(), &q, scale.data(), infos, margin,
+                                        unconfirmed.data());
         if (sc == WC_ERR_CUDA || sc == WC_ERR_ARG || sc == WC_ERR_STATE) st = sc;
     }
     wc_status worst = WC_OK;
@@ -843,6 +866,19 @@ static wc_status batch_even_odd(int n, const wc_lattice *lats, wc_field *xs, wc_
         wc_lattice lat = lats[i];
         double rr = 0.0;
         st = eo_reconstruct_residual(lat, 0, F(i, 0), F(i, 1), F(i, 2), F(i, 3), xs[i], &rr);
+        if (st == WC_OK && unconfirmed[i] && bb[i] > 0.0 && !(rr <= p->tol * p->tol * bb[i])) {
+            // the deferred confirmation failed: resume this Schur solve from
+            // x_e on the host, confirming in FP64 itself
+            wc_solve_params qi = q;
+            qi.tol = p->tol * scale[i];
+            wc_solve_info sub{};
+            H[i]->st.stream = lat->stream;
+            const wc_status sr = bicgstab(H[i], H[i]->st, 0, F(i, 2), F(i, 4), qi, &sub, infos[i].iters, bbh[i]);
+            if (sr != WC_OK && sr != WC_ERR_NOT_CONVERGED && sr != WC_ERR_BREAKDOWN) st = sr;
+            infos[i].iters = sub.iters;
+            infos[i].restarts += 1 + sub.restarts;
+            if (st == WC_OK) st = eo_reconstruct_residual(lat, 0, F(i, 0), F(i, 1), F(i, 2), F(i, 3), xs[i], &rr);
+        }
         if (st != WC_OK) break;
         wc_solve_info &inf = infos[i];
         inf.true_rel_resid = bb[i] > 0.0 ? sqrt(rr / bb[i]) : 0.0;

@@ -64,9 +64,8 @@ namespace {
 
 double2 *d2(wc_field f) { return static_cast<double2 *>(f->data); }
 
-// An even-odd reliable half solve ends unconfirmed at |r| <= m tol, m = 0.5
-// unless WC_EO_DEFER_MARGIN gives another (0: always confirm in the half
-// solve; a large m makes the confirmation fail, for tests of the resume).
+}  // namespace
+
 double defer_margin()
 {
     const char *e = getenv("WC_EO_DEFER_MARGIN");
@@ -74,8 +73,6 @@ double defer_margin()
     const double m = atof(e);
     return m > 0.0 && isfinite(m) ? m : 0.0;
 }
-
-}  // namespace
 
 wc_status read_scalars(wc_lattice lat, SolverState &S)
 {

@@ -28,6 +28,11 @@ wc_status enqueue_iteration(wc_lattice lat, SolverState &S, const wc_solve_param
                             const SolverVecs &w);
 wc_status enqueue_true_residual(wc_lattice lat, SolverState &S, int kind, wc_field x, wc_field b,
                                 const SolverVecs &w);
+// An even-odd reliable half solve (single or batched) ends unconfirmed at
+// |r| <= m tol: m = 0.5 unless the environment variable WC_EO_DEFER_MARGIN
+// gives another (0: the half solve always confirms in FP64 itself; a large
+// m makes the full-residual confirmation fail, for tests of the resume).
+double defer_margin();
 // end of an even-odd solve of the full lattice lat from its half fields:
 // x_o reconstructed, x = (x_e, x_o), *rr = |b - op x|^2 (one synchronisation)
 wc_status eo_reconstruct_residual(wc_lattice lat, int kind, wc_field be, wc_field bo, wc_field xe, wc_field xo,

@@ -196,6 +196,30 @@ def test_even_odd_reliable_confirmation_paths(margin, monkeypatch):
     assert info.iters >= base.iters - 1
 
 
+@pytest.mark.parametrize("margin", ["0", "1e3"])
+@pytest.mark.parametrize("krylov", [1, 2])
+def test_even_odd_batch_confirmation_paths(margin, krylov, monkeypatch):
+    """The batched even-odd reliable solve with its half solves confirming
+    in FP64 themselves (margin 0), and with a margin so large that every
+    full-residual confirmation fails and each Schur solve resumes on the
+    host: every source converges, checked with the oracle's M."""
+    w = wc()
+    monkeypatch.setenv("WC_EO_DEFER_MARGIN", margin)
+    dims = (6, 6, 6, 8)
+    U = synth.exp_links(dims, 0.3, 1700)
+    lat = make_lattice(dims, U, 1.0, 0.124, -1)
+    srcs = [synth.point_source(dims, spin=k, colour=2 - k) for k in range(3)]
+    xs = [lat.field(0) for _ in srcs]
+    bs = [lat.field(0).load(src) for src in srcs]
+    infos = w.solve_batch([lat] * 3, xs, bs, tol=1e-10, solver=w.SOLVER_RELIABLE, krylov_prec=krylov,
+                          even_odd=True, max_iter=2000)
+    for info, x, src in zip(infos, xs, srcs):
+        assert info.status == 0 and info.true_rel_resid <= 1e-10
+        sol = x.store(np.zeros_like(src))
+        r = src - oracle.apply_M(dims, -1, 0.124, 1.0, U, sol)
+        assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
+
+
 def test_even_odd_action_and_zero_source():
     """M^+ solves through the action (even-odd vs full lattice give the same
     S), and a zero source gives x = 0."""
