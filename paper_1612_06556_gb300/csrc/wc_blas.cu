@@ -715,22 +715,6 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_xr(long long n, float4 *xlo, c
     body_lo_xr(n, xlo, phat, shat, s, t, r, rhat, rs, sc);
 }
 
-// r was replaced by the true residual: rho = <rhat, r>,
-// beta = (rho / rho0)(alpha / omega); rr keeps the FP64 true residual that
-// the refresh wrote
-__global__ void __launch_bounds__(kRedBlock) k_lo_rho(long long n, const float4 *rhat, const float4 *r,
-                                                      ReduceScratch rs, SolverScalars *sc)
-{
-    float acc[2] = {0.f, 0.f};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float4 h = rhat[i], a = r[i];
-        acc[0] = fmaf(h.x, a.x, fmaf(h.y, a.y, fmaf(h.z, a.z, fmaf(h.w, a.w, acc[0]))));
-        acc[1] = fmaf(h.x, a.y, fmaf(-h.y, a.x, fmaf(h.z, a.w, fmaf(-h.w, a.z, acc[1]))));
-    }
-    if (grid_reduce_f<2>(acc, rs, rs.result)) lo_rho_update(rs.result, sc);
-}
-
 // ------------------------------------------------------------------------
 // The same updates with FP16 storage (per-site scale) of the BiCGStab
 // vectors: one site per thread, FP32 arithmetic, FP32 partial sums; the
@@ -891,23 +875,12 @@ __global__ void __launch_bounds__(kRedBlock) k_lo_xr_h(int V, float4 *xlo, HF ph
     body_lo_xr_h(V, xlo, phat, shat, s, t, r, rhat, rs, sc);
 }
 
-__global__ void __launch_bounds__(kRedBlock) k_lo_rho_h(int V, HF rhat, HF r, ReduceScratch rs, SolverScalars *sc)
-{
-    float acc[2] = {0.f, 0.f};
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
-        cx<float> a[12], b[12];
-        hld(rhat, V, x, a);
-        hld(r, V, x, b);
-        cdot_acc(a, b, acc);
-    }
-    if (grid_reduce_f<2>(acc, rs, rs.result)) lo_rho_update(rs.result, sc);
-}
-
 // End of a reliable update in one pass (the FP64 residual, its
 // low-precision copy and the new rho of the recurrence): r = b - r (r holds
 // op x), rr = |r|^2; rlo = r rounded to the Krylov storage PL (FP32, or
-// FP16 with its per-site scale); rho = <rhat, rlo> of the stored rlo, beta
-// recomputed as lo_rho does.  One site per thread.
+// FP16 with its per-site scale); rho = <rhat, rlo> of the stored rlo and
+// beta from rho0, alpha, omega of the last step (lo_rho_update).  One site
+// per thread.
 template <class PL>
 __global__ void __launch_bounds__(kRedBlock) k_refresh_tail(int V, const void *b, void *r, void *rlo, float *rlo_n,
                                                             const void *rhat, const float *rhat_n, ReduceScratch rs,
@@ -1145,16 +1118,6 @@ cudaError_t lo_xr(wc_lattice lat, SolverState &S, wc_field xlo, wc_field phat, w
                                          S.scal);
     else
         k_lo_xr<<<WC_GRID(n)>>>(n, f4(xlo), f4(phat), f4(shat), f4(s), f4(t), f4(r), f4(rhat), S.red, S.scal);
-    return cudaGetLastError();
-}
-cudaError_t lo_rho(wc_lattice lat, SolverState &S, wc_field rhat, wc_field r)
-{
-    const int V = lat->g.V;
-    const long long n = 6LL * V;
-    if (half_vectors(r))
-        k_lo_rho_h<<<WC_GRID_SITES(V)>>>(V, hf(rhat), hf(r), S.red, S.scal);
-    else
-        k_lo_rho<<<WC_GRID(n)>>>(n, f4(rhat), f4(r), S.red, S.scal);
     return cudaGetLastError();
 }
 cudaError_t refresh_tail(wc_lattice lat, SolverState &S, const wc_field b, wc_field r_hp, wc_field r, wc_field rhat)

@@ -331,7 +331,7 @@ static wc_status eo_bicgstab(wc_lattice lat, int kind, wc_field x, wc_field b, c
             const wc_status sr = bicgstab(h, h->st, kind, xe, bh, q, &inf, iters, bbh);
             if (sr != WC_OK && sr != WC_ERR_NOT_CONVERGED && sr != WC_ERR_BREAKDOWN) st = sr;
             iters = inf.iters;
-            restarts += inf.restarts;
+            restarts += 1 + inf.restarts;
             half_status = inf.status;
             if (st != WC_OK) break;
         }

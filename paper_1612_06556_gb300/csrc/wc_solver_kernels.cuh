@@ -41,10 +41,8 @@ cudaError_t lo_omega(wc_lattice lat, SolverState &S, wc_field t, wc_field s);
 // xlo += alpha phat + omega shat; r = s - omega t; rho, beta, rr updated
 cudaError_t lo_xr(wc_lattice lat, SolverState &S, wc_field xlo, wc_field phat, wc_field shat, wc_field s,
                   wc_field t, wc_field r, wc_field rhat);
-// after r was replaced: rho = <rhat, r>, beta from rho0 (rr untouched)
-cudaError_t lo_rho(wc_lattice lat, SolverState &S, wc_field rhat, wc_field r);
 // r_hp = b - r_hp (r_hp holds op x), rr = |r_hp|^2, r = r_hp in the Krylov
-// storage, rho = <rhat, r> and beta as lo_rho: one pass (FP64 b and r_hp)
+// storage, rho = <rhat, r> and beta recomputed: one pass (FP64 b and r_hp)
 cudaError_t refresh_tail(wc_lattice lat, SolverState &S, const wc_field b, wc_field r_hp, wc_field r, wc_field rhat);
 // x (FP64) += xlo (FP32); xlo = 0
 cudaError_t hp_add_lo(wc_lattice lat, SolverState &S, double2 *x, wc_field xlo);
