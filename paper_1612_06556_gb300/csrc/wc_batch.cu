@@ -75,7 +75,7 @@ struct BatchDev {
     int *iters;
     int *active;
     int *refresh;
-    double *rmax2;
+    double *rmax2;                              // [2n]: max |r|^2 since the last refresh, last |r|^2
     const cudaGraphConditionalHandle *h_iter;   // per RHS outside lockstep groups
     const cudaGraphConditionalHandle *h_ref;
     int *fresh;                                 // per RHS: 1 stopped right after a refresh, 2 stopped
@@ -108,13 +108,17 @@ __global__ void k_batch_check_iter(BatchDev d, int n, int reliable, cudaGraphCon
                 d.fresh[i] = 0;
                 if (d.group[i] >= 0) it.scal->skip = 1;
             } else {
+                const double prev = d.rmax2[n + i];
+                d.rmax2[n + i] = s.rr;
                 if (s.rr > d.rmax2[i]) d.rmax2[i] = s.rr;
                 if (it.defer2 > 0.0 && s.rr <= it.defer2) {
                     a = 0;   // the caller folds the correction and confirms
                     d.fresh[i] = 2;
                 } else {
-                    ref = (s.rr <= it.d2 * d.rmax2[i] || (it.defer2 <= 0.0 && s.rr <= it.tol2) ||
-                           k >= it.max_iter) ? 1 : 0;
+                    // below tol but above defer2 the step refreshes only when
+                    // the recurrence stopped decreasing
+                    const bool at_tol = s.rr <= it.tol2 && (it.defer2 <= 0.0 || !(s.rr < prev));
+                    ref = (s.rr <= it.d2 * d.rmax2[i] || at_tol || k >= it.max_iter) ? 1 : 0;
                 }
             }
             d.active[i] = a;
@@ -151,6 +155,7 @@ __global__ void k_batch_check_refresh(BatchDev d, int n, cudaGraphConditionalHan
                 d.fresh[i] = 1;   // x and the FP64 residual rr are current
             }
             d.rmax2[i] = rr;
+            d.rmax2[n + i] = rr;
             d.active[i] = a;
         }
         const int g = d.group[i];
@@ -568,13 +573,16 @@ static wc_status batch_core(int n, const wc_lattice *lats, wc_field *xs, wc_fiel
     for (int i = 0; i < n && st == WC_OK; ++i) st = check_cuda(lats[i], cudaStreamSynchronize(R.streams[i]), "sync");
     if (st != WC_OK) return st;
     std::vector<int> active(n, 0), iters(n, 0), zeros(n, 0), fresh(n, 0);
-    std::vector<double> rmax2(n, 0.0);
+    // per RHS: the largest |r|^2 since the last refresh, then (entries n +
+    // i) the |r|^2 of the previous step
+    std::vector<double> rmax2(2 * (size_t)n, 0.0);
     int any = 0;
     for (int i = 0; i < n; ++i) {
         infos[i] = wc_solve_info{};
         tol2[i] = P[i].tol * P[i].tol * bb[i];
         const SolverScalars &h = *R.S[i].scal_host;
         rmax2[i] = h.rr;
+        rmax2[n + i] = h.rr;
         if (!isfinite(bb[i]) || (h.flags & FLAG_NAN) || !isfinite(h.rr)) {
             infos[i].status = WC_ERR_NAN;
         } else if (bb[i] == 0.0 || h.rr <= tol2[i]) {

@@ -668,7 +668,7 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
         if (st == WC_OK)
             st = check_cuda(lat, lo_init(lat, S, w.r, w.rhat, w.p, w.v, w.xlo), "lo_init");
         if (st != WC_OK) return st;
-        double rmax2 = rr_true, rr_refresh = rr_true;
+        double rmax2 = rr_true, rr_refresh = rr_true, rr_prev = rr_true;
         bool breakdown = false, converged = false, diverged = false;
         while (inf.iters < p.max_iter) {
             st = enqueue_lo_iteration(lat, S, p, kind, w);
@@ -687,6 +687,8 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
                 break;
             }
             if (h.rr > rmax2) rmax2 = h.rr;
+            const double prev = rr_prev;
+            rr_prev = h.rr;
             if (defer_rr > 0.0 && h.rr <= defer_rr) {
                 // the caller confirms with its own true residual: fold the
                 // correction only
@@ -697,7 +699,10 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
                 converged = true;
                 break;
             }
-            if (h.rr <= d2 * rmax2 || (defer_rr <= 0.0 && h.rr <= tol2)) {
+            // deferring, a recurrence below tol but above defer_rr refreshes
+            // only once it stops decreasing
+            const bool at_tol = h.rr <= tol2 && (defer_rr <= 0.0 || !(h.rr < prev));
+            if (h.rr <= d2 * rmax2 || at_tol) {
                 // reliable update: fold the FP32 correction into the FP64
                 // solution and restart the recurrence from the true residual
                 // (its low-precision copy and rho in the same pass)
@@ -712,6 +717,7 @@ wc_status reliable_bicgstab(wc_lattice lat, SolverState &S, int kind, wc_field x
                 }
                 rmax2 = rr_true;
                 rr_refresh = rr_true;
+                rr_prev = rr_true;
             }
         }
         if (converged) {
