@@ -176,8 +176,8 @@ def test_even_odd_reported_residual_is_that_of_the_solution(solver, krylov, arit
 def test_even_odd_reliable_confirmation_paths(margin, monkeypatch):
     """Even-odd reliable solves with the half solve's own FP64 confirmation
     (margin 0) and with a deferral margin so large that the full-residual
-    check fails and the half solve resumes: both end converged, checked with
-    the oracle's M, in at least the default path's iterations."""
+    check fails and the half solve resumes (reported as a restart): both end
+    converged, checked with the oracle's M."""
     w = wc()
     dims, kappa, csw, tbc = (8, 8, 8, 16), 0.125, 1.0, -1
     U = synth.exp_links(dims, 0.3, 161)
@@ -185,7 +185,6 @@ def test_even_odd_reliable_confirmation_paths(margin, monkeypatch):
     lat = make_lattice(dims, U, csw, kappa, tbc)
     b = lat.field(0).load(src)
     kw = dict(tol=1e-10, solver=w.SOLVER_RELIABLE, krylov_prec=w.F16, even_odd=True, max_iter=2000)
-    base = lat.solve(lat.field(0), b, **kw)
     monkeypatch.setenv("WC_EO_DEFER_MARGIN", margin)
     x = lat.field(0)
     info = lat.solve(x, b, **kw)
@@ -193,7 +192,7 @@ def test_even_odd_reliable_confirmation_paths(margin, monkeypatch):
     sol = x.store(np.zeros_like(src))
     r = src - oracle.apply_M(dims, tbc, kappa, csw, U, sol)
     assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
-    assert info.iters >= base.iters - 1
+    assert info.restarts == (0 if margin == "0" else 1)
 
 
 @pytest.mark.parametrize("margin", ["0", "1e3"])
@@ -215,6 +214,7 @@ def test_even_odd_batch_confirmation_paths(margin, krylov, monkeypatch):
                           even_odd=True, max_iter=2000)
     for info, x, src in zip(infos, xs, srcs):
         assert info.status == 0 and info.true_rel_resid <= 1e-10
+        assert info.restarts == (0 if margin == "0" else 1)
         sol = x.store(np.zeros_like(src))
         r = src - oracle.apply_M(dims, -1, 0.124, 1.0, U, sol)
         assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(src)
