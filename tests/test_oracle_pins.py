@@ -511,6 +511,25 @@ def test_schur_solve_reconstructs_full_solution():
     assert np.allclose(op.M(x), b, atol=1e-11)
 
 
+def test_full_residual_of_a_reconstruction_is_the_schur_residual():
+    """For any x_e (not only a solution) and x_o = A_oo^-1 (b_o + k H_oe
+    x_e), the full residual b - M x vanishes on the odd sites and equals
+    the Schur residual b^_e - M^ x_e on the even sites: an even-odd solve's
+    full true residual and its half solve's residual are one quantity."""
+    dims = (4, 2, 4, 4)
+    op, eo = _eo_setup(dims, 71)
+    b = synth.gaussian_source(dims, 72)
+    xe = synth.gaussian_source(dims, 73)
+    xe[eo.odd] = 0
+    x = eo.reconstruct(xe, b)
+    r = b - op.M(x)
+    rs = eo.prepare(b) - eo.schur(xe)
+    scale = np.abs(b).max() + np.abs(op.M(x)).max()
+    assert np.abs(r[eo.odd]).max() <= 1e-13 * scale
+    assert np.abs(r[eo.even] - rs[eo.even]).max() <= 1e-13 * scale
+    assert np.abs(rs[eo.even]).max() > 1e-2 * scale   # x_e is far from a solution
+
+
 def test_schur_determinant_identity_and_adjoint():
     """det M = det A_oo det M^, and M^+ is the conjugate transpose of M^."""
     dims = (2, 2, 2, 4)
