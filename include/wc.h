@@ -157,7 +157,8 @@ typedef struct {
 
 typedef struct {
     int iters;             /* BiCGStab iterations performed */
-    int restarts;
+    int restarts;          /* restarts after a failed true-residual check (the resume of an even-odd
+                              RELIABLE half solve whose deferred confirmation failed counts as one) */
     double true_rel_resid; /* |b - M x| / |b| recomputed in FP64 at the end */
     double seconds;        /* wall time of the solve on the host clock */
     wc_status status;
